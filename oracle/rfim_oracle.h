@@ -1,0 +1,89 @@
+/*
+ * rfim_oracle.h -- CPU oracle for the time- and frequency-domain sigma cuts.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is the plain, slow, single-threaded
+ * reference that the GPU library is checked against.  Only the test suite,
+ * the package smoke check and the CPU-baseline leg of the benchmark may load
+ * it.  It shares no code, header, table or constant with the CUDA library.
+ *
+ * Method (Sclocco, Vohl, van Nieuwpoort, "Real-Time RFI Mitigation for the
+ * Apertif Radio Transient System", arXiv:2001.03389):
+ *   TDSC  Sec. IV, TDSC paragraph and Fig. 2: per (beam, channel), compare every
+ *         time sample of the batch with the batch mean and standard deviation;
+ *         |x - mu| > k sigma (symmetric, Fig. 2 caption) flags the sample,
+ *         which is replaced by the batch mean.
+ *   FDSC  Sec. IV, FDSC paragraph and Fig. 3: per (beam, time sample), subtract
+ *         from each channel the mean of its channel bin, compare the corrected
+ *         value with the mean and standard deviation of the corrected values of
+ *         all channels, and replace an outlier's ORIGINAL value by its bin mean.
+ *   Replacement strategy parameter (mean or median): Sec. IV, last paragraph.
+ *   Iterations: Sec. V-A (three iterations in production) and Sec. V-B.
+ *
+ * Readings taken where the paper is silent (all listed in the design notes):
+ *   - sigma is the population standard deviation (divide by the count);
+ *   - statistics of each iteration are taken over all current values of the
+ *     row/column, including values replaced by earlier iterations;
+ *   - uint8 decisions use exact integers and a single IEEE rounding:
+ *       TDSC: flag iff (double)((T*x - S)^2) > fl(k2 * (double)(T*Q - S^2)),
+ *       FDSC: flag iff (double)(C*D^2) > fl(k2 * (double)sum(D^2)), with
+ *             D = (L/G_g)(G_g*x - S_g), L = lcm of the bin sizes,
+ *     where k2 = fl(k*k);
+ *   - uint8 mean replacement rounds half up: floor((2S + n) / (2n));
+ *   - median replacement is the lower median (rank floor((n-1)/2), 0-based)
+ *     of the current values, taken over all of them;
+ *   - FDSC bins are contiguous groups of `bin` channels, the last one may be
+ *     shorter; bin == C is the single-bin (bandpass-corrected) case;
+ *   - the combined cleaner runs all TDSC iterations on every row, then all
+ *     FDSC iterations on every column of the TDSC output;
+ *   - flags: one byte per sample, bit 0 = TDSC, bit 1 = FDSC, OR-ed over
+ *     iterations.
+ *   - float32 inputs must be finite; the float median orders -0 before +0.
+ */
+#ifndef RFIM_ORACLE_H
+#define RFIM_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* layout: 0 = beam x channel x time (time fastest), 1 = beam x time x channel */
+#define ORC_LAYOUT_BCT 0
+#define ORC_LAYOUT_BTC 1
+/* replacement strategy */
+#define ORC_REPLACE_MEAN 0
+#define ORC_REPLACE_MEDIAN 1
+/* return codes */
+#define ORC_OK 0
+#define ORC_ERR_ARG 1
+#define ORC_ERR_RANGE 2
+
+/* One cut's parameters. enabled == 0 skips the method in orc_clean_*. */
+typedef struct {
+  int enabled;
+  double k;        /* threshold in units of sigma, > 0 */
+  int iterations;  /* 1..16 */
+  int replace;     /* ORC_REPLACE_* */
+  int bin;         /* FDSC channel-bin size, 1..C (ignored for TDSC) */
+} orc_cut;
+
+/* in and out may alias exactly (in-place).  flags: B*C*T bytes, nullable. */
+int orc_clean_u8(const uint8_t* in, uint8_t* out, uint8_t* flags,
+                 int64_t B, int64_t C, int64_t T, int layout,
+                 const orc_cut* tdsc, const orc_cut* fdsc);
+int orc_clean_f32(const float* in, float* out, uint8_t* flags,
+                  int64_t B, int64_t C, int64_t T, int layout,
+                  const orc_cut* tdsc, const orc_cut* fdsc);
+
+/* Single-row / single-column primitives (exported for the pinning tests). */
+void orc_tdsc_row_u8(uint8_t* x, uint8_t* f, int64_t n, double k, int iters, int replace);
+void orc_fdsc_col_u8(uint8_t* x, uint8_t* f, int64_t n, double k, int iters, int replace, int64_t bin);
+void orc_tdsc_row_f32(float* x, uint8_t* f, int64_t n, double k, int iters, int replace);
+void orc_fdsc_col_f32(float* x, uint8_t* f, int64_t n, double k, int iters, int replace, int64_t bin);
+uint8_t orc_lower_median_u8(const uint8_t* x, int64_t n);
+float orc_lower_median_f32(const float* x, int64_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

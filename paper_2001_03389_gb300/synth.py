@@ -1,0 +1,180 @@
+"""Seeded synthetic filterbanks shaped like the paper's ARTS data.
+
+This module only draws inputs; it holds none of the cleaning arithmetic, so
+both the GPU path and the CPU oracle can be fed from it.
+
+Recipe (the paper's own data are not available; these stand in for them):
+  * Noise: uint8 blocks are round(N(128, 16^2)) clipped to [0, 255]; float32
+    blocks are g_c * chi^2_2 with a per-channel bandpass gain g_c drawn
+    log-uniform in [0.5, 2] (sigma_c = 2 g_c).  The paper's own simulation
+    (Sec. V-A) uses N(0, 1) on an ARTS-shaped canvas.
+  * Narrowband RFI (Sec. V-A: "narrow-band periodic pulses"): a fraction of
+    channels carries +A_nb * (1 + 0.5 sin(2 pi t / P + phi)) for every t,
+    P ~ U[500, 5000] samples, phi ~ U[0, 2 pi); optionally constant (no sine).
+  * Broadband RFI (Sec. V-A: "bright low-DM broadband pulses"): a set of time
+    samples carries +A_bb in every channel; bursts are `bb_width` samples wide.
+  * One faint dispersed pulse (Sec. V-A, the FRB stand-in): +A_disp, one
+    sample wide per channel, delayed per Eq. 2, delay(nu) proportional to
+    nu^-2 - nu_hi^-2 over the Apertif band (1250-1550 MHz, channel 0 the
+    highest frequency), scaled so the lowest channel lags by `disp_span`
+    samples.
+  * ARTS shapes: 1536 channels, 81.92 us sampling (Sec. V-A footnote),
+    12 beams per node (Sec. V-B).
+Seeds: configuration i uses SeedSequence(2001033890 + i); beam j draws from
+child j of that sequence, so any subset of beams can be regenerated alone.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+SEED_BASE = 2001033890
+F_HI_MHZ = 1550.0
+BW_MHZ = 300.0
+
+
+@dataclasses.dataclass
+class RFIModel:
+    nb_frac: float = 0.02        # fraction of channels with narrowband RFI
+    nb_count: int | None = None  # exact number of narrowband channels (overrides nb_frac)
+    nb_amp: float = 60.0         # narrowband amplitude (uint8 units or sigma_c multiples)
+    nb_sine: bool = True         # sinusoidal amplitude drift
+    bb_frac: float = 0.01        # fraction of time samples hit by broadband bursts
+    bb_count: int | None = None  # exact number of bursts (overrides bb_frac)
+    bb_width: int = 1            # samples per burst
+    bb_amp: float = 90.0
+    disp_amp: float = 20.0       # dispersed pulse amplitude (0 disables)
+    disp_span: int = 300         # delay of the lowest channel, samples
+
+
+def _dispersion_delays(C: int, span: int) -> np.ndarray:
+    """Per-channel delay in samples following Eq. 2 (delay ~ nu^-2 - nu_hi^-2)."""
+    nu = F_HI_MHZ - BW_MHZ * (np.arange(C) + 0.5) / C
+    d = nu ** -2 - F_HI_MHZ ** -2
+    d = d / d.max() if d.max() > 0 else d
+    return np.rint(d * span).astype(np.int64)
+
+
+def _beam_rng(cfg_seed: int, beam: int) -> np.random.Generator:
+    ss = np.random.SeedSequence(cfg_seed, spawn_key=(beam,))
+    return np.random.Generator(np.random.PCG64(ss))
+
+
+def _rfi_offsets(rng, C: int, T: int, m: RFIModel, scale: np.ndarray | float):
+    """Additive RFI for one beam, as a float32 (C, T) array in units of `scale`."""
+    add = np.zeros((C, T), dtype=np.float32)
+    n_nb = m.nb_count if m.nb_count is not None else int(round(m.nb_frac * C))
+    if n_nb > 0:
+        chans = rng.choice(C, size=min(n_nb, C), replace=False)
+        t = np.arange(T, dtype=np.float64)
+        for c in chans:
+            if m.nb_sine:
+                P = rng.uniform(500.0, 5000.0)
+                phi = rng.uniform(0.0, 2 * np.pi)
+                add[c] += (m.nb_amp * (1.0 + 0.5 * np.sin(2 * np.pi * t / P + phi))).astype(np.float32)
+            else:
+                add[c] += m.nb_amp
+    n_bb = m.bb_count if m.bb_count is not None else int(round(m.bb_frac * T / max(m.bb_width, 1)))
+    if n_bb > 0:
+        starts = rng.choice(max(T - m.bb_width + 1, 1), size=min(n_bb, max(T - m.bb_width + 1, 1)), replace=False)
+        for s in starts:
+            add[:, s:s + m.bb_width] += m.bb_amp
+    if m.disp_amp:
+        t0 = int(rng.integers(0, max(T // 2, 1)))
+        delays = _dispersion_delays(C, m.disp_span)
+        ts = t0 + delays
+        ok = ts < T
+        add[np.arange(C)[ok], ts[ok]] += m.disp_amp
+    return add * scale
+
+
+def beam_u8(cfg_seed: int, beam: int, C: int, T: int, model: RFIModel, layout: str = "bct") -> np.ndarray:
+    """One uint8 beam: round(N(128,16^2) + RFI) clipped to [0,255]; (C,T) or (T,C)."""
+    rng = _beam_rng(cfg_seed, beam)
+    x = rng.standard_normal((C, T), dtype=np.float32)
+    x *= 16.0
+    x += 128.0
+    x += _rfi_offsets(rng, C, T, model, 1.0)
+    np.rint(x, out=x)
+    np.clip(x, 0, 255, out=x)
+    out = x.astype(np.uint8)
+    return np.ascontiguousarray(out.T) if layout == "btc" else out
+
+
+def beam_f32(cfg_seed: int, beam: int, C: int, T: int, model: RFIModel, layout: str = "bct") -> np.ndarray:
+    """One float32 beam: g_c chi^2_2 noise plus RFI in multiples of sigma_c = 2 g_c."""
+    rng = _beam_rng(cfg_seed, beam)
+    g = np.exp(rng.uniform(np.log(0.5), np.log(2.0), size=C)).astype(np.float32)
+    x = rng.standard_exponential((C, T), dtype=np.float32)
+    x *= 2.0                       # chi^2 with 2 degrees of freedom
+    x += _rfi_offsets(rng, C, T, model, 1.0)  # in sigma units (sigma of chi^2_2 is 2)
+    x *= g[:, None]
+    return np.ascontiguousarray(x.T) if layout == "btc" else x
+
+
+# ---------------------------------------------------------------------------
+# The paper-shaped workloads.
+# ---------------------------------------------------------------------------
+
+def cfg1_model() -> RFIModel:
+    # 3 persistent narrowband channels at +60, 5 broadband impulses 4 samples wide at +90,
+    # one dispersed pulse at +20.
+    return RFIModel(nb_count=3, nb_amp=60.0, nb_sine=False, bb_count=5, bb_width=4, bb_amp=90.0,
+                    disp_amp=20.0, disp_span=300)
+
+
+def cfg2_model() -> RFIModel:
+    # 2% of channels sinusoidal narrowband around +60, 1% of samples broadband +90, one pulse.
+    return RFIModel(nb_frac=0.02, nb_amp=60.0, nb_sine=True, bb_frac=0.01, bb_width=1, bb_amp=90.0,
+                    disp_amp=20.0, disp_span=300)
+
+
+def cfg3_model() -> RFIModel:
+    # Same mix at 5x density, amplitudes as multiples of sigma_c: 60/16 = 3.75, 90/16 = 5.625, 20/16 = 1.25.
+    return RFIModel(nb_frac=0.10, nb_amp=3.75, nb_sine=True, bb_frac=0.05, bb_width=1, bb_amp=5.625,
+                    disp_amp=1.25, disp_span=300)
+
+
+CONFIGS = {
+    1: dict(name="tdsc_1x64x2048_u8", dtype="u8", B=1, C=64, T=2048, model=cfg1_model,
+            tdsc=dict(k=3.0, iterations=1, replace="mean"), fdsc=None),
+    2: dict(name="arts_12x1536x12500_u8", dtype="u8", B=12, C=1536, T=12500, model=cfg2_model,
+            tdsc=dict(k=3.0, iterations=2, replace="median"),
+            fdsc=dict(k=3.0, iterations=2, replace="median", bin=32)),
+    3: dict(name="fp32_32x4096x8192", dtype="f32", B=32, C=4096, T=8192, model=cfg3_model,
+            tdsc=dict(k=2.5, iterations=3, replace="mean"),
+            fdsc=dict(k=2.5, iterations=3, replace="mean", bin=32)),
+}
+
+
+def seed_of(cfg: int) -> int:
+    return SEED_BASE + cfg
+
+
+def make_beams(cfg: int, beams=None, layout: str = "bct"):
+    """Generate beams of a fixed-shape configuration (1..3) as one (b, C, T) array."""
+    spec = CONFIGS[cfg]
+    ids = list(range(spec["B"])) if beams is None else list(beams)
+    fn = beam_u8 if spec["dtype"] == "u8" else beam_f32
+    model = spec["model"]()
+    return np.stack([fn(seed_of(cfg), j, spec["C"], spec["T"], model, layout) for j in ids])
+
+
+def ragged_shapes(n: int = 200, seed: int | None = None):
+    """Shapes of the ragged batch: C from {384, 768, 1536, 4096}, T ~ U[1000, 25000]."""
+    rng = np.random.Generator(np.random.PCG64(seed_of(4) if seed is None else seed))
+    Cs = rng.choice([384, 768, 1536, 4096], size=n)
+    Ts = rng.integers(1000, 25001, size=n)
+    return [(int(c), int(t)) for c, t in zip(Cs, Ts)]
+
+
+def ragged_beam(j: int, C: int, T: int, layout: str = "bct") -> np.ndarray:
+    """Beam j of the ragged batch, config-2 noise and RFI model."""
+    return beam_u8(seed_of(4), j, C, T, cfg2_model(), layout)
+
+
+def stream_chunk(beam: int, chunk: int, C: int = 1536, T: int = 1250) -> np.ndarray:
+    """Chunk `chunk` of streaming beam `beam` (config-2 model), shape (C, T)."""
+    rng_seed = seed_of(5) * 1_000_003 + beam
+    return beam_u8(rng_seed, chunk, C, T, cfg2_model())

@@ -1,0 +1,446 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself.  The pins are:
+  * hand-worked rows/columns (tests/golden, derivations in the files);
+  * brute force against exact rational arithmetic (fractions.Fraction) of the
+    definitions in Sec. IV -- a formulation with real mu and sigma^2, not the
+    scaled-integer form the oracle evaluates;
+  * closed-form tail fractions on clean noise;
+  * invariants (idempotence, range, untouched unflagged samples) and special
+    cases that reduce one method to another (FDSC with one bin == TDSC on the
+    column; float32 == uint8 on integer-valued data with median replacement);
+  * the qualitative results of Sec. V-A on the paper-shaped synthetic canvas.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from conftest import read_golden
+from paper_2001_03389_gb300 import synth
+
+# ---------------------------------------------------------------------------
+# exact-rational restatements of Sec. IV (used only as pins)
+# ---------------------------------------------------------------------------
+
+
+def _frac_k2(k):
+    return Fraction(k) ** 2  # k is a binary double; its square is an exact rational
+
+
+def rational_tdsc(row, k, iterations, replace):
+    """TDSC on exact rationals: mu = mean, sigma^2 = population variance."""
+    x = [Fraction(int(v)) for v in row]
+    n = len(x)
+    flags = [0] * n
+    k2 = _frac_k2(k)
+    for _ in range(iterations):
+        mu = sum(x) / n
+        var = sum((v - mu) ** 2 for v in x) / n
+        if replace == "mean":
+            r = Fraction(math.floor(mu + Fraction(1, 2)))  # round half up
+        else:
+            r = sorted(x)[(n - 1) // 2]
+        hit = [(v - mu) ** 2 > k2 * var for v in x]
+        for i, h in enumerate(hit):
+            if h:
+                x[i] = r
+                flags[i] = 1
+    return [int(v) for v in x], flags
+
+
+def rational_fdsc(col, k, iterations, replace, bin):
+    """FDSC on exact rationals: bin means, corrected values d, mu', sigma'."""
+    x = [Fraction(int(v)) for v in col]
+    n = len(x)
+    flags = [0] * n
+    k2 = _frac_k2(k)
+    bins = [list(range(s, min(s + bin, n))) for s in range(0, n, bin)]
+    for _ in range(iterations):
+        m = {}
+        rep = {}
+        for b in bins:
+            mb = sum(x[c] for c in b) / len(b)
+            for c in b:
+                m[c] = mb
+            if replace == "mean":
+                rep[tuple(b)] = Fraction(math.floor(mb + Fraction(1, 2)))
+            else:
+                rep[tuple(b)] = sorted(x[c] for c in b)[(len(b) - 1) // 2]
+        d = [x[c] - m[c] for c in range(n)]
+        mu = sum(d) / n
+        var = sum((v - mu) ** 2 for v in d) / n
+        hit = [(d[c] - mu) ** 2 > k2 * var for c in range(n)]
+        for b in bins:
+            for c in b:
+                if hit[c]:
+                    x[c] = rep[tuple(b)]
+                    flags[c] = 1
+    return [int(v) for v in x], flags
+
+
+# ---------------------------------------------------------------------------
+# hand-worked fixtures
+# ---------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("case", read_golden("tdsc_u8_handworked.txt"), ids=lambda c: str(c["params"]))
+def test_tdsc_u8_handworked(oracle, case):
+    p = case["params"]
+    row = np.array(case["in"], dtype=np.uint8)
+    out, fl = oracle.tdsc_row(row, float(p["k"]), int(p["iterations"]), p["replace"])
+    assert out.tolist() == [int(v) for v in case["out"]]
+    assert fl.tolist() == [int(v) for v in case["flag"]]
+
+
+@pytest.mark.parametrize("case", read_golden("fdsc_u8_handworked.txt"), ids=lambda c: str(c["params"]))
+def test_fdsc_u8_handworked(oracle, case):
+    p = case["params"]
+    col = np.array(case["in"], dtype=np.uint8)
+    out, fl = oracle.fdsc_col(col, float(p["k"]), int(p["iterations"]), p["replace"], int(p["bin"]))
+    assert out.tolist() == [int(v) for v in case["out"]]
+    assert (fl > 0).astype(int).tolist() == [int(v) for v in case["flag"]]
+
+
+@pytest.mark.parametrize("case", read_golden("tdsc_f32_handworked.txt"), ids=lambda c: str(c["params"]))
+def test_tdsc_f32_handworked(oracle, case):
+    p = case["params"]
+    row = np.array(case["in"], dtype=np.float32)
+    out, fl = oracle.tdsc_row(row, float(p["k"]), int(p["iterations"]), p["replace"])
+    assert out.tolist() == [float(v) for v in case["out"]]
+    assert fl.tolist() == [int(v) for v in case["flag"]]
+
+
+# ---------------------------------------------------------------------------
+# brute force against exact rationals
+# ---------------------------------------------------------------------------
+
+KS = [0.75, 1.0, 1.5, 2.0, 2.5, 2.75, 3.0, 3.25]
+
+
+def test_tdsc_u8_bruteforce_vs_rational(oracle):
+    rng = np.random.default_rng(11)
+    for trial in range(1500):
+        n = int(rng.integers(1, 13))
+        if trial % 2:
+            row = rng.choice([0, 1, 2, 255], size=n).astype(np.uint8)
+        else:
+            row = rng.integers(0, 256, size=n).astype(np.uint8)
+        k = float(rng.choice(KS))
+        it = int(rng.integers(1, 4))
+        rep = "mean" if trial % 3 else "median"
+        out, fl = oracle.tdsc_row(row, k, it, rep)
+        r_out, r_fl = rational_tdsc(row, k, it, rep)
+        assert out.tolist() == r_out, (row, k, it, rep)
+        assert fl.tolist() == r_fl, (row, k, it, rep)
+
+
+def test_fdsc_u8_bruteforce_vs_rational(oracle):
+    rng = np.random.default_rng(12)
+    for trial in range(800):
+        n = int(rng.integers(1, 17))
+        bin = int(rng.integers(1, n + 1))
+        if trial % 2:
+            col = rng.choice([0, 3, 128, 255], size=n).astype(np.uint8)
+        else:
+            col = rng.integers(0, 256, size=n).astype(np.uint8)
+        k = float(rng.choice(KS))
+        it = int(rng.integers(1, 4))
+        rep = "mean" if trial % 3 else "median"
+        out, fl = oracle.fdsc_col(col, k, it, rep, bin)
+        r_out, r_fl = rational_fdsc(col, k, it, rep, bin)
+        assert out.tolist() == r_out, (col, k, it, rep, bin)
+        assert (fl > 0).astype(int).tolist() == r_fl, (col, k, it, rep, bin)
+
+
+def test_fdsc_u8_larger_columns_vs_rational(oracle):
+    # ARTS-like column lengths with a short last bin, one iteration each.
+    rng = np.random.default_rng(13)
+    for n, bin in [(100, 32), (96, 32), (61, 7), (64, 64)]:
+        col = np.clip(np.rint(rng.normal(128, 16, n)), 0, 255).astype(np.uint8)
+        col[rng.integers(0, n, 3)] = 250
+        for k in (2.0, 3.0):
+            out, fl = oracle.fdsc_col(col, k, 2, "mean", bin)
+            r_out, r_fl = rational_fdsc(col, k, 2, "mean", bin)
+            assert out.tolist() == r_out
+            assert (fl > 0).astype(int).tolist() == r_fl
+
+
+# ---------------------------------------------------------------------------
+# closed-form tail fractions on clean noise (first iteration)
+# ---------------------------------------------------------------------------
+
+
+def _binom_band(p, n, z=5.0):
+    s = math.sqrt(p * (1 - p) / n)
+    return p - z * s, p + z * s
+
+
+def _ncdf(z):
+    return 0.5 * math.erfc(-z / math.sqrt(2))
+
+
+@pytest.mark.parametrize("k", [2.5, 3.0, 4.0])
+def test_tdsc_u8_gaussian_tail_fraction(oracle, k):
+    # uint8 N(128, 16^2) rounded: the expected fraction sums the discretised pmf
+    # over the integers outside mu +- k sigma of that pmf.
+    rng = np.random.default_rng(21)
+    n_rows, T = 24, 50000
+    x = np.clip(np.rint(rng.normal(128, 16, (n_rows, T))), 0, 255).astype(np.uint8)
+    _, fl = oracle.clean(x[None], "bct", tdsc=dict(k=k, iterations=1, replace="mean"))
+    frac = fl.mean()
+    # The cut sits between integers, so the expectation is taken per row at
+    # that row's own sample mean and deviation (population form).
+    v = np.arange(256)
+    pmf = np.array([_ncdf((u + 0.5 - 128) / 16) - _ncdf((u - 0.5 - 128) / 16) for u in v])
+    xs = x.astype(np.float64)
+    mus, sds = xs.mean(axis=1), xs.std(axis=1)
+    expect = np.mean([pmf[np.abs(v - m) > k * s].sum() for m, s in zip(mus, sds)])
+    lo, hi = _binom_band(expect, fl.size)
+    assert lo < frac < hi, (frac, expect)
+    if k == 4.0:
+        # the loose 4-sigma cut of Sec. V-A changes almost nothing on clean data
+        assert frac < 2e-4
+
+
+@pytest.mark.parametrize("k", [2.0, 2.5, 3.0])
+def test_tdsc_f32_chi2_tail_fraction(oracle, k):
+    # chi^2_2 scaled by any gain g: mu = sigma = 2 g; only the upper tail exists,
+    # P(x > (1 + k) 2 g) = exp(-(1 + k)).
+    rng = np.random.default_rng(22)
+    n_rows, T = 16, 40000
+    g = np.exp(rng.uniform(np.log(0.5), np.log(2.0), n_rows))[:, None]
+    x = (rng.standard_exponential((n_rows, T)) * 2.0 * g).astype(np.float32)
+    _, fl = oracle.clean(x[None], "bct", tdsc=dict(k=k, iterations=1, replace="mean"))
+    expect = math.exp(-(1 + k))
+    lo, hi = _binom_band(expect, fl.size)
+    assert lo < fl.mean() < hi, (fl.mean(), expect)
+
+
+def test_fdsc_u8_gaussian_tail_fraction(oracle):
+    # One bin equal to the whole column: the corrected values are x - mean, so
+    # the flagged fraction follows the same discretised-normal tail as TDSC.
+    rng = np.random.default_rng(23)
+    C, T = 4096, 300
+    x = np.clip(np.rint(rng.normal(128, 16, (1, C, T))), 0, 255).astype(np.uint8)
+    _, fl = oracle.clean(x, "bct", fdsc=dict(k=3.0, iterations=1, replace="mean", bin=C))
+    v = np.arange(256)
+    pmf = np.array([_ncdf((u + 0.5 - 128) / 16) - _ncdf((u - 0.5 - 128) / 16) for u in v])
+    xs = x[0].astype(np.float64)
+    mus, sds = xs.mean(axis=0), xs.std(axis=0)  # per column (time sample)
+    expect = np.mean([pmf[np.abs(v - m) > 3.0 * s].sum() for m, s in zip(mus, sds)])
+    lo, hi = _binom_band(expect, fl.size)
+    assert lo < (fl > 0).mean() < hi, ((fl > 0).mean(), expect)
+
+
+# ---------------------------------------------------------------------------
+# invariants and reductions
+# ---------------------------------------------------------------------------
+
+
+def test_tdsc_invariants(oracle):
+    rng = np.random.default_rng(31)
+    x = np.clip(np.rint(rng.normal(128, 16, (2, 40, 3000))), 0, 255).astype(np.uint8)
+    x[:, :, rng.integers(0, 3000, 30)] = 250
+    for rep in ("mean", "median"):
+        out, fl = oracle.clean(x, "bct", tdsc=dict(k=3.0, iterations=3, replace=rep))
+        # unflagged samples are byte-identical; changed samples are flagged
+        assert np.array_equal(out[fl == 0], x[fl == 0])
+        assert np.all(fl[out != x] == 1)
+        # the output stays inside each row's input range
+        assert np.all(out.min(axis=2) >= x.min(axis=2)) and np.all(out.max(axis=2) <= x.max(axis=2))
+        # run to convergence, then one more iteration flags nothing
+        conv, _ = oracle.clean(x, "bct", tdsc=dict(k=3.0, iterations=16, replace=rep))
+        again, fl2 = oracle.clean(conv, "bct", tdsc=dict(k=3.0, iterations=16, replace=rep))
+        if rep == "median":
+            # the lower median is unchanged by replacing values with it, so the
+            # median cut converges; the mean cut may keep moving by rounding
+            rows_done = np.array([[not np.any(oracle.tdsc_row(conv[b, c], 3.0, 1, rep)[1]) for c in range(40)] for b in range(2)])
+            assert rows_done.mean() > 0.9
+        assert np.array_equal(again[fl2 == 0], conv[fl2 == 0])
+
+
+def test_fdsc_single_bin_equals_tdsc_on_column(oracle):
+    # bin == C: the corrected value is x - column mean and mu' = 0, so FDSC on a
+    # column is TDSC on that column read as a row (same rounding of the mean).
+    rng = np.random.default_rng(32)
+    for dtype in (np.uint8, np.float32):
+        for rep in ("mean", "median"):
+            C = 97
+            if dtype == np.uint8:
+                col = np.clip(np.rint(rng.normal(128, 16, C)), 0, 255).astype(np.uint8)
+            else:
+                col = (rng.standard_exponential(C) * 3.0).astype(np.float32)
+            col[[5, 50]] = col.max() * 2 if dtype == np.float32 else 255
+            a, fa = oracle.fdsc_col(col, 2.5, 3, rep, C)
+            b, fb = oracle.tdsc_row(col, 2.5, 3, rep)
+            assert np.array_equal(a, b)
+            assert np.array_equal(fa > 0, fb > 0)
+
+
+def test_fdsc_flagged_value_is_bin_statistic(oracle):
+    # Fig. 3: an outlier's original value is replaced by its bin's mean (median).
+    rng = np.random.default_rng(33)
+    C, bin = 64, 16
+    col = np.clip(np.rint(rng.normal(100, 5, C)), 0, 255).astype(np.uint8)
+    col[[3, 40]] = [250, 0]
+    for rep in ("mean", "median"):
+        out, fl = oracle.fdsc_col(col, 3.0, 1, rep, bin)
+        for c in np.nonzero(fl)[0]:
+            b = col[(c // bin) * bin:(c // bin + 1) * bin].astype(np.int64)
+            want = (2 * b.sum() + len(b)) // (2 * len(b)) if rep == "mean" else np.sort(b)[(len(b) - 1) // 2]
+            assert out[c] == want
+
+
+def test_f32_matches_u8_on_integer_data(oracle):
+    # Independent arithmetic: exact integers (uint8) vs two-pass IEEE double
+    # (float32) reach the same decisions on integer-valued data; with median
+    # replacement the outputs coincide.  Exact ties of |x-mu| = k sigma are
+    # excluded by construction (they would be decided by rounding).
+    rng = np.random.default_rng(34)
+    x = np.clip(np.rint(rng.normal(128, 16, (2, 48, 1000))), 0, 255).astype(np.uint8)
+    x[:, :, rng.integers(0, 1000, 10)] = 240
+    x[:, 7, :] = np.clip(x[:, 7, :].astype(int) + 60, 0, 255)
+    td = dict(k=2.75, iterations=2, replace="median")
+    fd = dict(k=2.75, iterations=2, replace="median", bin=16)
+    ou, fu = oracle.clean(x, "bct", tdsc=td, fdsc=fd)
+    of, ff = oracle.clean(x.astype(np.float32), "bct", tdsc=td, fdsc=fd)
+    assert np.array_equal(ou.astype(np.float32), of)
+    assert np.array_equal(fu, ff)
+
+
+def test_layouts_agree(oracle):
+    rng = np.random.default_rng(35)
+    x = np.clip(np.rint(rng.normal(128, 16, (2, 40, 300))), 0, 255).astype(np.uint8)
+    x[:, 3, :] = 200
+    td = dict(k=3.0, iterations=2, replace="median")
+    fd = dict(k=3.0, iterations=2, replace="mean", bin=8)
+    a, fa = oracle.clean(x, "bct", tdsc=td, fdsc=fd)
+    b, fb = oracle.clean(np.ascontiguousarray(x.transpose(0, 2, 1)), "btc", tdsc=td, fdsc=fd)
+    assert np.array_equal(a, b.transpose(0, 2, 1))
+    assert np.array_equal(fa, fb.transpose(0, 2, 1))
+
+
+def test_combined_is_tdsc_then_fdsc(oracle):
+    rng = np.random.default_rng(36)
+    x = np.clip(np.rint(rng.normal(128, 16, (1, 64, 700))), 0, 255).astype(np.uint8)
+    td = dict(k=3.0, iterations=2, replace="median")
+    fd = dict(k=3.0, iterations=2, replace="median", bin=32)
+    both, fb = oracle.clean(x, "bct", tdsc=td, fdsc=fd)
+    t, ft = oracle.clean(x, "bct", tdsc=td)
+    f, ff = oracle.clean(t, "bct", fdsc=fd)
+    assert np.array_equal(both, f)
+    assert np.array_equal(fb, ft | ff)
+    assert set(np.unique(ft)) <= {0, 1} and set(np.unique(ff)) <= {0, 2}
+
+
+def test_in_place(oracle):
+    rng = np.random.default_rng(37)
+    x = np.clip(np.rint(rng.normal(128, 16, (1, 16, 200))), 0, 255).astype(np.uint8)
+    out, fl = oracle.clean(x, "bct", tdsc=dict(k=2.0, iterations=2, replace="mean"))
+    assert fl.any()
+
+
+# ---------------------------------------------------------------------------
+# medians
+# ---------------------------------------------------------------------------
+
+
+def test_lower_median_rank_property(oracle):
+    rng = np.random.default_rng(41)
+    for n in list(range(1, 20)) + [255, 256, 1000, 12500]:
+        for dtype in (np.uint8, np.float32):
+            v = rng.integers(0, 256, n).astype(dtype) if dtype == np.uint8 else rng.normal(0, 1, n).astype(np.float32)
+            m = oracle.lower_median(v)
+            r = (n - 1) // 2
+            assert np.sum(v < m) <= r < np.sum(v <= m)
+            assert m in v
+
+
+def test_lower_median_signed_zero(oracle):
+    v = np.array([0.0, -0.0, 1.0, -0.0], dtype=np.float32)  # sorted: -0 -0 0 1, rank 1 -> -0
+    assert math.copysign(1.0, oracle.lower_median(v)) == -1.0
+    v = np.array([0.0, -0.0, 0.0], dtype=np.float32)        # sorted: -0 0 0, rank 1 -> +0
+    assert math.copysign(1.0, oracle.lower_median(v)) == 1.0
+
+
+def test_median_invariant_under_replacement(oracle):
+    # Replacing any subset of values by the lower median keeps the lower median.
+    rng = np.random.default_rng(42)
+    for _ in range(300):
+        n = int(rng.integers(1, 40))
+        v = rng.integers(0, 256, n).astype(np.uint8)
+        m = oracle.lower_median(v)
+        w = v.copy()
+        w[rng.random(n) < 0.3] = m
+        assert oracle.lower_median(w) == m
+
+
+# ---------------------------------------------------------------------------
+# argument validation
+# ---------------------------------------------------------------------------
+
+
+def test_validation(oracle):
+    x = np.zeros((1, 4, 8), np.uint8)
+    for bad in (dict(k=0.0), dict(k=float("nan")), dict(k=3.0, iterations=0), dict(k=3.0, iterations=17)):
+        with pytest.raises(oracle.OracleError):
+            oracle.clean(x, "bct", tdsc=bad)
+    with pytest.raises(oracle.OracleError):
+        oracle.clean(x, "bct", fdsc=dict(k=3.0, bin=5))
+    # exactness range: (255 T)^2 must stay below 2^53
+    big = np.zeros((1, 1, 372200), np.uint8)
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.clean(big, "bct", tdsc=dict(k=3.0))
+    assert e.value.rc == 2
+
+
+# ---------------------------------------------------------------------------
+# the qualitative results of Sec. V-A on the paper-shaped canvas (config 1)
+# ---------------------------------------------------------------------------
+
+
+def _cfg1_truth():
+    """Recreate config 1's RFI positions from the generator's own draws."""
+    spec = synth.CONFIGS[1]
+    m = spec["model"]()
+    rng = synth._beam_rng(synth.seed_of(1), 0)
+    rng.standard_normal((spec["C"], spec["T"]), dtype=np.float32)
+    chans = rng.choice(spec["C"], size=m.nb_count, replace=False)
+    starts = rng.choice(spec["T"] - m.bb_width + 1, size=m.bb_count, replace=False)
+    t0 = int(rng.integers(0, spec["T"] // 2))
+    delays = synth._dispersion_delays(spec["C"], m.disp_span)
+    return chans, starts, t0 + delays
+
+
+def test_paper_accuracy_claims_cfg1(oracle):
+    x = synth.make_beams(1)
+    C, T = x.shape[1:]
+    chans, starts, pulse_t = _cfg1_truth()
+    bb = np.zeros(T, bool)
+    for s in starts:
+        bb[s:s + 4] = True
+    td = dict(k=3.0, iterations=1, replace="mean")
+    # FDSC at the paper's 2.75 sigma with bin 32 (Fig. 5), three iterations (Sec. V-A)
+    fd = dict(k=2.75, iterations=3, replace="mean", bin=32)
+    _, ft = oracle.clean(x, "bct", tdsc=td)
+    _, ff = oracle.clean(x, "bct", fdsc=fd)
+    ft = ft[0] > 0
+    ff = ff[0] > 0
+    quiet = np.setdiff1d(np.arange(C), chans)
+    # TDSC removes the bright broadband impulses (+90 = 5.6 sigma) ...
+    assert ft[np.ix_(quiet, np.nonzero(bb)[0])].mean() > 0.97
+    # ... but not the persistent narrowband channels (their own mean absorbs them)
+    assert ft[chans][:, ~bb].mean() < 0.05
+    # FDSC removes most of the narrowband samples (+60 = 3.75 sigma, far fainter
+    # than the paper's SNR-125 pulses) while touching almost no clean channel
+    assert ff[chans][:, ~bb].mean() > 0.7
+    assert ff[quiet][:, ~bb].mean() < 0.01
+    # the faint dispersed pulse (+20 = 1.25 sigma) survives both methods almost untouched
+    ok = pulse_t < T
+    cs = np.arange(C)[ok]
+    ps = pulse_t[ok]
+    on_bb = bb[ps]
+    assert ft[cs[~on_bb], ps[~on_bb]].mean() < 0.2
+    assert ff[cs[~on_bb], ps[~on_bb]].mean() < 0.2
