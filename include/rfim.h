@@ -1,0 +1,250 @@
+/*
+ * rfim.h -- C ABI of the GB300 (sm_103a) RFI mitigation library, librfim.so.
+ *
+ * The library cleans radio filterbanks (beam x channel x time intensities) with
+ * the two thresholding methods of Sclocco, Vohl and van Nieuwpoort, "Real-Time
+ * RFI Mitigation for the Apertif Radio Transient System" (arXiv:2001.03389):
+ *
+ *   TDSC, time-domain sigma cut (Sec. IV, TDSC paragraph; Fig. 2): for every
+ *     (beam, channel), the mean mu and standard deviation sigma of the batch's
+ *     time samples are computed; a sample with |x - mu| > k sigma (the test is
+ *     symmetric, Fig. 2 caption) is flagged and replaced.
+ *   FDSC, frequency-domain sigma cut (Sec. IV, FDSC paragraph; Fig. 3): for
+ *     every (beam, time sample), channels are grouped into bins of `fdsc_bin`
+ *     channels; each value minus its bin mean is compared with the mean and
+ *     standard deviation of these mean-corrected values over all channels; an
+ *     outlier's original value is replaced by its bin's replacement value.
+ *   Replacement strategy (Sec. IV, last paragraph): the mean, or the median.
+ *   Iterations (Sec. V-A: three in production): the cut is re-run on its own
+ *     output, statistics recomputed from the current values.
+ *   Cleaning happens in device memory and, out of place, leaves the input
+ *     untouched (Sec. VI).
+ *
+ * Definitions the paper leaves open, as implemented (bit-exact for uint8):
+ *   - sigma is the population deviation (divide by the count);
+ *   - uint8 decisions are exact: TDSC flags iff
+ *       (double)((T x - S)^2) > fl(k2 * (double)(T Q - S^2)),  S = sum x, Q = sum x^2,
+ *     FDSC flags iff (double)(C D^2) > fl(k2 * (double)sum D^2),
+ *       D = (L / G_g)(G_g x - S_g), L = lcm of the bin sizes,
+ *     where k2 = fl(k * k) and fl() is one IEEE double rounding;
+ *   - uint8 mean replacement rounds half up, floor((2S + n) / (2n));
+ *     float32 mean replacement is (float) of the double mean;
+ *   - the median is the lower median (rank floor((n-1)/2), 0-based) of the
+ *     current values of the row (TDSC) or bin (FDSC);
+ *   - FDSC bins are contiguous channel groups [g*bin, (g+1)*bin), the last one
+ *     possibly shorter; fdsc_bin == channels is one bin (bandpass corrected);
+ *   - rfim_clean runs all TDSC iterations on every row, then all FDSC
+ *     iterations on every column of the TDSC output.
+ *
+ * Conventions for every call below:
+ *   - Pointers inside rfim_block are DEVICE pointers owned by the caller,
+ *     except for rfim_clean_host.  `out == in` cleans in place; any other
+ *     overlap of out with in is RFIM_ERR_ARG.
+ *   - Calls are asynchronous on the given CUDA stream (a cudaStream_t passed as
+ *     void*, NULL = legacy default stream) unless stated otherwise.  Errors are
+ *     returned as status codes, never thrown; rfim_last_error(ctx) holds a
+ *     message for the last failing call on that context.
+ *   - A context is not thread-safe, except for the rfim_stream_* family, whose
+ *     calls may come from any thread.
+ *   - Device memory the context needs (work queues, descriptors, staging and
+ *     streaming slots) is owned by the context and freed by rfim_destroy.
+ */
+#ifndef RFIM_H
+#define RFIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RFIM_OK = 0,
+  RFIM_ERR_ARG = 1,     /* invalid argument (null pointer, bad size, bad enum, overlap) */
+  RFIM_ERR_RANGE = 2,   /* shape outside the exact-integer range of the uint8 decisions */
+  RFIM_ERR_OOM = 3,     /* a device or pinned-host allocation failed */
+  RFIM_ERR_CUDA = 4,    /* a CUDA runtime call failed (message in rfim_last_error) */
+  RFIM_ERR_TIMEOUT = 5, /* a bounded device-side wait gave up (see rfim_device_status) */
+  RFIM_ERR_BUSY = 6,    /* streaming: result not ready, or no slot / memory to admit */
+  RFIM_ERR_STATE = 7    /* call not valid in the current context state */
+} rfim_status;
+
+typedef enum { RFIM_U8 = 0, RFIM_F32 = 1 } rfim_dtype;
+
+/* BCT: x[b][c][t], time fastest ("channel-major").  BTC: x[b][t][c], channel fastest. */
+typedef enum { RFIM_LAYOUT_BCT = 0, RFIM_LAYOUT_BTC = 1 } rfim_layout;
+
+typedef enum { RFIM_REPLACE_MEAN = 0, RFIM_REPLACE_MEDIAN = 1 } rfim_replace;
+
+/*
+ * Flag-mask output.
+ *   BITS:  one bit per sample along the fastest axis of the layout.  With
+ *          R = beams * (slow axes) rows of N samples (N = samples for BCT,
+ *          channels for BTC), sample i of row r is bit i % 32 of uint32 word
+ *          r * ceil(N / 32) + i / 32; padding bits are 0.  The bit is the OR of
+ *          both methods and all iterations.  Needs a 4-byte aligned pointer.
+ *   BYTES: one byte per sample, same layout as the data; bit 0 = flagged by
+ *          TDSC, bit 1 = flagged by FDSC (any iteration).
+ */
+typedef enum { RFIM_MASK_NONE = 0, RFIM_MASK_BITS = 1, RFIM_MASK_BYTES = 2 } rfim_mask_fmt;
+
+/* One sigma cut.  k > 0 (accepted range [1e-3, 1e6]), iterations 1..16,
+ * fdsc_bin: FDSC channels per bin, 1..channels (0 means 32, capped at channels);
+ * ignored by TDSC. */
+typedef struct {
+  double k;
+  int iterations;
+  rfim_replace replace;
+  int fdsc_bin;
+} rfim_cut;
+
+/* A block of `beams` beams of channels x samples, contiguous in the given layout. */
+typedef struct {
+  const void* in;  /* input intensities (uint8 or float32) */
+  void* out;       /* cleaned output, same shape; may equal in */
+  void* mask;      /* flag mask in mask_fmt, or NULL */
+  int beams, channels, samples;
+  rfim_dtype dtype;
+  rfim_layout layout;
+  rfim_mask_fmt mask_fmt;
+} rfim_block;
+
+typedef struct rfim_ctx rfim_ctx;
+
+/*
+ * Create a context on CUDA device `device`.
+ *   hbm_budget_bytes: device memory the streaming service may hold for its
+ *     slots (0 = no limit beyond what is free).
+ *   tune_cache: path of the autotuner's JSON cache (read if present, written
+ *     after tuning), or NULL for no persistence.
+ * Returns RFIM_ERR_ARG for a null ctx or bad device, RFIM_ERR_CUDA if the
+ * device cannot be used.
+ */
+rfim_status rfim_create(rfim_ctx** ctx, int device, size_t hbm_budget_bytes, const char* tune_cache);
+
+/* Synchronise the context's work, free everything it owns, destroy it.  NULL is a no-op. */
+rfim_status rfim_destroy(rfim_ctx* ctx);
+
+/*
+ * Set a tuning or test option (returns RFIM_ERR_ARG for an unknown key):
+ *   "spin_limit_us"   limit of every device-side wait, microseconds (default 2e6);
+ *   "schedule"        0 = auto, 1 = fused persistent (L2-resident re-read),
+ *                     2 = separate launches (TDSC pass, then FDSC pass);
+ *   "tile_samples"    FDSC slab width in time samples (0 = automatic);
+ *   "ctas_per_sm"     persistent-kernel CTAs per SM (0 = occupancy maximum);
+ *   "withhold_tdsc_done"  test hook: 1 makes the fused kernel never publish the
+ *                     TDSC completion of beam 0, so its FDSC items time out
+ *                     (RFIM_ERR_TIMEOUT via rfim_device_status).
+ */
+rfim_status rfim_set_option(rfim_ctx* ctx, const char* key, long long value);
+
+/*
+ * TDSC on every (beam, channel) row of the block (Sec. IV, Fig. 2).
+ * Writes out (all samples) and mask (TDSC flags), asynchronously on stream.
+ */
+rfim_status rfim_tdsc(rfim_ctx* ctx, const rfim_block* blk, const rfim_cut* cut, void* stream);
+
+/* FDSC on every (beam, time) column of the block (Sec. IV, Fig. 3). */
+rfim_status rfim_fdsc(rfim_ctx* ctx, const rfim_block* blk, const rfim_cut* cut, void* stream);
+
+/*
+ * TDSC (all iterations) then FDSC (all iterations) in one pass over the data:
+ * a persistent kernel whose FDSC work items re-read each beam's TDSC output
+ * while it is resident in L2.  Either cut may be NULL to skip that method.
+ */
+rfim_status rfim_clean(rfim_ctx* ctx, const rfim_block* blk, const rfim_cut* tdsc, const rfim_cut* fdsc,
+                       void* stream);
+
+/* flags for rfim_clean_batch */
+#define RFIM_BATCH_GRAPH 1u    /* capture the launch in a CUDA graph, replay it when the batch repeats */
+#define RFIM_BATCH_AUTOTUNE 2u /* time candidate tilings per shape on first use, cache the winner */
+
+/*
+ * Clean n blocks of possibly different shapes (same dtype and layout) in ONE
+ * persistent launch with a device work queue (ragged batching).  Results equal
+ * n separate rfim_clean calls bit for bit.  The descriptor table is uploaded
+ * with the launch; with RFIM_BATCH_GRAPH the upload and launch are captured
+ * once per distinct batch (same pointers and shapes) and replayed afterwards.
+ */
+rfim_status rfim_clean_batch(rfim_ctx* ctx, const rfim_block* blocks, int n, const rfim_cut* tdsc,
+                             const rfim_cut* fdsc, unsigned flags, void* stream);
+
+/*
+ * rfim_clean on HOST buffers (pinned memory recommended): the context copies
+ * beams to device staging buffers, cleans them and copies results back,
+ * overlapping the copies of one beam group with the cleaning of another on two
+ * streams.  Synchronous: returns when out and mask are written.
+ */
+rfim_status rfim_clean_host(rfim_ctx* ctx, const rfim_block* host_blk, const rfim_cut* tdsc,
+                            const rfim_cut* fdsc);
+
+/*
+ * Synchronise `stream` and return the device status word of the context's
+ * kernels since the last check: RFIM_OK, or RFIM_ERR_TIMEOUT if a device-side
+ * wait gave up (the affected output is then incomplete).  Clears the word.
+ */
+rfim_status rfim_device_status(rfim_ctx* ctx, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Streaming service (continuous batching of beam chunks).                   */
+/* Each chunk is one batch in the paper's sense (Sec. IV): its statistics come */
+/* from the chunk alone, so a chunk's result is the same alone or in a mix.  */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Open the streaming service: n_beams beams of `channels` x `chunk_samples`
+ * chunks (BCT layout per chunk), cleaned with the given cuts (either may be
+ * NULL).  Device slots are allocated up to the context's HBM budget; a
+ * dispatcher thread closes micro-batches and launches them on several CUDA
+ * streams so that batches overlap on the device.
+ */
+rfim_status rfim_stream_open(rfim_ctx* ctx, int n_beams, int channels, int chunk_samples, rfim_dtype dtype,
+                             const rfim_cut* tdsc, const rfim_cut* fdsc);
+
+/*
+ * Submit one chunk of beam `beam`.  chunk: device or host pointer (detected),
+ * copied into a device slot before the call returns.  arrival_time_s: the
+ * scheduled arrival time on the CLOCK_MONOTONIC scale (seconds), from which
+ * latency is measured.  Returns RFIM_ERR_BUSY if no slot or memory is free
+ * (the caller retries), RFIM_ERR_STATE if the service is not open.
+ */
+rfim_status rfim_stream_push(rfim_ctx* ctx, int beam, const void* chunk, double arrival_time_s,
+                             unsigned long long* ticket);
+
+/*
+ * Poll a ticket.  When cleaned, *out_dev and *mask_dev (bit mask, BCT rows)
+ * point to context-owned device memory valid until rfim_stream_release.
+ * wait_us: how long to wait for completion (0 = do not wait).  Returns
+ * RFIM_ERR_BUSY if not done in time, RFIM_ERR_ARG for an unknown ticket.
+ */
+rfim_status rfim_stream_poll(rfim_ctx* ctx, unsigned long long ticket, void** out_dev, void** mask_dev,
+                             int wait_us);
+
+/* Return the ticket's slot to the pool. */
+rfim_status rfim_stream_release(rfim_ctx* ctx, unsigned long long ticket);
+
+/*
+ * Latency percentiles (seconds, from scheduled arrival to completion seen by
+ * the service) and input GB/s since rfim_stream_open or the last reset; any
+ * pointer may be NULL.  reset != 0 clears the statistics after reading.
+ */
+rfim_status rfim_stream_stats(rfim_ctx* ctx, double* p50, double* p99, double* p999, double* gbps,
+                              unsigned long long* chunks, int reset);
+
+/* Drain outstanding work and stop the service's threads; frees its slots. */
+rfim_status rfim_stream_close(rfim_ctx* ctx);
+
+/* Static description of a status code. */
+const char* rfim_status_str(rfim_status s);
+
+/* Message of the last failing call on ctx ("" if none); valid until the next call. */
+const char* rfim_last_error(rfim_ctx* ctx);
+
+/* Library version string, e.g. "rfim-gb300 0.1 sm_103a". */
+const char* rfim_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RFIM_H */

@@ -1,0 +1,669 @@
+// api.cu -- the C ABI of librfim.so: context, validation, work-queue planning,
+// launches, CUDA-graph batching and host-buffer cleaning.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/rfim.h"
+#include "engine.h"
+#include "runtime.h"
+
+using namespace rfim;
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int COUNTER_BLOCKS = 256;
+constexpr int COUNTER_STRIDE = 2 + MAX_JOBS;  // head + per-job done counters (+ pad)
+
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<unsigned char> key;
+};
+
+}  // namespace
+
+struct rfim_ctx {
+  int device = 0;
+  int sms = 0;
+  size_t hbm_budget = 0;
+  std::string tune_cache;
+  std::string last_error;
+  unsigned* d_counters = nullptr;  // COUNTER_BLOCKS x COUNTER_STRIDE
+  unsigned* d_status = nullptr;
+  unsigned seq = 0;
+  // options
+  long long spin_limit_us = 2000000;
+  int schedule = 0;
+  int tile_samples = 0;
+  int ctas_per_sm = 0;
+  int withhold = 0;
+  int smem_target = 113 * 1024;
+  int fused_lag = 1;
+  // graphs for rfim_clean_batch (each with its own counter blocks)
+  std::map<std::vector<unsigned char>, std::pair<cudaGraphExec_t, unsigned*>> graphs;
+  unsigned* capture_counters = nullptr;  // while capturing: counter blocks of the graph
+  int capture_used = 0;
+  cudaStream_t capture_stream = nullptr;
+  // host staging (rfim_clean_host)
+  HostStager* stager = nullptr;
+  // streaming service
+  StreamService* stream = nullptr;
+  // autotuner
+  Tuner* tuner = nullptr;
+  std::mutex mu;
+};
+
+namespace {
+
+rfim_status fail(rfim_ctx* ctx, rfim_status s, const char* fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    ctx->last_error = buf;
+  }
+  return s;
+}
+
+rfim_status cuda_fail(rfim_ctx* ctx, cudaError_t e, const char* what) {
+  return fail(ctx, RFIM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+ExactK2 make_k2(double k) {
+  const double k2 = k * k;
+  int e = 0;
+  const double f = std::frexp(k2, &e);  // k2 = f * 2^e, f in [0.5, 1)
+  ExactK2 r;
+  r.M = (unsigned long long)std::ldexp(f, 53);
+  r.E = e - 53;
+  r.k2f = (float)k2;
+  return r;
+}
+
+long long gcdll(long long a, long long b) {
+  while (b) {
+    long long t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+size_t dtype_size(rfim_dtype d) { return d == RFIM_F32 ? 4 : 1; }
+
+struct CutNorm {
+  bool on = false;
+  double k = 0;
+  int it = 0;
+  int rep = 0;
+  int bin = 0;
+};
+
+rfim_status check_cut(rfim_ctx* ctx, const rfim_cut* c, int C, bool fdsc, CutNorm& out) {
+  out = CutNorm();
+  if (!c) return RFIM_OK;
+  if (!std::isfinite(c->k) || !(c->k >= 1e-3) || !(c->k <= 1e6))
+    return fail(ctx, RFIM_ERR_ARG, "k must be finite and in [1e-3, 1e6], got %g", c->k);
+  if (c->iterations < 1 || c->iterations > 16)
+    return fail(ctx, RFIM_ERR_ARG, "iterations must be in 1..16, got %d", c->iterations);
+  if (c->replace != RFIM_REPLACE_MEAN && c->replace != RFIM_REPLACE_MEDIAN)
+    return fail(ctx, RFIM_ERR_ARG, "unknown replacement strategy %d", (int)c->replace);
+  int bin = c->fdsc_bin;
+  if (fdsc) {
+    if (bin == 0) bin = std::min(32, C);
+    if (bin < 1 || bin > C) return fail(ctx, RFIM_ERR_ARG, "fdsc_bin must be in 1..channels (%d), got %d", C, bin);
+  }
+  out.on = true;
+  out.k = c->k;
+  out.it = c->iterations;
+  out.rep = (int)c->replace;
+  out.bin = bin;
+  return RFIM_OK;
+}
+
+bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const char* pa = (const char*)a;
+  const char* pb = (const char*)b;
+  return pa < pb + nb && pb < pa + na;
+}
+
+const long long LIM53 = (1LL << 53) / 65025;  // (255 n)^2 style bounds: n^2 <= LIM53
+
+rfim_status check_block(rfim_ctx* ctx, const rfim_block* b, const CutNorm& td, const CutNorm& fd) {
+  if (!b) return fail(ctx, RFIM_ERR_ARG, "null block");
+  if (!b->in || !b->out) return fail(ctx, RFIM_ERR_ARG, "null in/out pointer");
+  if (b->beams < 1 || b->channels < 1 || b->samples < 1)
+    return fail(ctx, RFIM_ERR_ARG, "beams, channels, samples must be >= 1 (%d, %d, %d)", b->beams, b->channels,
+                b->samples);
+  if (b->dtype != RFIM_U8 && b->dtype != RFIM_F32) return fail(ctx, RFIM_ERR_ARG, "unknown dtype %d", (int)b->dtype);
+  if (b->layout != RFIM_LAYOUT_BCT && b->layout != RFIM_LAYOUT_BTC)
+    return fail(ctx, RFIM_ERR_ARG, "unknown layout %d", (int)b->layout);
+  if (b->mask_fmt != RFIM_MASK_NONE && b->mask_fmt != RFIM_MASK_BITS && b->mask_fmt != RFIM_MASK_BYTES)
+    return fail(ctx, RFIM_ERR_ARG, "unknown mask format %d", (int)b->mask_fmt);
+  if (b->mask_fmt != RFIM_MASK_NONE && !b->mask) return fail(ctx, RFIM_ERR_ARG, "mask format set but mask is null");
+  if (b->mask_fmt == RFIM_MASK_BITS && ((uintptr_t)b->mask & 3))
+    return fail(ctx, RFIM_ERR_ARG, "bit mask pointer must be 4-byte aligned");
+  if (b->dtype == RFIM_F32 && (((uintptr_t)b->in & 3) || ((uintptr_t)b->out & 3)))
+    return fail(ctx, RFIM_ERR_ARG, "float32 buffers must be 4-byte aligned");
+  const size_t N = (size_t)b->beams * b->channels * b->samples;
+  const size_t bytes = N * dtype_size(b->dtype);
+  if (b->out != b->in && ranges_overlap(b->in, bytes, b->out, bytes))
+    return fail(ctx, RFIM_ERR_ARG, "out overlaps in without being equal to it");
+  if (b->mask_fmt != RFIM_MASK_NONE) {
+    const size_t slow = b->layout == RFIM_LAYOUT_BCT ? (size_t)b->beams * b->channels : (size_t)b->beams * b->samples;
+    const size_t fast = b->layout == RFIM_LAYOUT_BCT ? (size_t)b->samples : (size_t)b->channels;
+    const size_t mbytes = b->mask_fmt == RFIM_MASK_BITS ? slow * ((fast + 31) / 32) * 4 : N;
+    if (ranges_overlap(b->mask, mbytes, b->in, bytes) || ranges_overlap(b->mask, mbytes, b->out, bytes))
+      return fail(ctx, RFIM_ERR_ARG, "mask overlaps the data");
+  }
+  if (b->dtype == RFIM_U8) {
+    if (td.on && (long long)b->samples * b->samples > LIM53)
+      return fail(ctx, RFIM_ERR_RANGE, "TDSC uint8: (255*T)^2 must stay below 2^53 (T <= 372181), T = %d", b->samples);
+    if (fd.on) {
+      const int C = b->channels, G = fd.bin;
+      const int nb = (C + G - 1) / G, gl = C - (nb - 1) * G;
+      const long long L = (long long)G / gcdll(G, gl) * gl;
+      if (L > 372181 || L * L > LIM53 / C)
+        return fail(ctx, RFIM_ERR_RANGE, "FDSC uint8: C * (255 * lcm(bin sizes))^2 must stay below 2^53");
+    }
+  }
+  return RFIM_OK;
+}
+
+// Engine limits of this build.
+rfim_status check_impl(rfim_ctx* ctx, const rfim_block* b, const CutNorm& td) {
+  if (b->dtype != RFIM_U8) return fail(ctx, RFIM_ERR_ARG, "float32 blocks are not available in this build");
+  if (b->layout != RFIM_LAYOUT_BCT) return fail(ctx, RFIM_ERR_ARG, "BTC layout is not available in this build");
+  if (td.on && engine_nch_for(b->samples) < 0)
+    return fail(ctx, RFIM_ERR_ARG, "TDSC rows longer than 65506 samples are not available in this build");
+  return RFIM_OK;
+}
+
+int pick_ws(const rfim_ctx* ctx, int C, int nb, int pitch, int budget) {
+  if (ctx->tile_samples > 0) return ctx->tile_samples;
+  for (int ws : {32, 16, 8, 4})
+    if (fd_smem_bytes(ws, pitch, nb, C) <= budget) return ws;
+  return 4;
+}
+
+struct Plan {
+  std::vector<Job> jobs;
+  CutNorm td, fd;
+  int mask_kind = 0;
+  int max_T = 1;
+};
+
+void add_block_jobs(rfim_ctx* ctx, Plan& pl, const rfim_block* b) {
+  const int C = b->channels, T = b->samples;
+  const size_t es = dtype_size(b->dtype);
+  const size_t beam = (size_t)C * T;
+  const int W32 = (T + 31) / 32;
+  for (int j = 0; j < b->beams; j++) {
+    Job J;
+    memset(&J, 0, sizeof J);
+    J.in = (const char*)b->in + j * beam * es;
+    J.out = (char*)b->out + j * beam * es;
+    if (b->mask_fmt == RFIM_MASK_BITS)
+      J.mask = (unsigned*)b->mask + (size_t)j * C * W32;
+    else if (b->mask_fmt == RFIM_MASK_BYTES)
+      J.mask = (unsigned char*)b->mask + j * beam;
+    else
+      J.mask = nullptr;
+    J.src_lo = J.in;
+    J.src_hi = (const char*)J.in + beam * es;
+    J.C = C;
+    J.T = T;
+    J.rows = C;
+    const int G = pl.fd.on ? pl.fd.bin : std::min(32, C);
+    J.nb = (C + G - 1) / G;
+    J.last_g = C - (J.nb - 1) * G;
+    const long long L = (long long)G / gcdll(G, J.last_g) * J.last_g;
+    J.m_full = (unsigned long long)(L / G);
+    J.m_last = (unsigned long long)(L / J.last_g);
+    J.pitch = ((C * (int)es + 127) / 128) * 128 + 4;
+    J.ws = pick_ws(ctx, C, J.nb, J.pitch, ctx->smem_target);
+    J.fd_items = (T + FD_ITEM_T - 1) / FD_ITEM_T;
+    pl.jobs.push_back(J);
+    pl.max_T = std::max(pl.max_T, T);
+  }
+}
+
+struct OccKey {
+  void* fn;
+  int smem;
+  bool operator<(const OccKey& o) const { return fn < o.fn || (fn == o.fn && smem < o.smem); }
+};
+
+int occupancy(void* fn, int smem) {
+  static std::mutex m;
+  static std::map<OccKey, int> cache;
+  std::lock_guard<std::mutex> g(m);
+  OccKey k{fn, smem};
+  auto it = cache.find(k);
+  if (it != cache.end()) return it->second;
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448 - 1024);
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, NT, smem) != cudaSuccess) n = 1;
+  if (n < 1) n = 1;
+  cache[k] = n;
+  return n;
+}
+
+// Build the Params of one launch over jobs [j0, j1) with the given item kinds.
+// mode: 0 = TDSC only, 1 = FDSC only (reads `in`), 2 = fused TDSC->FDSC, 3 = FDSC reading `out`.
+void fill_params(rfim_ctx* ctx, const Plan& pl, int j0, int j1, int mode, Params& p, unsigned* counters) {
+  memset(&p, 0, sizeof p);
+  p.n_jobs = j1 - j0;
+  for (int j = j0; j < j1; j++) p.jobs[j - j0] = pl.jobs[j];
+  auto mk = [](const CutNorm& c) {
+    CutDev d;
+    memset(&d, 0, sizeof d);
+    if (c.on) {
+      d.k2 = make_k2(c.k);
+      d.k = c.k;
+      d.iterations = c.it;
+      d.replace = c.rep;
+      d.bin = c.bin;
+    }
+    return d;
+  };
+  p.td = mk(pl.td);
+  p.fd = mk(pl.fd);
+  if (mode == 1 || mode == 3) p.td.iterations = 0;
+  if (mode == 0) p.fd.iterations = 0;
+  p.mask_kind = pl.mask_kind;
+  p.fd_reads_out = (mode == 2 || mode == 3) ? 1 : 0;
+  p.wait_tdsc = mode == 2 ? 1 : 0;
+  p.mask_or = (mode == 2 || mode == 3) ? 1 : 0;
+  p.withhold_job = (ctx->withhold && mode == 2) ? 0 : -1;
+  p.spin_limit_ns = (unsigned long long)ctx->spin_limit_us * 1000ull;
+  p.counters = counters;
+  p.status = ctx->d_status;
+  // queue segments
+  int n = 0, s = 0;
+  auto push = [&](int job, int kind, int count) {
+    if (count <= 0) return;
+    p.segs[s].start = n;
+    p.segs[s].job = job;
+    p.segs[s].kind = kind;
+    s++;
+    n += count;
+  };
+  const int nj = p.n_jobs;
+  if (mode == 0) {
+    for (int j = 0; j < nj; j++) push(j, 0, p.jobs[j].rows);
+  } else if (mode == 1 || mode == 3) {
+    for (int j = 0; j < nj; j++) push(j, 1, p.jobs[j].fd_items);
+  } else {
+    // fused: TDSC rows of beam j+lag are queued before the FDSC items of beam j
+    const int lag = std::max(0, ctx->fused_lag);
+    for (int j = 0; j < nj + lag; j++) {
+      if (j < nj) push(j, 0, p.jobs[j].rows);
+      const int f = j - lag;
+      if (f >= 0) push(f, 1, p.jobs[f].fd_items);
+    }
+  }
+  p.n_segs = s;
+  p.n_items = n;
+}
+
+rfim_status launch_one(rfim_ctx* ctx, Params& p, int max_T, cudaStream_t st) {
+  const int nch = p.td.iterations > 0 ? engine_nch_for(max_T) : 1;
+  if (nch < 0) return fail(ctx, RFIM_ERR_ARG, "row too long");
+  LaunchCfg cfg;
+  cfg.nch = nch;
+  cfg.smem = engine_smem_u8(p, nch);
+  if (cfg.smem > 232448 - 1024) return fail(ctx, RFIM_ERR_ARG, "tile does not fit in shared memory (%d bytes)", cfg.smem);
+  void* fn = engine_kernel_u8(nch);
+  int per_sm = occupancy(fn, cfg.smem);
+  if (ctx->ctas_per_sm > 0) per_sm = std::min(per_sm, ctx->ctas_per_sm);
+  cfg.grid = std::max(1, std::min(p.n_items, ctx->sms * per_sm));
+  cudaError_t e = cudaMemsetAsync(p.counters, 0, sizeof(unsigned) * (1 + p.n_jobs), st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync");
+  e = (cudaError_t)launch_engine_u8(p, cfg, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "engine launch");
+  return RFIM_OK;
+}
+
+unsigned* next_counters(rfim_ctx* ctx) {
+  if (ctx->capture_counters) return ctx->capture_counters + (size_t)(ctx->capture_used++) * COUNTER_STRIDE;
+  const unsigned b = ctx->seq++ % COUNTER_BLOCKS;
+  return ctx->d_counters + (size_t)b * COUNTER_STRIDE;
+}
+
+// Run a plan: mode as in fill_params; fused may fall back to two launches.
+rfim_status run_plan(rfim_ctx* ctx, const Plan& pl, cudaStream_t st) {
+  const int nj = (int)pl.jobs.size();
+  static thread_local Params p;  // ~20 KB: keep off the stack
+  for (int j0 = 0; j0 < nj; j0 += MAX_JOBS) {
+    const int j1 = std::min(nj, j0 + MAX_JOBS);
+    rfim_status s;
+    if (pl.td.on && pl.fd.on) {
+      const bool fused = ctx->schedule != 2;
+      if (fused) {
+        fill_params(ctx, pl, j0, j1, 2, p, next_counters(ctx));
+        if ((s = launch_one(ctx, p, pl.max_T, st)) != RFIM_OK) return s;
+      } else {
+        fill_params(ctx, pl, j0, j1, 0, p, next_counters(ctx));
+        if ((s = launch_one(ctx, p, pl.max_T, st)) != RFIM_OK) return s;
+        fill_params(ctx, pl, j0, j1, 3, p, next_counters(ctx));
+        if ((s = launch_one(ctx, p, pl.max_T, st)) != RFIM_OK) return s;
+      }
+    } else if (pl.td.on) {
+      fill_params(ctx, pl, j0, j1, 0, p, next_counters(ctx));
+      if ((s = launch_one(ctx, p, pl.max_T, st)) != RFIM_OK) return s;
+    } else if (pl.fd.on) {
+      fill_params(ctx, pl, j0, j1, 1, p, next_counters(ctx));
+      if ((s = launch_one(ctx, p, pl.max_T, st)) != RFIM_OK) return s;
+    }
+  }
+  return RFIM_OK;
+}
+
+rfim_status make_plan(rfim_ctx* ctx, const rfim_block* blocks, int n, const rfim_cut* tdsc, const rfim_cut* fdsc,
+                      Plan& pl) {
+  if (n < 1) return fail(ctx, RFIM_ERR_ARG, "empty batch");
+  if (!blocks) return fail(ctx, RFIM_ERR_ARG, "null block array");
+  for (int i = 0; i < n; i++) {
+    const rfim_block* b = &blocks[i];
+    if (!b) return fail(ctx, RFIM_ERR_ARG, "null block");
+    CutNorm td, fd;
+    rfim_status s;
+    if ((s = check_cut(ctx, tdsc, b->channels, false, td)) != RFIM_OK) return s;
+    if ((s = check_cut(ctx, fdsc, b->channels, true, fd)) != RFIM_OK) return s;
+    if ((s = check_block(ctx, b, td, fd)) != RFIM_OK) return s;
+    if ((s = check_impl(ctx, b, td)) != RFIM_OK) return s;
+    if (i == 0) {
+      pl.td = td;
+      pl.fd = fd;
+      pl.mask_kind = (int)b->mask_fmt;
+    } else {
+      if (b->dtype != blocks[0].dtype || b->layout != blocks[0].layout)
+        return fail(ctx, RFIM_ERR_ARG, "all blocks of a batch must share dtype and layout");
+      if ((int)b->mask_fmt != pl.mask_kind) return fail(ctx, RFIM_ERR_ARG, "all blocks of a batch must share mask format");
+      if (fd.on && fd.bin != pl.fd.bin)
+        return fail(ctx, RFIM_ERR_ARG, "fdsc_bin resolves differently across blocks; pass an explicit bin");
+    }
+  }
+  for (int i = 0; i < n; i++) add_block_jobs(ctx, pl, &blocks[i]);
+  return RFIM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+rfim_status rfim_create(rfim_ctx** out, int device, size_t hbm_budget_bytes, const char* tune_cache) {
+  if (!out) return RFIM_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return RFIM_ERR_ARG;
+  rfim_ctx* ctx = new (std::nothrow) rfim_ctx();
+  if (!ctx) return RFIM_ERR_OOM;
+  ctx->device = device;
+  ctx->hbm_budget = hbm_budget_bytes;
+  if (tune_cache) ctx->tune_cache = tune_cache;
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_counters, sizeof(unsigned) * COUNTER_BLOCKS * COUNTER_STRIDE);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, sizeof(unsigned) * 4);
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_counters, 0, sizeof(unsigned) * COUNTER_BLOCKS * COUNTER_STRIDE);
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(unsigned) * 4);
+  if (e != cudaSuccess) {
+    cudaFree(ctx->d_counters);
+    cudaFree(ctx->d_status);
+    delete ctx;
+    return e == cudaErrorMemoryAllocation ? RFIM_ERR_OOM : RFIM_ERR_CUDA;
+  }
+  ctx->tuner = tuner_create(ctx->tune_cache);
+  *out = ctx;
+  return RFIM_OK;
+}
+
+rfim_status rfim_destroy(rfim_ctx* ctx) {
+  if (!ctx) return RFIM_OK;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) {
+    stream_service_destroy(ctx->stream);
+    ctx->stream = nullptr;
+  }
+  cudaDeviceSynchronize();
+  for (auto& kv : ctx->graphs) {
+    cudaGraphExecDestroy(kv.second.first);
+    cudaFree(kv.second.second);
+  }
+  if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+  if (ctx->stager) stager_destroy(ctx->stager);
+  if (ctx->tuner) tuner_destroy(ctx->tuner);
+  cudaFree(ctx->d_counters);
+  cudaFree(ctx->d_status);
+  delete ctx;
+  return RFIM_OK;
+}
+
+rfim_status rfim_set_option(rfim_ctx* ctx, const char* key, long long value) {
+  if (!ctx || !key) return RFIM_ERR_ARG;
+  const std::string k = key;
+  if (k == "spin_limit_us") {
+    if (value < 1) return fail(ctx, RFIM_ERR_ARG, "spin_limit_us must be >= 1");
+    ctx->spin_limit_us = value;
+  } else if (k == "schedule") {
+    if (value < 0 || value > 2) return fail(ctx, RFIM_ERR_ARG, "schedule must be 0, 1 or 2");
+    ctx->schedule = (int)value;
+  } else if (k == "tile_samples") {
+    if (value != 0 && value != 4 && value != 8 && value != 16 && value != 32)
+      return fail(ctx, RFIM_ERR_ARG, "tile_samples must be 0, 4, 8, 16 or 32");
+    ctx->tile_samples = (int)value;
+  } else if (k == "ctas_per_sm") {
+    if (value < 0 || value > 32) return fail(ctx, RFIM_ERR_ARG, "ctas_per_sm must be in 0..32");
+    ctx->ctas_per_sm = (int)value;
+  } else if (k == "withhold_tdsc_done") {
+    ctx->withhold = value ? 1 : 0;
+  } else if (k == "smem_target") {
+    if (value < 16384 || value > 231424) return fail(ctx, RFIM_ERR_ARG, "smem_target out of range");
+    ctx->smem_target = (int)value;
+  } else if (k == "fused_lag") {
+    if (value < 0 || value > 8) return fail(ctx, RFIM_ERR_ARG, "fused_lag must be in 0..8");
+    ctx->fused_lag = (int)value;
+  } else {
+    return fail(ctx, RFIM_ERR_ARG, "unknown option '%s'", key);
+  }
+  return RFIM_OK;
+}
+
+static rfim_status clean_common(rfim_ctx* ctx, const rfim_block* blk, const rfim_cut* tdsc, const rfim_cut* fdsc,
+                                void* stream) {
+  if (!ctx) return RFIM_ERR_ARG;
+  if (!tdsc && !fdsc) return fail(ctx, RFIM_ERR_ARG, "no cut given");
+  cudaSetDevice(ctx->device);
+  Plan pl;
+  rfim_status s = make_plan(ctx, blk, 1, tdsc, fdsc, pl);
+  if (s != RFIM_OK) return s;
+  return run_plan(ctx, pl, (cudaStream_t)stream);
+}
+
+rfim_status rfim_tdsc(rfim_ctx* ctx, const rfim_block* blk, const rfim_cut* cut, void* stream) {
+  if (ctx && !cut) return fail(ctx, RFIM_ERR_ARG, "null cut");
+  return clean_common(ctx, blk, cut, nullptr, stream);
+}
+
+rfim_status rfim_fdsc(rfim_ctx* ctx, const rfim_block* blk, const rfim_cut* cut, void* stream) {
+  if (ctx && !cut) return fail(ctx, RFIM_ERR_ARG, "null cut");
+  return clean_common(ctx, blk, nullptr, cut, stream);
+}
+
+rfim_status rfim_clean(rfim_ctx* ctx, const rfim_block* blk, const rfim_cut* tdsc, const rfim_cut* fdsc,
+                       void* stream) {
+  return clean_common(ctx, blk, tdsc, fdsc, stream);
+}
+
+rfim_status rfim_clean_batch(rfim_ctx* ctx, const rfim_block* blocks, int n, const rfim_cut* tdsc,
+                             const rfim_cut* fdsc, unsigned flags, void* stream) {
+  if (!ctx) return RFIM_ERR_ARG;
+  if (!tdsc && !fdsc) return fail(ctx, RFIM_ERR_ARG, "no cut given");
+  if (flags & ~(RFIM_BATCH_GRAPH | RFIM_BATCH_AUTOTUNE)) return fail(ctx, RFIM_ERR_ARG, "unknown batch flags");
+  cudaSetDevice(ctx->device);
+  Plan pl;
+  rfim_status s = make_plan(ctx, blocks, n, tdsc, fdsc, pl);
+  if (s != RFIM_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (flags & RFIM_BATCH_AUTOTUNE) {
+    s = tuner_apply(ctx->tuner, ctx, blocks, n, tdsc, fdsc);
+    if (s != RFIM_OK) return s;
+    pl = Plan();
+    if ((s = make_plan(ctx, blocks, n, tdsc, fdsc, pl)) != RFIM_OK) return s;
+  }
+  if (!(flags & RFIM_BATCH_GRAPH)) return run_plan(ctx, pl, st);
+  // key: the plan's jobs, cuts and the options that shape the launch
+  std::vector<unsigned char> key(sizeof(Job) * pl.jobs.size() + 256);
+  memcpy(key.data(), pl.jobs.data(), sizeof(Job) * pl.jobs.size());
+  unsigned char* kp = key.data() + sizeof(Job) * pl.jobs.size();
+  memcpy(kp, &pl.td, sizeof(CutNorm));
+  memcpy(kp + 64, &pl.fd, sizeof(CutNorm));
+  int opts[8] = {pl.mask_kind, ctx->schedule, ctx->ctas_per_sm, ctx->fused_lag, ctx->withhold, (int)ctx->spin_limit_us,
+                 ctx->tile_samples, ctx->smem_target};
+  memcpy(kp + 128, opts, sizeof opts);
+  auto it = ctx->graphs.find(key);
+  if (it == ctx->graphs.end()) {
+    if (!ctx->capture_stream) {
+      cudaError_t e = cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamCreate");
+    }
+    // A replayed graph reuses its counter blocks: give it its own, outside the ring.
+    const int launches = 2 * (((int)pl.jobs.size() + MAX_JOBS - 1) / MAX_JOBS);
+    unsigned* gc = nullptr;
+    cudaError_t e = cudaMalloc(&gc, sizeof(unsigned) * COUNTER_STRIDE * launches);
+    if (e != cudaSuccess) return fail(ctx, RFIM_ERR_OOM, "graph counters: %s", cudaGetErrorString(e));
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      cudaFree(gc);
+      return cuda_fail(ctx, e, "cudaStreamBeginCapture");
+    }
+    ctx->capture_counters = gc;
+    ctx->capture_used = 0;
+    s = run_plan(ctx, pl, ctx->capture_stream);
+    ctx->capture_counters = nullptr;
+    e = cudaStreamEndCapture(ctx->capture_stream, &g);
+    if (s != RFIM_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaFree(gc);
+      return s != RFIM_OK ? s : cuda_fail(ctx, e, "cudaStreamEndCapture");
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      cudaFree(gc);
+      return cuda_fail(ctx, e, "cudaGraphInstantiate");
+    }
+    if (ctx->graphs.size() > 64) {
+      cudaDeviceSynchronize();
+      for (auto& kv : ctx->graphs) {
+        cudaGraphExecDestroy(kv.second.first);
+        cudaFree(kv.second.second);
+      }
+      ctx->graphs.clear();
+    }
+    it = ctx->graphs.emplace(key, std::make_pair(ex, gc)).first;
+  }
+  cudaError_t e = cudaGraphLaunch(it->second.first, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
+  return RFIM_OK;
+}
+
+rfim_status rfim_clean_host(rfim_ctx* ctx, const rfim_block* host_blk, const rfim_cut* tdsc, const rfim_cut* fdsc) {
+  if (!ctx) return RFIM_ERR_ARG;
+  if (!tdsc && !fdsc) return fail(ctx, RFIM_ERR_ARG, "no cut given");
+  cudaSetDevice(ctx->device);
+  if (!ctx->stager) {
+    ctx->stager = stager_create(ctx);
+    if (!ctx->stager) return fail(ctx, RFIM_ERR_OOM, "could not create host staging");
+  }
+  return stager_run(ctx->stager, ctx, host_blk, tdsc, fdsc);
+}
+
+rfim_status rfim_device_status(rfim_ctx* ctx, void* stream) {
+  if (!ctx) return RFIM_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
+  unsigned st = 0;
+  e = cudaMemcpy(&st, ctx->d_status, sizeof st, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "status read");
+  if (st) {
+    cudaMemset(ctx->d_status, 0, sizeof(unsigned));
+    // counters of a launch that timed out are left mid-way; the ring resets them per launch
+    return fail(ctx, RFIM_ERR_TIMEOUT, "a device-side wait gave up (status %u)", st);
+  }
+  return RFIM_OK;
+}
+
+const char* rfim_status_str(rfim_status s) {
+  switch (s) {
+    case RFIM_OK: return "ok";
+    case RFIM_ERR_ARG: return "invalid argument";
+    case RFIM_ERR_RANGE: return "shape outside the exact-integer range";
+    case RFIM_ERR_OOM: return "out of memory";
+    case RFIM_ERR_CUDA: return "CUDA error";
+    case RFIM_ERR_TIMEOUT: return "device-side wait timed out";
+    case RFIM_ERR_BUSY: return "busy";
+    case RFIM_ERR_STATE: return "invalid state";
+  }
+  return "unknown status";
+}
+
+const char* rfim_last_error(rfim_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+const char* rfim_version(void) { return "rfim-gb300 0.1 sm_103a"; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// entry points used by the runtime (stream service, stager, tuner)
+// ---------------------------------------------------------------------------
+namespace rfim {
+
+rfim_status ctx_clean_async(rfim_ctx* ctx, const rfim_block* blocks, int n, const rfim_cut* tdsc,
+                            const rfim_cut* fdsc, cudaStream_t st) {
+  Plan pl;
+  rfim_status s = make_plan(ctx, blocks, n, tdsc, fdsc, pl);
+  if (s != RFIM_OK) return s;
+  return run_plan(ctx, pl, st);
+}
+
+int ctx_device(rfim_ctx* ctx) { return ctx->device; }
+size_t ctx_hbm_budget(rfim_ctx* ctx) { return ctx->hbm_budget; }
+void ctx_set_error(rfim_ctx* ctx, const char* msg) { ctx->last_error = msg; }
+StreamService*& ctx_stream_service(rfim_ctx* ctx) { return ctx->stream; }
+void ctx_get_tunables(rfim_ctx* ctx, Tunables& t) {
+  t.schedule = ctx->schedule;
+  t.ctas_per_sm = ctx->ctas_per_sm;
+  t.smem_target = ctx->smem_target;
+  t.fused_lag = ctx->fused_lag;
+}
+void ctx_set_tunables(rfim_ctx* ctx, const Tunables& t) {
+  ctx->schedule = t.schedule;
+  ctx->ctas_per_sm = t.ctas_per_sm;
+  ctx->smem_target = t.smem_target;
+  ctx->fused_lag = t.fused_lag;
+}
+
+}  // namespace rfim

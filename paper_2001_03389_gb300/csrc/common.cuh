@@ -1,0 +1,217 @@
+// common.cuh -- device helpers shared by the sigma-cut kernels (sm_103a).
+//
+// Exact uint8 decisions.  The library decides a uint8 flag as
+//     (double)lhs > fl(k2 * (double)R)
+// with lhs, R exact integers below 2^53 and k2 = fl(k*k) a double (TDSC:
+// lhs = (T x - S)^2, R = T Q - S^2; FDSC: lhs = C D^2, R = sum D^2).  On GB300
+// an FP64 warp instruction occupies the SM's FP64 pipe for ~20 cycles even
+// with one active lane, so the product is evaluated in 128-bit integers:
+// k2 = M * 2^E with an integer 53-bit M, the exact product M * R is rounded to
+// 53 significant bits (round to nearest, ties to even -- the IEEE rounding of
+// the double product) and compared with lhs scaled by 2^-E.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rfim {
+
+typedef unsigned __int128 u128;
+
+constexpr int NT = 256;  // threads per CTA in every kernel of the engine
+
+// k2 = fl(k*k) = M * 2^E exactly, M in [2^52, 2^53).  Built on the host.
+struct ExactK2 {
+  unsigned long long M;
+  int E;
+  float k2f;  // k2 rounded to float, for first guesses only
+};
+
+__device__ __forceinline__ int bitlen128(u128 x) {
+  const unsigned long long hi = (unsigned long long)(x >> 64);
+  const unsigned long long lo = (unsigned long long)x;
+  if (hi) return 128 - __clzll((long long)hi);
+  if (lo) return 64 - __clzll((long long)lo);
+  return 0;
+}
+
+// (double)lhs <= fl(k2 * (double)R), for integers lhs, R < 2^53.
+__device__ __forceinline__ bool le_thr(unsigned long long lhs, unsigned long long R, const ExactK2& k) {
+  if (R == 0) return lhs == 0;
+  u128 q = (u128)k.M * R;
+  int s = bitlen128(q) - 53;
+  if (s > 0) {
+    const u128 rem = q & (((u128)1 << s) - 1);
+    const u128 half = (u128)1 << (s - 1);
+    q >>= s;
+    if (rem > half || (rem == half && (q & 1))) q += 1;
+  } else {
+    s = 0;
+  }
+  const int e = s + k.E;  // threshold = q * 2^e
+  if (e >= 0) {
+    if (e >= 60) return true;  // q >= 1 so the threshold is >= 2^60 > lhs
+    return (u128)lhs <= (q << e);
+  }
+  const int ne = -e;
+  if (ne >= 75) return lhs == 0;  // lhs * 2^ne would exceed every q < 2^54
+  return ((u128)lhs << ne) <= q;
+}
+
+// Largest a in [0, amax] with (double)(mult * a^2) <= fl(k2 * (double)R).
+// Requires mult * amax^2 < 2^53.  a = 0 always qualifies.
+__device__ __forceinline__ unsigned max_keep(unsigned long long R, unsigned long long mult, unsigned amax,
+                                             const ExactK2& k) {
+  float est = sqrtf(k.k2f * (float)R / (float)mult);
+  long long a = (long long)est;
+  if (a > (long long)amax) a = amax;
+  if (a < 0) a = 0;
+  while (a < (long long)amax && le_thr(mult * (unsigned long long)(a + 1) * (unsigned long long)(a + 1), R, k)) a++;
+  while (a > 0 && !le_thr(mult * (unsigned long long)a * (unsigned long long)a, R, k)) a--;
+  return (unsigned)a;
+}
+
+// ---------------------------------------------------------------------------
+// SIMD-within-a-word helpers on 4 packed bytes.
+// ---------------------------------------------------------------------------
+
+// per-byte |a - b| (PTX vabsdiff4, a native instruction on sm_103a)
+__device__ __forceinline__ uint32_t absdiff4(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("vabsdiff4.u32.u32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(0u));
+  return d;
+}
+
+// acc + sum over bytes |a_i - b_i|
+__device__ __forceinline__ uint32_t sad4(uint32_t a, uint32_t b, uint32_t acc) {
+  uint32_t d;
+  asm("vabsdiff4.u32.u32.u32.add %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(acc));
+  return d;
+}
+
+__device__ __forceinline__ uint32_t dp4a_u(uint32_t a, uint32_t b, uint32_t c) {
+  return (uint32_t)__dp4a(a, b, c);  // unsigned bytes: __dp4a(unsigned, unsigned, unsigned)
+}
+
+// Keep-interval test on bytes.  A byte x is kept iff lo <= x <= hi.
+//   m = lo + floor((hi - lo) / 2), h = floor((hi - lo) / 2) (h <= 127):
+//   |x - m| > h  covers x < lo and x > hi, and also x == hi when hi - lo is odd,
+//   so the exact test additionally clears bytes equal to hi in that case.
+struct ByteKeep {
+  uint32_t m4;   // m in every byte
+  uint32_t k4;   // (127 - h) in every byte
+  uint32_t hi4;  // hi in every byte
+  uint32_t all;  // 0x80808080 when the keep interval is empty (everything flagged)
+  bool odd;      // hi - lo odd
+};
+
+__device__ __forceinline__ ByteKeep make_keep(int lo, int hi) {
+  ByteKeep k;
+  if (lo > hi) {
+    k.m4 = 0;
+    k.k4 = 0;
+    k.hi4 = 0;
+    k.all = 0x80808080u;
+    k.odd = false;
+    return k;
+  }
+  const int h = (hi - lo) >> 1;
+  k.m4 = (uint32_t)(lo + h) * 0x01010101u;
+  k.k4 = (uint32_t)(127 - h) * 0x01010101u;
+  k.hi4 = (uint32_t)hi * 0x01010101u;
+  k.all = 0;
+  k.odd = ((hi - lo) & 1) != 0;
+  return k;
+}
+
+// bit 7 of each byte set iff that byte is outside [lo, hi] (exact)
+__device__ __forceinline__ uint32_t outside_exact(uint32_t x, const ByteKeep& k) {
+  const uint32_t d = absdiff4(x, k.m4);
+  uint32_t g = ((d & 0x7F7F7F7Fu) + k.k4) | d;  // bit 7: d > h, per byte exactly
+  if (k.odd) {
+    const uint32_t e = x ^ k.hi4;
+    g &= ((e & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | e;  // bit 7: x != hi
+  }
+  return (g & 0x80808080u) | k.all;
+}
+
+// superset test: bit 7 set for every byte outside [lo, hi], possibly also for x == hi
+__device__ __forceinline__ uint32_t outside_fast(uint32_t x, const ByteKeep& k) {
+  const uint32_t d = absdiff4(x, k.m4);
+  return (((d & 0x7F7F7F7Fu) + k.k4) | d | k.all);
+}
+
+// 0x80 per byte -> 0xFF per byte
+__device__ __forceinline__ uint32_t widen80(uint32_t f) { return f | (f - (f >> 7)); }
+
+// 0x80 flags of a word -> 4 low bits (byte i -> bit i)
+__device__ __forceinline__ uint32_t bits4(uint32_t f) { return (((f >> 7) * 0x01020408u) >> 24) & 0xFu; }
+
+// 4 low bits -> 0x01 per selected byte
+__device__ __forceinline__ uint32_t bytes_from_bits4(uint32_t n) { return ((n & 0xFu) * 0x00204081u) & 0x01010101u; }
+
+// Byte-mask words of a 16-byte chunk keeping bytes with index in [lo, hi)
+__device__ __forceinline__ uint4 chunk_keep_mask(int lo, int hi) {
+  const uint32_t vb = (hi >= 16 ? 0xFFFFu : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
+  uint4 m;
+  m.x = bytes_from_bits4(vb) * 0xFFu;
+  m.y = bytes_from_bits4(vb >> 4) * 0xFFu;
+  m.z = bytes_from_bits4(vb >> 8) * 0xFFu;
+  m.w = bytes_from_bits4(vb >> 12) * 0xFFu;
+  return m;
+}
+
+// 4x4 byte transpose: rows r0..r3 (byte j of r_i is element (i, j)) -> columns.
+__device__ __forceinline__ void transpose4x4(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  const uint32_t t0 = __byte_perm(r0, r1, 0x5140);
+  const uint32_t t1 = __byte_perm(r0, r1, 0x7362);
+  const uint32_t t2 = __byte_perm(r2, r3, 0x5140);
+  const uint32_t t3 = __byte_perm(r2, r3, 0x7362);
+  r0 = __byte_perm(t0, t2, 0x5410);
+  r1 = __byte_perm(t0, t2, 0x7632);
+  r2 = __byte_perm(t1, t3, 0x5410);
+  r3 = __byte_perm(t1, t3, 0x7632);
+}
+
+// ---------------------------------------------------------------------------
+// Reductions over the CTA (NT threads).  `scratch` holds NT/32 * N words.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void block_sum(T (&v)[N], T* scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < N; i++) v[i] = warp_sum(v[i]);
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < N; i++) scratch[i * (NT / 32) + warp] = v[i];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < N; i++) {
+    T s = 0;
+#pragma unroll
+    for (int w = 0; w < NT / 32; w++) s += scratch[i * (NT / 32) + w];
+    v[i] = s;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+}  // namespace rfim

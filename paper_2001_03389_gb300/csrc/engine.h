@@ -1,0 +1,86 @@
+// engine.h -- launch parameters shared by the host runtime and the kernels.
+#pragma once
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace rfim {
+
+constexpr int MAX_JOBS = 160;      // beams per launch (kernel parameters stay below 32 KB)
+constexpr int MAX_SEGS = 2 * MAX_JOBS;
+constexpr int FD_ITEM_T = 32;      // time samples per FDSC work item (one mask word column)
+
+enum ReplaceKind { REP_MEAN = 0, REP_MEDIAN = 1 };
+enum MaskKind { MASK_NONE = 0, MASK_BITS = 1, MASK_BYTES = 2 };
+
+// One sigma cut as the kernels see it.
+struct CutDev {
+  ExactK2 k2;      // uint8: exact form of fl(k*k)
+  double k;        // float32 path
+  int iterations;  // 0 = method disabled
+  int replace;     // ReplaceKind
+  int bin;         // FDSC channels per bin
+};
+
+// One beam: C x T samples, BCT (time fastest) or BTC (channel fastest).
+struct Job {
+  const void* in;   // beam base of the input
+  void* out;        // beam base of the output
+  void* mask;       // beam base of the mask (uint32 words for bits, bytes for bytes) or null
+  const void* src_lo;  // bounds of the input buffer (for guarded vector loads)
+  const void* src_hi;
+  int C, T;
+  // FDSC geometry
+  int nb;           // number of bins
+  int last_g;       // size of the last bin
+  unsigned long long m_full, m_last;  // L / G and L / G_last
+  int ws;           // sub-slab width (time samples) of the FDSC tile
+  int pitch;        // bytes per tile row (>= C * esize, pitch/4 = 1 mod 32)
+  int fd_items;     // number of FDSC work items (ceil(T / 32))
+  int rows;         // TDSC rows (C)
+};
+
+// A run of consecutive queue items: `count` items of one kind for one job.
+struct Seg {
+  int start;  // first queue index of the run
+  int job;
+  int kind;   // 0 = TDSC rows, 1 = FDSC items
+};
+
+struct Params {
+  Job jobs[MAX_JOBS];
+  Seg segs[MAX_SEGS];
+  int n_jobs, n_segs, n_items;
+  CutDev td, fd;
+  int mask_kind;
+  int fd_reads_out;     // FDSC items read the output buffer (TDSC ran before)
+  int wait_tdsc;        // FDSC items wait for their beam's TDSC rows
+  int mask_or;          // FDSC ORs its bits into the mask (TDSC wrote it before)
+  int withhold_job;     // test hook: job index whose TDSC completion is never published (-1 = none)
+  unsigned long long spin_limit_ns;
+  unsigned* counters;   // [0] queue head, [1 + j] TDSC rows done for job j
+  unsigned* status;     // device status word (0 = ok, 5 = timeout)
+};
+
+__host__ __device__ inline int align16i(int x) { return (x + 15) & ~15; }
+
+// Shared memory of one FDSC tile (uint8): ws x pitch tile, per-(t, bin) sums and
+// cached medians, per-column sums of D^2 and keep half-widths, item flag bits,
+// list of flagged (t, bin) pairs.
+__host__ __device__ inline int fd_smem_bytes(int ws, int pitch, int nb, int C) {
+  return ws * pitch + align16i(ws * nb * 4) + align16i(ws * nb * 2) + align16i(ws * 8) + align16i(ws * 8) +
+         align16i(C * 4) + align16i(ws * nb * 4) + 16;
+}
+
+// Launchers (engine_u8.cu).
+struct LaunchCfg {
+  int grid;
+  int smem;
+  int nch;  // TDSC chunks of 16 bytes per thread (register-resident rows)
+};
+int engine_smem_u8(const Params& p, int nch);
+int engine_nch_for(int max_T_bytes);
+void* engine_kernel_u8(int nch);
+int launch_engine_u8(const Params& p, const LaunchCfg& cfg, void* stream);
+
+}  // namespace rfim

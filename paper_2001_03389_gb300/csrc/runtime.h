@@ -1,0 +1,49 @@
+// runtime.h -- host runtime pieces around the kernels: host-buffer staging,
+// autotuner and the streaming (continuous-batching) service.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/rfim.h"
+
+namespace rfim {
+
+struct HostStager;
+struct StreamService;
+struct Tuner;
+
+// Options of the context that the tuner chooses.
+struct Tunables {
+  int schedule;     // 0 auto, 1 fused, 2 separate launches
+  int ctas_per_sm;  // 0 = occupancy maximum
+  int smem_target;  // bytes of shared memory an FDSC tile may use
+  int fused_lag;    // beams of TDSC queued ahead of a beam's FDSC items
+};
+
+// context accessors (api.cu)
+rfim_status ctx_clean_async(rfim_ctx* ctx, const rfim_block* blocks, int n, const rfim_cut* tdsc,
+                            const rfim_cut* fdsc, cudaStream_t st);
+int ctx_device(rfim_ctx* ctx);
+size_t ctx_hbm_budget(rfim_ctx* ctx);
+void ctx_set_error(rfim_ctx* ctx, const char* msg);
+StreamService*& ctx_stream_service(rfim_ctx* ctx);
+void ctx_get_tunables(rfim_ctx* ctx, Tunables& t);
+void ctx_set_tunables(rfim_ctx* ctx, const Tunables& t);
+
+// host staging (runtime.cu)
+HostStager* stager_create(rfim_ctx* ctx);
+void stager_destroy(HostStager* s);
+rfim_status stager_run(HostStager* s, rfim_ctx* ctx, const rfim_block* host_blk, const rfim_cut* tdsc,
+                       const rfim_cut* fdsc);
+
+// autotuner (runtime.cu)
+Tuner* tuner_create(const std::string& cache_path);
+void tuner_destroy(Tuner* t);
+rfim_status tuner_apply(Tuner* t, rfim_ctx* ctx, const rfim_block* blocks, int n, const rfim_cut* tdsc,
+                        const rfim_cut* fdsc);
+
+// streaming service (stream.cu)
+void stream_service_destroy(StreamService* s);
+
+}  // namespace rfim

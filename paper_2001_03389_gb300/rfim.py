@@ -1,0 +1,196 @@
+"""Thin Python binding of librfim.so (ctypes).
+
+Functions carry the C ABI's names and only marshal arguments; every step of
+the cleaning runs in the library's CUDA kernels.  PyTorch is used for device
+memory and streams only.  Importing this module loads the in-tree
+librfim.so and raises ImportError if it is missing (build it with
+`python -m paper_2001_03389_gb300.build`): there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librfim.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "rfim.h")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2001_03389_gb300.build`")
+_lib = ctypes.CDLL(LIB_PATH)
+
+# ---- enums (include/rfim.h)
+OK, ERR_ARG, ERR_RANGE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BUSY, ERR_STATE = range(8)
+U8, F32 = 0, 1
+LAYOUT_BCT, LAYOUT_BTC = 0, 1
+REPLACE_MEAN, REPLACE_MEDIAN = 0, 1
+MASK_NONE, MASK_BITS, MASK_BYTES = 0, 1, 2
+BATCH_GRAPH, BATCH_AUTOTUNE = 1, 2
+
+_LAYOUTS = {"bct": LAYOUT_BCT, "btc": LAYOUT_BTC}
+_REPLACE = {"mean": REPLACE_MEAN, "median": REPLACE_MEDIAN}
+_MASKS = {None: MASK_NONE, "none": MASK_NONE, "bits": MASK_BITS, "bytes": MASK_BYTES}
+
+
+class rfim_cut(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_double), ("iterations", ctypes.c_int), ("replace", ctypes.c_int),
+                ("fdsc_bin", ctypes.c_int)]
+
+
+class rfim_block(ctypes.Structure):
+    _fields_ = [("in_", ctypes.c_void_p), ("out", ctypes.c_void_p), ("mask", ctypes.c_void_p),
+                ("beams", ctypes.c_int), ("channels", ctypes.c_int), ("samples", ctypes.c_int),
+                ("dtype", ctypes.c_int), ("layout", ctypes.c_int), ("mask_fmt", ctypes.c_int)]
+
+
+_vp = ctypes.c_void_p
+_cutp = ctypes.POINTER(rfim_cut)
+_blkp = ctypes.POINTER(rfim_block)
+_SIGS = {
+    "rfim_create": ([ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_size_t, ctypes.c_char_p], ctypes.c_int),
+    "rfim_destroy": ([_vp], ctypes.c_int),
+    "rfim_set_option": ([_vp, ctypes.c_char_p, ctypes.c_longlong], ctypes.c_int),
+    "rfim_tdsc": ([_vp, _blkp, _cutp, _vp], ctypes.c_int),
+    "rfim_fdsc": ([_vp, _blkp, _cutp, _vp], ctypes.c_int),
+    "rfim_clean": ([_vp, _blkp, _cutp, _cutp, _vp], ctypes.c_int),
+    "rfim_clean_batch": ([_vp, _blkp, ctypes.c_int, _cutp, _cutp, ctypes.c_uint, _vp], ctypes.c_int),
+    "rfim_clean_host": ([_vp, _blkp, _cutp, _cutp], ctypes.c_int),
+    "rfim_device_status": ([_vp, _vp], ctypes.c_int),
+    "rfim_stream_open": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _cutp, _cutp], ctypes.c_int),
+    "rfim_stream_push": ([_vp, ctypes.c_int, _vp, ctypes.c_double, ctypes.POINTER(ctypes.c_ulonglong)], ctypes.c_int),
+    "rfim_stream_poll": ([_vp, ctypes.c_ulonglong, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int], ctypes.c_int),
+    "rfim_stream_release": ([_vp, ctypes.c_ulonglong], ctypes.c_int),
+    "rfim_stream_stats": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int], ctypes.c_int),
+    "rfim_stream_close": ([_vp], ctypes.c_int),
+    "rfim_status_str": ([ctypes.c_int], ctypes.c_char_p),
+    "rfim_last_error": ([_vp], ctypes.c_char_p),
+    "rfim_version": ([], ctypes.c_char_p),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = _res
+    globals()[_name] = _fn
+
+
+def header_functions():
+    """Names of the functions declared in include/rfim.h."""
+    with open(HEADER) as fh:
+        text = fh.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rfim_[a-z_0-9]+)\s*\(", text)))
+
+
+class RfimError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{rfim_status_str(status).decode()}: {msg}")
+        self.status = status
+
+
+def make_cut(k, iterations=1, replace="mean", bin=0):
+    return rfim_cut(float(k), int(iterations), _REPLACE[replace] if isinstance(replace, str) else int(replace), int(bin))
+
+
+def _cut_arg(c):
+    if c is None:
+        return None
+    if isinstance(c, dict):
+        c = make_cut(c["k"], c.get("iterations", 1), c.get("replace", "mean"), c.get("bin", 0))
+    return ctypes.byref(c)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Context:
+    """An rfim_ctx on one device; methods take torch tensors (device memory)."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 0, tune_cache: str | None = None):
+        h = _vp()
+        st = rfim_create(ctypes.byref(h), int(device), int(hbm_budget),
+                         tune_cache.encode() if tune_cache else None)
+        if st != OK:
+            raise RfimError(st, f"rfim_create(device={device})")
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "h", None):
+            rfim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != OK:
+            raise RfimError(st, f"{what}: {rfim_last_error(self.h).decode()}")
+
+    def set_option(self, key: str, value: int):
+        self._check(rfim_set_option(self.h, key.encode(), int(value)), f"set_option({key})")
+
+    @staticmethod
+    def block(x, out=None, mask=None, layout="bct", mask_fmt=None):
+        """rfim_block for a 3-D tensor x shaped (B, C, T) ('bct') or (B, T, C) ('btc')."""
+        import torch
+
+        if x.dim() != 3:
+            raise ValueError("expected a (beams, channels, samples) tensor")
+        if x.dtype == torch.uint8:
+            dt = U8
+        elif x.dtype == torch.float32:
+            dt = F32
+        else:
+            raise TypeError(f"unsupported dtype {x.dtype}")
+        B = x.shape[0]
+        C, T = (x.shape[1], x.shape[2]) if layout == "bct" else (x.shape[2], x.shape[1])
+        mf = _MASKS[mask_fmt] if mask is not None else MASK_NONE
+        return rfim_block(_ptr(x), _ptr(out if out is not None else x), _ptr(mask), B, C, T, dt, _LAYOUTS[layout], mf)
+
+    def tdsc(self, blk, cut, stream=None):
+        self._check(rfim_tdsc(self.h, ctypes.byref(blk), _cut_arg(cut), _stream_ptr(stream)), "rfim_tdsc")
+
+    def fdsc(self, blk, cut, stream=None):
+        self._check(rfim_fdsc(self.h, ctypes.byref(blk), _cut_arg(cut), _stream_ptr(stream)), "rfim_fdsc")
+
+    def clean(self, blk, tdsc=None, fdsc=None, stream=None):
+        self._check(rfim_clean(self.h, ctypes.byref(blk), _cut_arg(tdsc), _cut_arg(fdsc), _stream_ptr(stream)),
+                    "rfim_clean")
+
+    def clean_batch(self, blocks, tdsc=None, fdsc=None, flags=0, stream=None):
+        arr = (rfim_block * len(blocks))(*blocks)
+        self._check(rfim_clean_batch(self.h, arr, len(blocks), _cut_arg(tdsc), _cut_arg(fdsc), int(flags),
+                                     _stream_ptr(stream)), "rfim_clean_batch")
+
+    def clean_host(self, blk, tdsc=None, fdsc=None):
+        self._check(rfim_clean_host(self.h, ctypes.byref(blk), _cut_arg(tdsc), _cut_arg(fdsc)), "rfim_clean_host")
+
+    def device_status(self, stream=None):
+        return rfim_device_status(self.h, _stream_ptr(stream))
+
+    def last_error(self) -> str:
+        return rfim_last_error(self.h).decode()
+
+
+def mask_words(C: int, T: int, B: int = 1) -> int:
+    """uint32 words of a BCT bit mask."""
+    return B * C * ((T + 31) // 32)
