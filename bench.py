@@ -1,0 +1,382 @@
+"""Benchmark: cleaned-filterbank throughput of the fused TDSC+FDSC path on GB300.
+
+Workload (one step): the ARTS-shaped batch of 12 beams x 1536 channels x 12500
+time samples, uint8, BCT layout; TDSC then FDSC, k = 3, 2 iterations each,
+median replacement, bit-mask output (Sec. IV and V of arXiv:2001.03389 give the
+method; beams, channels and the sampling come from its ARTS description).
+Inputs are synthetic (seeded noise + RFI, see paper_2001_03389_gb300/synth.py).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints ONE JSON line on rank 0.  `value` = input bytes cleaned per second over
+all ranks (each rank cleans its own batch: weak scaling, no collective on the
+data path).  `roofline` compares the engine kernel's algorithmic bytes
+(1 read + 1 write + 1/8 mask byte per sample) per launch with the measured
+HBM copy peak.  `e2e` measures the same metric through rfim_clean_host with
+pinned host buffers (copies inside the timed region).  `cpu_baseline` times
+the CPU oracle (test infrastructure) on one beam on the host cores.
+`--impl reference` times that oracle alone, as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CFG = 2
+METRIC = "cleaned filterbank GB/s (TDSC+FDSC) & % HBM peak; p99 chunk latency"
+UNIT = "GB/s"
+ALG_BYTES_PER_SAMPLE = 1 + 1 + 1 / 8  # uint8 read + write + 1-bit mask
+NOMINAL_HBM_GBS = 8000.0
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_config():
+    from paper_2001_03389_gb300 import synth
+
+    spec = synth.CONFIGS[CFG]
+    return spec
+
+
+def config_json(spec, n):
+    return {
+        "workload": f"arts_{spec['B']}x{spec['C']}x{spec['T']}_u8_bct_tdsc_then_fdsc",
+        "beams": spec["B"], "channels": spec["C"], "samples": spec["T"], "dtype": "u8", "layout": "BCT",
+        "tdsc": spec["tdsc"], "fdsc": spec["fdsc"], "mask": "bits",
+        "global_batch": spec["B"] * n, "parallelism": f"replicas{n}" if n > 1 else "single",
+        "l2": "inputs larger than L2 (230.4 MB read + 230.4 MB written per step vs 135.5 MB L2)",
+    }
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        for r in rows:
+            for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                                 r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_time_sample(x_beam, spec, T_sample):
+    """Run the CPU oracle on one beam restricted to T_sample time samples."""
+    from oracle import oracle
+
+    xs = x_beam[:, :, :T_sample].copy()
+    t0 = time.perf_counter()
+    oracle.clean(xs, "bct", tdsc=spec["tdsc"], fdsc=spec["fdsc"])
+    return time.perf_counter() - t0, xs.nbytes
+
+
+def cpu_baseline(spec, budget_s=15.0):
+    from paper_2001_03389_gb300 import synth
+
+    x = synth.make_beams(CFG, beams=[0])
+    t_small, b_small = oracle_time_sample(x, spec, 256)
+    rate = b_small / t_small
+    T_s = int(min(spec["T"], max(256, rate * budget_s / spec["C"])))
+    dt, nbytes = oracle_time_sample(x, spec, T_s)
+    return {"value": nbytes / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 beam x {spec['C']} channels x {T_s} of {spec['T']} samples, full TDSC+FDSC, "
+                      f"single-threaded C oracle, {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    spec = workload_config()
+    from paper_2001_03389_gb300 import synth
+
+    x = synth.make_beams(CFG, beams=[0])
+    K, W = args.steps, args.warmup
+    # size each step so the whole run stays within about two minutes
+    t_small, b_small = oracle_time_sample(x, spec, 128)
+    rate = b_small / t_small
+    per_step_s = max(0.05, min(5.0, 120.0 / max(1, K + W)))
+    T_s = int(min(spec["T"], max(64, rate * per_step_s / spec["C"])))
+    for _ in range(W):
+        oracle_time_sample(x, spec, T_s)
+    tot_t, tot_b = 0.0, 0
+    for _ in range(K):
+        dt, nb = oracle_time_sample(x, spec, T_s)
+        tot_t += dt
+        tot_b += nb
+    v = tot_b / tot_t / 1e9
+    out = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+           "ms_per_step": tot_t / K * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "u8", "data": "synthetic", "impl": "reference",
+           "config": config_json(spec, 1),
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"per step: 1 beam x {spec['C']} channels x {T_s} samples, full TDSC+FDSC"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    from paper_2001_03389_gb300 import build
+
+    if rank == 0 or ws == 1:
+        build.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    from paper_2001_03389_gb300 import rfim, synth
+
+    spec = workload_config()
+    B, C, T = spec["B"], spec["C"], spec["T"]
+    x = synth.make_beams(CFG)
+    nbytes = x.nbytes
+    xin = torch.from_numpy(x).to(dev)
+    out = torch.empty_like(xin)
+    mask = torch.zeros(rfim.mask_words(C, T, B), dtype=torch.int32, device=dev)
+    ctx = rfim.Context(local)
+    td, fd = rfim.make_cut(**spec["tdsc"]), rfim.make_cut(**spec["fdsc"])
+    blk = ctx.block(xin, out, mask, "bct", "bits")
+    stream = torch.cuda.Stream(device=dev)
+
+    def step():
+        ctx.clean(blk, td, fd, stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            step()
+    stream.synchronize()
+    if args.profile:
+        # profiling mode: W warm-up steps above, K plain steps, nothing else
+        for _ in range(args.steps):
+            step()
+        stream.synchronize()
+        print(json.dumps({"profile_run": True, "steps": args.steps, "status": ctx.device_status(stream),
+                          "source_hash": source_hash()}), flush=True)
+        ctx.close()
+        return
+    st = ctx.device_status(stream)
+    if st != rfim.OK:
+        raise RuntimeError(f"device status {st}: {ctx.last_error()}")
+
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    clocks = Clocks(local)
+    if rank == 0:
+        clocks.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(K):
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    t_end.record(stream)
+    t_end.synchronize()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop() if rank == 0 else None
+    total_ms = t_start.elapsed_time(t_end)
+    per_launch = [a.elapsed_time(b) for a, b in ev]
+    avg_launch_ms = sum(per_launch) / len(per_launch)
+    st = ctx.device_status(stream)
+    if st != rfim.OK:
+        raise RuntimeError(f"device status {st}: {ctx.last_error()}")
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = nbytes * K * ws / (total_ms * 1e-3) / 1e9
+
+    # e2e through the host-buffer API: pinned in/out/mask, copies inside the timed region
+    hin = torch.from_numpy(x).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    hmask = torch.empty(rfim.mask_words(C, T, B), dtype=torch.int32).pin_memory()
+    hblk = rfim.rfim_block(hin.data_ptr(), hout.data_ptr(), hmask.data_ptr(), B, C, T, rfim.U8, rfim.LAYOUT_BCT,
+                           rfim.MASK_BITS)
+    for _ in range(2):
+        ctx.clean_host(hblk, td, fd)
+    Ke = max(3, min(K, 30))
+    if ws > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(Ke):
+        ctx.clean_host(hblk, td, fd)
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": nbytes * Ke * ws / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes + hmask.numel() * 4, "api": "rfim_clean_host",
+           "steps": Ke}
+    ok = bool(np.array_equal(hout.numpy(), out.cpu().numpy()))
+
+    if rank == 0:
+        peak, peak_kind = peaks()
+        alg = ALG_BYTES_PER_SAMPLE * B * C * T
+        achieved = alg / (avg_launch_ms * 1e-3) / 1e9
+        traffic = profiled_traffic()
+        res = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
+            "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u8", "data": "synthetic", "config": config_json(spec, ws),
+            "samples_per_s": B * C * T * K * ws / (total_ms * 1e-3),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_kind": f"{peak_kind} copy (MEASURED_PEAKS.json hbm_gbs)",
+                         "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS,
+                         "kernel": "k_engine_u8<4> (fused TDSC->FDSC persistent work queue)",
+                         "alg_bytes_per_launch": alg, "avg_launch_ms": avg_launch_ms},
+            "e2e": e2e, "e2e_matches_device": ok,
+            "gpu_launches": K,
+        }
+        if clk:
+            res["clocks"] = clk
+        if not args.no_cpu_baseline and ws == 1:
+            res["cpu_baseline"] = cpu_baseline(spec)
+        print(json.dumps(res), flush=True)
+    ctx.close()
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the engine kernel from the committed ncu summary,
+    or None when the kernel sources changed since that capture."""
+    prof = os.path.join(ROOT, "profiles", "engine_u8_arts12.md")
+    if not os.path.exists(prof):
+        return None
+    vals = {}
+    with open(prof) as fh:
+        for line in fh:
+            if line.startswith("traffic:"):
+                for kv in line.split()[1:]:
+                    if "=" in kv:
+                        k, v = kv.split("=", 1)
+                        vals[k] = v
+    if vals.get("source_hash") != source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def source_hash():
+    import hashlib
+
+    h = hashlib.sha256()
+    cs = os.path.join(ROOT, "paper_2001_03389_gb300", "csrc")
+    for f in sorted(os.listdir(cs)):
+        with open(os.path.join(cs, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="warm-up and plain steps only (for ncu captures)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

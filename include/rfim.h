@@ -131,7 +131,9 @@ rfim_status rfim_destroy(rfim_ctx* ctx);
  *   "spin_limit_us"   limit of every device-side wait, microseconds (default 2e6);
  *   "schedule"        0 = auto, 1 = fused persistent (L2-resident re-read),
  *                     2 = separate launches (TDSC pass, then FDSC pass);
- *   "tile_samples"    FDSC slab width in time samples (0 = automatic);
+ *   "tile_samples"    FDSC tile width in time samples: 0 (automatic), 8, 16 or 32;
+ *   "smem_target"     shared memory an FDSC tile may use, bytes (sets the automatic width);
+ *   "fused_lag"       beams of TDSC rows queued ahead of a beam's FDSC items (0..8);
  *   "ctas_per_sm"     persistent-kernel CTAs per SM (0 = occupancy maximum);
  *   "withhold_tdsc_done"  test hook: 1 makes the fused kernel never publish the
  *                     TDSC completion of beam 0, so its FDSC items time out

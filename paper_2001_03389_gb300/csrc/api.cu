@@ -188,16 +188,16 @@ rfim_status check_block(rfim_ctx* ctx, const rfim_block* b, const CutNorm& td, c
 rfim_status check_impl(rfim_ctx* ctx, const rfim_block* b, const CutNorm& td) {
   if (b->dtype != RFIM_U8) return fail(ctx, RFIM_ERR_ARG, "float32 blocks are not available in this build");
   if (b->layout != RFIM_LAYOUT_BCT) return fail(ctx, RFIM_ERR_ARG, "BTC layout is not available in this build");
-  if (td.on && engine_nch_for(b->samples) < 0)
-    return fail(ctx, RFIM_ERR_ARG, "TDSC rows longer than 65506 samples are not available in this build");
+  if (td.on && td_row_mode(b->samples) < 0)
+    return fail(ctx, RFIM_ERR_ARG, "TDSC rows longer than 98274 samples are not available in this build");
   return RFIM_OK;
 }
 
 int pick_ws(const rfim_ctx* ctx, int C, int nb, int pitch, int budget) {
   if (ctx->tile_samples > 0) return ctx->tile_samples;
-  for (int ws : {32, 16, 8, 4})
+  for (int ws : {32, 16, 8})
     if (fd_smem_bytes(ws, pitch, nb, C) <= budget) return ws;
-  return 4;
+  return 8;
 }
 
 struct Plan {
@@ -234,9 +234,11 @@ void add_block_jobs(rfim_ctx* ctx, Plan& pl, const rfim_block* b) {
     const long long L = (long long)G / gcdll(G, J.last_g) * J.last_g;
     J.m_full = (unsigned long long)(L / G);
     J.m_last = (unsigned long long)(L / J.last_g);
-    J.pitch = ((C * (int)es + 127) / 128) * 128 + 4;
+    J.pitch = fd_pitch(C * (int)es);
     J.ws = pick_ws(ctx, C, J.nb, J.pitch, ctx->smem_target);
     J.fd_items = (T + FD_ITEM_T - 1) / FD_ITEM_T;
+    J.td_mode = td_row_mode(T) == 1 ? 1 : 0;
+    J.td_items = J.td_mode == 0 ? (C + TD_ROWS_PER_ITEM - 1) / TD_ROWS_PER_ITEM : C;
     pl.jobs.push_back(J);
     pl.max_T = std::max(pl.max_T, T);
   }
@@ -305,14 +307,14 @@ void fill_params(rfim_ctx* ctx, const Plan& pl, int j0, int j1, int mode, Params
   };
   const int nj = p.n_jobs;
   if (mode == 0) {
-    for (int j = 0; j < nj; j++) push(j, 0, p.jobs[j].rows);
+    for (int j = 0; j < nj; j++) push(j, 0, p.jobs[j].td_items);
   } else if (mode == 1 || mode == 3) {
     for (int j = 0; j < nj; j++) push(j, 1, p.jobs[j].fd_items);
   } else {
     // fused: TDSC rows of beam j+lag are queued before the FDSC items of beam j
     const int lag = std::max(0, ctx->fused_lag);
     for (int j = 0; j < nj + lag; j++) {
-      if (j < nj) push(j, 0, p.jobs[j].rows);
+      if (j < nj) push(j, 0, p.jobs[j].td_items);
       const int f = j - lag;
       if (f >= 0) push(f, 1, p.jobs[f].fd_items);
     }
@@ -322,13 +324,11 @@ void fill_params(rfim_ctx* ctx, const Plan& pl, int j0, int j1, int mode, Params
 }
 
 rfim_status launch_one(rfim_ctx* ctx, Params& p, int max_T, cudaStream_t st) {
-  const int nch = p.td.iterations > 0 ? engine_nch_for(max_T) : 1;
-  if (nch < 0) return fail(ctx, RFIM_ERR_ARG, "row too long");
+  (void)max_T;
   LaunchCfg cfg;
-  cfg.nch = nch;
-  cfg.smem = engine_smem_u8(p, nch);
-  if (cfg.smem > 232448 - 1024) return fail(ctx, RFIM_ERR_ARG, "tile does not fit in shared memory (%d bytes)", cfg.smem);
-  void* fn = engine_kernel_u8(nch);
+  cfg.smem = engine_smem_u8(p);
+  if (cfg.smem > 232448 - 2048) return fail(ctx, RFIM_ERR_ARG, "tile does not fit in shared memory (%d bytes)", cfg.smem);
+  void* fn = engine_kernel_u8();
   int per_sm = occupancy(fn, cfg.smem);
   if (ctx->ctas_per_sm > 0) per_sm = std::min(per_sm, ctx->ctas_per_sm);
   cfg.grid = std::max(1, std::min(p.n_items, ctx->sms * per_sm));
@@ -468,8 +468,8 @@ rfim_status rfim_set_option(rfim_ctx* ctx, const char* key, long long value) {
     if (value < 0 || value > 2) return fail(ctx, RFIM_ERR_ARG, "schedule must be 0, 1 or 2");
     ctx->schedule = (int)value;
   } else if (k == "tile_samples") {
-    if (value != 0 && value != 4 && value != 8 && value != 16 && value != 32)
-      return fail(ctx, RFIM_ERR_ARG, "tile_samples must be 0, 4, 8, 16 or 32");
+    if (value != 0 && value != 8 && value != 16 && value != 32)
+      return fail(ctx, RFIM_ERR_ARG, "tile_samples must be 0, 8, 16 or 32");
     ctx->tile_samples = (int)value;
   } else if (k == "ctas_per_sm") {
     if (value < 0 || value > 32) return fail(ctx, RFIM_ERR_ARG, "ctas_per_sm must be in 0..32");

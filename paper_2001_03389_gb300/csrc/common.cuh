@@ -104,6 +104,9 @@ struct ByteKeep {
   bool odd;      // hi - lo odd
 };
 
+// byte 0 of v replicated into all four bytes
+__device__ __forceinline__ uint32_t splat4(uint32_t v) { return __byte_perm(v, 0u, 0u); }
+
 __device__ __forceinline__ ByteKeep make_keep(int lo, int hi) {
   ByteKeep k;
   if (lo > hi) {
@@ -115,12 +118,21 @@ __device__ __forceinline__ ByteKeep make_keep(int lo, int hi) {
     return k;
   }
   const int h = (hi - lo) >> 1;
-  k.m4 = (uint32_t)(lo + h) * 0x01010101u;
-  k.k4 = (uint32_t)(127 - h) * 0x01010101u;
-  k.hi4 = (uint32_t)hi * 0x01010101u;
+  k.m4 = splat4((uint32_t)(lo + h));
+  k.k4 = splat4((uint32_t)(127 - h));
+  k.hi4 = splat4((uint32_t)hi);
   k.all = 0;
   k.odd = ((hi - lo) & 1) != 0;
   return k;
+}
+
+// floor(n / d) for d >= 1 and quotients below 2^20 (every quotient here is a
+// byte value or a few hundred): a float-reciprocal estimate, corrected exactly.
+__device__ __forceinline__ unsigned udiv_q(unsigned n, unsigned d, float rcp) {
+  unsigned q = __float2uint_rz(__uint2float_rz(n) * rcp);
+  while (q * d > n) q--;
+  while ((q + 1) * d <= n) q++;
+  return q;
 }
 
 // bit 7 of each byte set iff that byte is outside [lo, hi] (exact)

@@ -38,6 +38,8 @@ struct Job {
   int pitch;        // bytes per tile row (>= C * esize, pitch/4 = 1 mod 32)
   int fd_items;     // number of FDSC work items (ceil(T / 32))
   int rows;         // TDSC rows (C)
+  int td_mode;      // 0: one warp per row, 8 rows per item; 1: one row per item, whole CTA
+  int td_items;     // number of TDSC work items
 };
 
 // A run of consecutive queue items: `count` items of one kind for one job.
@@ -67,20 +69,43 @@ __host__ __device__ inline int align16i(int x) { return (x + 15) & ~15; }
 // Shared memory of one FDSC tile (uint8): ws x pitch tile, per-(t, bin) sums and
 // cached medians, per-column sums of D^2 and keep half-widths, item flag bits,
 // list of flagged (t, bin) pairs.
+// Rows of the per-(t, bin) arrays are padded to nbp = 8 (mod 32) entries, so the
+// 8 lanes of 4 neighbouring columns hit 32 distinct banks.
+__host__ __device__ inline int fd_nbp(int nb) { return nb + ((8 - nb) % 32 + 32) % 32; }
+
 __host__ __device__ inline int fd_smem_bytes(int ws, int pitch, int nb, int C) {
-  return ws * pitch + align16i(ws * nb * 4) + align16i(ws * nb * 2) + align16i(ws * 8) + align16i(ws * 8) +
-         align16i(C * 4) + align16i(ws * nb * 4) + 16;
+  const int nbp = fd_nbp(nb);
+  return ws * pitch + align16i(ws * nbp * 4) + align16i(ws * nbp * 2) + align16i(ws * 8) + align16i(ws * 8) +
+         align16i(C * 4) + align16i(ws * nb * 4) + 4 * (NT / 32);
+}
+
+// Tile row pitch: C bytes rounded up to 128, so that the XOR swizzle of the 16-byte
+// units of a row (by (row >> 2) & 7) stays inside the row.
+__host__ __device__ inline int fd_pitch(int C_bytes) { return ((C_bytes + 127) / 128) * 128; }
+
+// TDSC row staging: a warp stages rows of up to TD_WARP_CHUNKS 16-byte chunks
+// (8 warps share TD_WARP_STAGE * 8 bytes); longer rows, up to TD_CTA_CHUNKS
+// chunks, are staged and processed by the whole CTA.
+constexpr int TD_WARP_CHUNKS = 800;
+constexpr int TD_WARP_STAGE = TD_WARP_CHUNKS * 16;
+constexpr int TD_CTA_CHUNKS = 6144;
+constexpr int TD_ROWS_PER_ITEM = NT / 32;
+
+// Row mode for rows of T bytes: 0 = warp rows, 1 = CTA rows, -1 = too long.
+inline int td_row_mode(long long T) {
+  const long long nch = (T + 30) / 16 + 1;  // worst-case alignment of the row start
+  if (nch <= TD_WARP_CHUNKS) return 0;
+  if (nch <= TD_CTA_CHUNKS) return 1;
+  return -1;
 }
 
 // Launchers (engine_u8.cu).
 struct LaunchCfg {
   int grid;
   int smem;
-  int nch;  // TDSC chunks of 16 bytes per thread (register-resident rows)
 };
-int engine_smem_u8(const Params& p, int nch);
-int engine_nch_for(int max_T_bytes);
-void* engine_kernel_u8(int nch);
+int engine_smem_u8(const Params& p);
+void* engine_kernel_u8();
 int launch_engine_u8(const Params& p, const LaunchCfg& cfg, void* stream);
 
 }  // namespace rfim

@@ -1,17 +1,30 @@
 // engine_u8.cu -- uint8 TDSC / FDSC kernels and the persistent work-queue engine.
 //
-// Work items (one queue, dequeued in order by every CTA of a persistent grid):
-//   TDSC row   : one (beam, channel) row of T samples, held in registers by a
-//                CTA of 256 threads (16-byte chunks, NCH per thread).  All
-//                iterations run on chip; the row's output and TDSC flags are
-//                written once.  Completion is published per beam.
-//   FDSC item  : 32 time samples x all C channels of one beam.  The slab is
-//                loaded (transposed to [t][c]) into shared memory, all FDSC
-//                iterations run on chip, output and flags are written once.
-//                In the fused schedule the item first waits (bounded) until
-//                its beam's TDSC rows are done and reads their output, which
-//                the queue order keeps resident in L2.
+// One persistent kernel serves every call.  CTAs of 256 threads dequeue work
+// items in queue order:
+//   TDSC rows  : rows of up to 800 16-byte chunks are processed one per warp
+//                (8 rows per item); longer rows (up to 6144 chunks) one per
+//                item by the whole CTA.  A row is staged once in shared memory;
+//                every TDSC iteration is a pass over the staged copy, reduced
+//                with warp shuffles; the output row and its flags are written
+//                once.
+//   FDSC item  : 32 time samples x all C channels of one beam, transposed into
+//                a [t][c] shared-memory tile.  Each warp owns a set of columns
+//                (LPC lanes per column), so the FDSC iterations run without CTA
+//                barriers; bins holding a sample outside their keep interval
+//                are compacted into a per-warp list and resolved one per lane.
+// In the fused schedule the FDSC items of a beam wait (bounded) until its TDSC
+// rows are published and read their output while it is still in L2.
 // Layout: BCT (x[b][c][t], time fastest).
+//
+// Decision rule (exact, bit-identical to the reference definition):
+//   TDSC keeps x iff |T x - S| <= A, A = max{a : (double)a^2 <= fl(k2 (T Q - S^2))};
+//   FDSC keeps x iff |G x - S_g| <= A_g, A_g = max{a : (double)(C m_g^2 a^2) <= fl(k2 V)},
+//   V = sum over channels of D^2 (see common.cuh).
+// With median replacement every replaced value is the row's (bin's) lower
+// median, which replacing values by it never changes; so the samples flagged
+// by any of the I iterations are those outside the intersection of the I keep
+// intervals, and they all end at the median.
 #include <cstdint>
 #include <cstdio>
 
@@ -20,16 +33,32 @@
 namespace rfim {
 
 // ---------------------------------------------------------------------------
-// loads / stores with alignment and bounds handling
+// memory access helpers
 // ---------------------------------------------------------------------------
 
-// 16 bytes at a 16-aligned address a, bytes outside [lo, hi) read as 0.
+// 16 bytes at a 16-aligned address, not allocated in L1 (another SM may later
+// write these addresses in place, and this SM must not keep a stale copy).
+__device__ __forceinline__ uint4 ld16_na(const uint8_t* a) {
+  uint4 v;
+  asm volatile("ld.global.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(a));
+  return v;
+}
+
+__device__ __forceinline__ uint8_t ld1_na(const uint8_t* a) {
+  unsigned short v;
+  asm volatile("ld.global.L1::no_allocate.u8 %0, [%1];" : "=h"(v) : "l"(a));
+  return (uint8_t)v;
+}
+
+// 16 bytes at a 16-aligned address a; bytes outside [lo, hi) read as 0.
 __device__ __forceinline__ uint4 load16_guarded(const uint8_t* a, const uint8_t* lo, const uint8_t* hi) {
-  if (a >= lo && a + 16 <= hi) return __ldcs(reinterpret_cast<const uint4*>(a));
+  if (a >= lo && a + 16 <= hi) return ld16_na(a);
   uint32_t w[4] = {0, 0, 0, 0};
   for (int b = 0; b < 16; b++) {
     const uint8_t* p = a + b;
-    if (p >= lo && p < hi) w[b >> 2] |= (uint32_t)__ldcs(p) << (8 * (b & 3));
+    if (p >= lo && p < hi) w[b >> 2] |= (uint32_t)ld1_na(p) << (8 * (b & 3));
   }
   return make_uint4(w[0], w[1], w[2], w[3]);
 }
@@ -43,52 +72,200 @@ __device__ __forceinline__ void store16_partial(uint8_t* dst, const uint4& v, in
   for (int b = lo; b < hi; b++) dst[b] = (uint8_t)(word_of(v, b >> 2) >> (8 * (b & 3)));
 }
 
-// 4 bytes of a row at global address a: bytes [0, n) valid (n <= 4), the rest 0.
-// Reads only inside [lo, hi).  `cg` loads bypass L1 (data written by other CTAs).
-__device__ __forceinline__ uint32_t load4_any(const uint8_t* a, int n, const uint8_t* lo, const uint8_t* hi) {
+// n (<= 16) bytes of a row starting at global address a, bytes past n read as
+// 0.  Reads only inside [lo, hi).
+__device__ __forceinline__ uint4 load_seg16(const uint8_t* a, int n, const uint8_t* lo, const uint8_t* hi) {
   const uintptr_t ia = (uintptr_t)a;
-  const int off = (int)(ia & 3);
-  const uint8_t* al = a - off;
-  if (n == 4 && off == 0 && a >= lo && a + 4 <= hi) return __ldcg(reinterpret_cast<const unsigned*>(a));
-  if (n == 4 && al >= lo && al + 8 <= hi) {
-    const uint32_t w0 = __ldcg(reinterpret_cast<const unsigned*>(al));
-    const uint32_t w1 = __ldcg(reinterpret_cast<const unsigned*>(al + 4));
-    return __funnelshift_r(w0, w1, 8 * off);
+  if (n == 16 && a >= lo && a + 16 <= hi) {
+    if ((ia & 15) == 0) return *reinterpret_cast<const uint4*>(a);
+    if ((ia & 3) == 0) {
+      const uint32_t* p = reinterpret_cast<const uint32_t*>(a);
+      return make_uint4(p[0], p[1], p[2], p[3]);
+    }
+    const int off = (int)(ia & 3);
+    const uint8_t* al = a - off;
+    if (al >= lo && al + 20 <= hi) {
+      const uint32_t* p = reinterpret_cast<const uint32_t*>(al);
+      const uint32_t w0 = p[0], w1 = p[1], w2 = p[2], w3 = p[3], w4 = p[4];
+      return make_uint4(__funnelshift_r(w0, w1, 8 * off), __funnelshift_r(w1, w2, 8 * off),
+                        __funnelshift_r(w2, w3, 8 * off), __funnelshift_r(w3, w4, 8 * off));
+    }
   }
-  uint32_t w = 0;
+  uint32_t w[4] = {0, 0, 0, 0};
   for (int b = 0; b < n; b++) {
     const uint8_t* p = a + b;
-    if (p >= lo && p < hi) w |= (uint32_t)__ldcg(p) << (8 * b);
+    if (p >= lo && p < hi) w[b >> 2] |= (uint32_t)(*p) << (8 * (b & 3));
   }
-  return w;
+  return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-__device__ __forceinline__ void store4_any(uint8_t* a, uint32_t w, int n) {
-  if (n == 4 && (((uintptr_t)a) & 3) == 0) {
-    *reinterpret_cast<uint32_t*>(a) = w;
-    return;
+// store n (<= 16) bytes of v to global address a
+__device__ __forceinline__ void store_seg16(uint8_t* a, const uint4& v, int n) {
+  const uintptr_t ia = (uintptr_t)a;
+  if (n == 16 && (ia & 15) == 0) {
+    *reinterpret_cast<uint4*>(a) = v;
+  } else if (n == 16 && (ia & 3) == 0) {
+    uint32_t* p = reinterpret_cast<uint32_t*>(a);
+    p[0] = v.x;
+    p[1] = v.y;
+    p[2] = v.z;
+    p[3] = v.w;
+  } else {
+    store16_partial(a, v, 0, n);
   }
-  for (int b = 0; b < n; b++) a[b] = (uint8_t)(w >> (8 * b));
 }
 
 // ---------------------------------------------------------------------------
-// exact thresholds
+// exact keep intervals, computed by a group of lanes in parallel
 // ---------------------------------------------------------------------------
 
-// TDSC keep interval of a row: |T x - S| <= A  <=>  lo <= x <= hi.
-__device__ __forceinline__ void tdsc_keep(unsigned long long S, unsigned long long Q, int T, const ExactK2& k2,
-                                          int& lo, int& hi) {
-  const unsigned long long Tl = (unsigned long long)T;
-  const unsigned long long R = Tl * Q - S * S;
-  const unsigned long long A = max_keep(R, 1ull, 255u * (unsigned)T, k2);
-  const long long lo_num = (long long)S - (long long)A;
-  lo = lo_num <= 0 ? 0 : (int)((lo_num + (long long)Tl - 1) / (long long)Tl);
-  const unsigned long long hv = (S + A) / Tl;
+// A = max{a in [0, amax] : (double)(mult a^2) <= fl(k2 R)}.  The W lanes of an
+// aligned group (W = 8 or 32) each test one candidate around a float estimate;
+// the passing candidates form a prefix.  All lanes of the group return A.
+template <int W>
+__device__ __forceinline__ unsigned max_keep_grp(unsigned long long R, unsigned long long mult, unsigned amax,
+                                                 const ExactK2& k) {
+  const int lane = threadIdx.x & 31;
+  const int gl = lane & (W - 1);
+  const int gshift = lane & ~(W - 1);
+  const unsigned full = (W == 32) ? 0xffffffffu : ((1u << W) - 1u);
+  const unsigned gmask = full << gshift;
+  const float est = sqrtf(k.k2f * (float)R / (float)mult);
+  long long e = (long long)est;
+  if (e > (long long)amax) e = amax;  // A never exceeds amax
+  long long base = e - (W / 2 - 1);
+  for (int round = 0; round < 1024; round++) {
+    const long long a = base + gl;
+    bool ok;
+    if (a < 0) ok = true;
+    else if (a > (long long)amax) ok = false;
+    else ok = le_thr(mult * (unsigned long long)a * (unsigned long long)a, R, k);
+    const unsigned b = (__ballot_sync(gmask, ok) >> gshift) & full;
+    if (b == full) {
+      if (base + (W - 1) >= (long long)amax) return amax;
+      base += W;
+      continue;
+    }
+    if (b == 0) {
+      base -= W;
+      continue;
+    }
+    return (unsigned)(base + __popc(b) - 1);
+  }
+  return 0;  // not reached: the float estimate lies within a few units of A
+}
+
+// keep interval [lo, hi] of |d x - S| <= A (S, A < 2^31, quotients <= 510)
+__device__ __forceinline__ void keep_from(unsigned S, unsigned A, unsigned d, float rcp, int& lo, int& hi) {
+  lo = S <= A ? 0 : (int)udiv_q(S - A + d - 1, d, rcp);
+  const unsigned hv = udiv_q(S + A, d, rcp);
   hi = hv > 255 ? 255 : (int)hv;
 }
 
+// TDSC keep interval of a row; all 32 lanes of the calling warp cooperate.
+__device__ __forceinline__ void tdsc_keep_warp(unsigned long long S, unsigned long long Q, int T, float rcpT,
+                                               const ExactK2& k2, int& lo, int& hi) {
+  const unsigned long long Tl = (unsigned long long)T;
+  const unsigned long long R = Tl * Q - S * S;
+  const unsigned A = max_keep_grp<32>(R, 1ull, 255u * (unsigned)T, k2);
+  keep_from((unsigned)S, A, (unsigned)T, rcpT, lo, hi);
+}
+
 // ---------------------------------------------------------------------------
-// TDSC on one row, row resident in registers
+// byte tests
+// ---------------------------------------------------------------------------
+// bit 7 of each byte set iff the byte is outside [lo, hi]; parity of hi - lo fixed
+template <bool ODD>
+__device__ __forceinline__ uint32_t outside_u(uint32_t x, const ByteKeep& k) {
+  const uint32_t d = absdiff4(x, k.m4);
+  uint32_t g = ((d & 0x7F7F7F7Fu) + k.k4) | d;
+  if (ODD) {
+    const uint32_t e = x ^ k.hi4;
+    g &= ((e & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | e;
+  }
+  return (g & 0x80808080u) | k.all;
+}
+
+// bit 7 of each byte set iff the byte is outside a non-empty [lo, hi]
+template <bool ODD>
+__device__ __forceinline__ uint32_t outside_ne(uint32_t x, const ByteKeep& k) {
+  const uint32_t d = absdiff4(x, k.m4);
+  uint32_t g = ((d & 0x7F7F7F7Fu) + k.k4) | d;
+  if (ODD) {
+    const uint32_t e = x ^ k.hi4;
+    g &= ((e & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | e;
+  }
+  return g & 0x80808080u;
+}
+
+__device__ __forceinline__ uint4 outside4(const uint4& w, const ByteKeep& k) {
+  if (k.all) return make_uint4(0x80808080u, 0x80808080u, 0x80808080u, 0x80808080u);
+  if (k.odd)
+    return make_uint4(outside_ne<true>(w.x, k), outside_ne<true>(w.y, k), outside_ne<true>(w.z, k),
+                      outside_ne<true>(w.w, k));
+  return make_uint4(outside_ne<false>(w.x, k), outside_ne<false>(w.y, k), outside_ne<false>(w.z, k),
+                    outside_ne<false>(w.w, k));
+}
+
+// 0xFF in every flagged byte (flags = 0x80 per byte), on the multiplier
+__device__ __forceinline__ uint32_t wide8(uint32_t f) { return (f >> 7) * 0xFFu; }
+
+// select r4 where flagged
+__device__ __forceinline__ uint32_t sel8(uint32_t x, uint32_t r4, uint32_t F8) { return x ^ ((x ^ r4) & F8); }
+
+// flags of a 16-byte chunk -> 16 bits (byte b -> bit b), multiplier-based
+__device__ __forceinline__ uint32_t chunk_bits16(const uint4& f) {
+  const uint32_t b0 = ((f.x >> 7) * 0x01020408u) >> 24, b1 = ((f.y >> 7) * 0x01020408u) >> 24;
+  const uint32_t b2 = ((f.z >> 7) * 0x01020408u) >> 24, b3 = ((f.w >> 7) * 0x01020408u) >> 24;
+  return b0 + 16u * (b1 + 16u * (b2 + 16u * b3));
+}
+
+__device__ __forceinline__ uint32_t sel_bytes(uint32_t x, uint32_t r4, uint32_t f) {
+  const uint32_t F = widen80(f);
+  return (x & ~F) | (r4 & F);
+}
+
+__device__ __forceinline__ uint4 and4(const uint4& a, const uint4& b) {
+  return make_uint4(a.x & b.x, a.y & b.y, a.z & b.z, a.w & b.w);
+}
+
+// byte flags (0x80 per byte) of a 16-byte chunk -> 16 bits, byte b -> bit b
+__device__ __forceinline__ uint32_t chunk_bits(const uint4& f) {
+  return bits4(f.x) | (bits4(f.y) << 4) | (bits4(f.z) << 8) | (bits4(f.w) << 12);
+}
+
+// ---------------------------------------------------------------------------
+// group reductions: LANES = 32 (one warp per row) or NT (the CTA)
+// ---------------------------------------------------------------------------
+template <int LANES, int N>
+__device__ __forceinline__ void grp_sum(unsigned long long (&v)[N], unsigned long long* scr) {
+#pragma unroll
+  for (int i = 0; i < N; i++) v[i] = warp_sum(v[i]);
+  if (LANES == 32) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < N; i++) scr[i * (NT / 32) + warp] = v[i];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < N; i++) {
+    unsigned long long s = 0;
+#pragma unroll
+    for (int w = 0; w < NT / 32; w++) s += scr[i * (NT / 32) + w];
+    v[i] = s;
+  }
+}
+
+template <int LANES>
+__device__ __forceinline__ void grp_sync() {
+  if (LANES == 32) __syncwarp();
+  else __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// TDSC on one row by a group of LANES threads; the row is staged in `st`.
 // ---------------------------------------------------------------------------
 struct RowGeom {
   const uint8_t* cb;  // 16-aligned base of the chunk grid of the input row
@@ -97,100 +274,109 @@ struct RowGeom {
   int tail;           // valid bytes in the last chunk (1..16)
 };
 
-__device__ __forceinline__ int chunk_lo(const RowGeom& g, int k) { return k == 0 ? g.head : 0; }
-__device__ __forceinline__ int chunk_hi(const RowGeom& g, int k) { return k == g.nch - 1 ? g.tail : 16; }
+__device__ __forceinline__ uint4 chunk_valid(const RowGeom& g, int k) {
+  const int lo = k == 0 ? g.head : 0, hi = k == g.nch - 1 ? g.tail : 16;
+  return chunk_keep_mask(lo, hi);
+}
 
-template <int NCH>
-__device__ __forceinline__ unsigned row_median(const uint4 (&v)[NCH], const RowGeom& g, int T, unsigned long long S,
-                                               unsigned long long Q, unsigned* red) {
-  // Lower median m = min{p : #(x <= p) >= need}, need = floor((T+1)/2).
-  // With f(p) = sum |x - p|, #(x <= p) = (T + f(p+1) - f(p)) / 2 for p <= 254.
-  // The median lies within one standard deviation of the mean.
-  const int need = (T + 1) >> 1;
+// Lower median of a staged row: m = min{p : #(x <= p) >= need}, need = floor((T+1)/2).
+// With f(p) = sum |x - p| (SAD), #(x <= p) = (T + f(p+1) - f(p)) / 2 for p <= 254,
+// and a median lies within one standard deviation of the mean.  The first pass
+// probes three consecutive points around the mean; later passes split the
+// remaining window in three.
+struct MedSearch {
+  int lo, hi;    // the median lies in [lo, hi]
+  int pts[4];    // probe points of the current pass
+  bool first;
+};
+
+__device__ __forceinline__ void med_init(MedSearch& m, unsigned long long S, unsigned long long Q, int T) {
   const float mu = (float)S / (float)T;
   float var = (float)Q / (float)T - mu * mu;
   var = var > 0.f ? var : 0.f;
   const float sd = sqrtf(var);
-  int lo = (int)floorf(mu - sd) - 1, hi = (int)ceilf(mu + sd) + 1;
-  lo = lo < 0 ? 0 : lo;
-  hi = hi > 255 ? 255 : hi;
-  const unsigned npad = 16u * (unsigned)g.nch - (unsigned)T;  // zero bytes inside the chunk grid
-  int q0 = (int)floorf(mu);
-  bool first = true;
-  while (lo < hi) {
-    int pts[4];
-    if (first) {
-      int c = q0 - 1;
-      if (c < lo) c = lo;
-      if (c > hi - 2) c = hi - 2;
-      if (c < 0) c = 0;
-      pts[0] = c;
-      pts[1] = c + 1;
-      pts[2] = c + 2;
-      pts[3] = c + 3;
-    } else {
-      const int a = lo + (hi - lo) / 3, b = lo + 2 * (hi - lo) / 3;
-      pts[0] = a;
-      pts[1] = a + 1;
-      pts[2] = b > a ? b : a + 1;
-      pts[3] = pts[2] + 1;
-    }
-    unsigned f[4] = {0, 0, 0, 0};
-    uint32_t p4[4];
-#pragma unroll
-    for (int i = 0; i < 4; i++) p4[i] = (uint32_t)(pts[i] > 255 ? 255 : pts[i]) * 0x01010101u;
-#pragma unroll
-    for (int j = 0; j < NCH; j++) {
-      const int k = threadIdx.x + j * NT;
-      if (k < g.nch) {
-#pragma unroll
-        for (int i = 0; i < 4; i++) {
-          f[i] = sad4(v[j].x, p4[i], f[i]);
-          f[i] = sad4(v[j].y, p4[i], f[i]);
-          f[i] = sad4(v[j].z, p4[i], f[i]);
-          f[i] = sad4(v[j].w, p4[i], f[i]);
-        }
+  m.lo = max(0, (int)floorf(mu - sd) - 1);
+  m.hi = min(255, (int)ceilf(mu + sd) + 1);
+  int c = (int)floorf(mu) - 1;
+  if (c > m.hi - 2) c = m.hi - 2;
+  if (c < m.lo) c = m.lo;
+  if (c < 0) c = 0;
+  m.pts[0] = c;
+  m.pts[1] = c + 1;
+  m.pts[2] = c + 2;
+  m.pts[3] = c + 3;
+  m.first = true;
+}
+
+__device__ __forceinline__ uint32_t med_probe4(const MedSearch& m, int i) {
+  return (uint32_t)(m.pts[i] > 255 ? 255 : m.pts[i]) * 0x01010101u;
+}
+
+// Narrow the window with the SAD sums f[i] = f(pts[i]) (padding already removed).
+__device__ __forceinline__ void med_update(MedSearch& m, const unsigned long long (&f)[4], int T) {
+  const int need = (T + 1) >> 1;
+  auto count_at = [&](int i) -> long long {  // #(x <= pts[i])
+    if (m.pts[i] >= 255) return T;
+    return ((long long)T + (long long)f[i + 1] - (long long)f[i]) / 2;
+  };
+  if (m.first) {
+    for (int i = 0; i < 3; i++) {
+      const int p = m.pts[i];
+      if (p < m.lo || p > m.hi) continue;
+      if (count_at(i) >= need) {
+        m.hi = p;
+        break;
       }
+      m.lo = p + 1;
     }
-    block_sum<unsigned, 4>(f, red);
-#pragma unroll
-    for (int i = 0; i < 4; i++) f[i] -= npad * (unsigned)(pts[i] > 255 ? 255 : pts[i]);
-    auto count_at = [&](int i) -> int {  // #(x <= pts[i]) from f[i], f[i+1]
-      if (pts[i] >= 255) return T;
-      return (int)(((long long)T + (long long)f[i + 1] - (long long)f[i]) / 2);
-    };
-    if (first) {
-      // counts at c, c+1, c+2
-      for (int i = 0; i < 3; i++) {
-        const int p = pts[i];
-        if (p < lo || p > hi) continue;
-        if (count_at(i) >= need) {
-          hi = p;
-          break;
-        }
-        lo = p + 1;
-      }
-      first = false;
+    m.first = false;
+  } else {
+    if (count_at(0) >= need) {
+      m.hi = m.pts[0];
     } else {
-      const int cA = count_at(0);
-      if (cA >= need) {
-        hi = pts[0];
-      } else {
-        lo = pts[0] + 1;
-        if (pts[2] <= hi) {
-          const int cB = count_at(2);
-          if (cB >= need) hi = pts[2];
-          else lo = pts[2] + 1;
-        }
+      m.lo = m.pts[0] + 1;
+      if (m.pts[2] <= m.hi) {
+        if (count_at(2) >= need) m.hi = m.pts[2];
+        else m.lo = m.pts[2] + 1;
       }
     }
   }
-  return (unsigned)lo;
+  const int a = m.lo + (m.hi - m.lo) / 3, b = m.lo + 2 * (m.hi - m.lo) / 3;
+  m.pts[0] = a;
+  m.pts[1] = a + 1;
+  m.pts[2] = b > a ? b : a + 1;
+  m.pts[3] = m.pts[2] + 1;
 }
 
-template <int NCH>
-__device__ void tdsc_row_u8(const Params& P, const Job& J, int row, unsigned char* smem, unsigned long long* red64,
-                            unsigned* red32, int* bc) {
+template <int LANES>
+__device__ unsigned med_finish(MedSearch& m, const uint4* st, int nch, int T, unsigned long long npad,
+                               unsigned long long* scr, int gl) {
+  while (m.lo < m.hi) {
+    uint32_t p4[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) p4[i] = med_probe4(m, i);
+    unsigned f32[4] = {0, 0, 0, 0};
+    for (int k = gl; k < nch; k += LANES) {
+      const uint4 w = st[k];
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        f32[i] = sad4(w.x, p4[i], f32[i]);
+        f32[i] = sad4(w.y, p4[i], f32[i]);
+        f32[i] = sad4(w.z, p4[i], f32[i]);
+        f32[i] = sad4(w.w, p4[i], f32[i]);
+      }
+    }
+    unsigned long long f[4] = {f32[0], f32[1], f32[2], f32[3]};
+    grp_sum<LANES, 4>(f, scr);
+#pragma unroll
+    for (int i = 0; i < 4; i++) f[i] -= npad * (unsigned long long)(m.pts[i] > 255 ? 255 : m.pts[i]);
+    med_update(m, f, T);
+  }
+  return (unsigned)m.lo;
+}
+
+template <int LANES>
+__device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, unsigned long long* scr, int gl) {
   const CutDev& cut = P.td;
   const int T = J.T;
   const uint8_t* beam_in = static_cast<const uint8_t*>(J.in);
@@ -205,177 +391,255 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, unsigned cha
   g.nch = (g.head + T + 15) >> 4;
   g.tail = g.head + T - ((g.nch - 1) << 4);
 
-  uint4 v[NCH];
-  uint32_t fl[NCH];
-  unsigned long long sq[2] = {0, 0};
+  // ---- pass 1: load (8 chunks in flight per lane), stage, S and Q
+  unsigned long long sq[2];
   {
-    uint32_t s = 0, q = 0;
+    unsigned s = 0;
+    unsigned long long q = 0;
+    for (int k0 = gl; k0 < g.nch; k0 += 8 * LANES) {
+      uint4 v[8];
 #pragma unroll
-    for (int j = 0; j < NCH; j++) {
-      const int k = threadIdx.x + j * NT;
-      uint4 w = make_uint4(0, 0, 0, 0);
-      if (k < g.nch) {
-        w = load16_guarded(g.cb + 16 * k, blo, bhi);
-        const int lo = chunk_lo(g, k), hi = chunk_hi(g, k);
-        if (lo != 0 || hi != 16) {
-          const uint4 m = chunk_keep_mask(lo, hi);
-          w.x &= m.x;
-          w.y &= m.y;
-          w.z &= m.z;
-          w.w &= m.w;
-        }
-        s = dp4a_u(w.x, 0x01010101u, s);
-        s = dp4a_u(w.y, 0x01010101u, s);
-        s = dp4a_u(w.z, 0x01010101u, s);
-        s = dp4a_u(w.w, 0x01010101u, s);
-        q = dp4a_u(w.x, w.x, q);
-        q = dp4a_u(w.y, w.y, q);
-        q = dp4a_u(w.z, w.z, q);
-        q = dp4a_u(w.w, w.w, q);
+      for (int u = 0; u < 8; u++) {
+        const int k = k0 + u * LANES;
+        if (k < g.nch) v[u] = load16_guarded(g.cb + 16 * k, blo, bhi);
       }
-      v[j] = w;
-      fl[j] = 0;
+#pragma unroll
+      for (int u = 0; u < 8; u++) {
+        const int k = k0 + u * LANES;
+        if (k < g.nch) {
+          uint4 w = v[u];
+          if (k == 0 || k == g.nch - 1) w = and4(w, chunk_valid(g, k));
+          s = dp4a_u(w.x, 0x01010101u, s) + dp4a_u(w.y, 0x01010101u, 0u) + dp4a_u(w.z, 0x01010101u, 0u) +
+              dp4a_u(w.w, 0x01010101u, 0u);
+          q += dp4a_u(w.x, w.x, 0u) + dp4a_u(w.y, w.y, 0u) + dp4a_u(w.z, w.z, 0u) + dp4a_u(w.w, w.w, 0u);
+          st[k] = w;
+        }
+      }
     }
     sq[0] = s;
     sq[1] = q;
   }
-  block_sum<unsigned long long, 2>(sq, red64);
+  if (LANES == 32) __syncwarp();
+  grp_sum<LANES, 2>(sq, scr);  // (the CTA variant's barriers also publish the staged row)
   unsigned long long S = sq[0], Q = sq[1];
 
-  unsigned med = 0;
-  if (cut.replace == REP_MEDIAN) med = row_median<NCH>(v, g, T, S, Q, red32);
+  // single: every flagged sample ends at one value (the median, or the mean of a
+  // one-iteration cut), so one keep interval (the intersection) decides everything
+  const bool median = cut.replace == REP_MEDIAN;
+  const bool single = median || cut.iterations == 1;
+  const unsigned long long npad = 16ull * (unsigned)g.nch - (unsigned)T;  // zero bytes in the chunk grid
+  const int I = cut.iterations;
+  const float rcpT = 1.0f / (float)T, rcp2T = 0.5f / (float)T;
+  unsigned r_med = 0;
+  int lo_i[16], hi_i[16];
+  ByteKeep kp_i[16];
+  uint32_t r4_i[16];
+  int klo = 0, khi = 255;  // intersection of the keep intervals so far
 
-  for (int it = 0; it < cut.iterations; it++) {
-    const bool last = (it == cut.iterations - 1);
-    if (threadIdx.x == 0) {
+  if (single) {
+    // Every replaced value is the median m, so after iteration i a sample holds
+    // x if x lies in every keep interval so far, else m: S_{i+1} = s_in + n_out m.
+    MedSearch ms;
+    med_init(ms, S, Q, T);
+    for (int it = 0; it < I; it++) {
       int lo, hi;
-      tdsc_keep(S, Q, T, cut.k2, lo, hi);
-      bc[0] = lo;
-      bc[1] = hi;
-      bc[2] = cut.replace == REP_MEDIAN ? (int)med : (int)((2 * S + (unsigned long long)T) / (2ull * T));
-    }
-    __syncthreads();
-    const int lo = bc[0], hi = bc[1], r = bc[2];
-    __syncthreads();
-    const ByteKeep kp = make_keep(lo, hi);
-    const uint32_t r4 = (uint32_t)r * 0x01010101u;
-    int ds = 0, dq = 0;
+      tdsc_keep_warp(S, Q, T, rcpT, cut.k2, lo, hi);
+      klo = lo > klo ? lo : klo;
+      khi = hi < khi ? hi : khi;
+      if (it == I - 1) break;
+      // statistics of the kept samples (and, in the first pass, the median probes)
+      const ByteKeep kp = make_keep(klo, khi);
+      const bool probe = (it == 0);
+      uint32_t p4[4];
 #pragma unroll
-    for (int j = 0; j < NCH; j++) {
-      const int k = threadIdx.x + j * NT;
-      if (k < g.nch) {
-        uint4 msk = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
-        const int clo = chunk_lo(g, k), chi = chunk_hi(g, k);
-        if (clo != 0 || chi != 16) msk = chunk_keep_mask(clo, chi);
-        uint32_t* w = reinterpret_cast<uint32_t*>(&v[j]);
-        const uint32_t* mw = reinterpret_cast<const uint32_t*>(&msk);
+      for (int i = 0; i < 4; i++) p4[i] = med_probe4(ms, i);
+      unsigned f32[4] = {0, 0, 0, 0};
+      unsigned s_in = 0, n_out = 0;
+      unsigned long long q_in = 0;
+      for (int k = gl; k < g.nch; k += LANES) {
+        const uint4 w = st[k];
+        if (probe) {
 #pragma unroll
-        for (int i = 0; i < 4; i++) {
-          const uint32_t x = w[i];
-          const uint32_t f = outside_exact(x, kp) & mw[i];
-          if (f) {
-            const uint32_t F = widen80(f);
-            if (!last) {
-              const uint32_t xm = x & F;
-              const int n = __popc(f);
-              ds += n * r - (int)dp4a_u(xm, 0x01010101u, 0u);
-              dq += n * r * r - (int)dp4a_u(xm, xm, 0u);
-            }
-            w[i] = (x & ~F) | (r4 & F);
-            fl[j] |= bits4(f) << (4 * i);
+          for (int i = 0; i < 4; i++) {
+            f32[i] = sad4(w.x, p4[i], f32[i]);
+            f32[i] = sad4(w.y, p4[i], f32[i]);
+            f32[i] = sad4(w.z, p4[i], f32[i]);
+            f32[i] = sad4(w.w, p4[i], f32[i]);
           }
         }
+        uint4 f = outside4(w, kp);
+        if (k == 0 || k == g.nch - 1) f = and4(f, chunk_valid(g, k));
+        const uint32_t i0 = w.x & ~wide8(f.x), i1 = w.y & ~wide8(f.y);
+        const uint32_t i2 = w.z & ~wide8(f.z), i3 = w.w & ~wide8(f.w);
+        s_in += dp4a_u(i0, 0x01010101u, 0u) + dp4a_u(i1, 0x01010101u, 0u) + dp4a_u(i2, 0x01010101u, 0u) +
+                dp4a_u(i3, 0x01010101u, 0u);
+        q_in += dp4a_u(i0, i0, 0u) + dp4a_u(i1, i1, 0u) + dp4a_u(i2, i2, 0u) + dp4a_u(i3, i3, 0u);
+        n_out += __popc(f.x) + __popc(f.y) + __popc(f.z) + __popc(f.w);
       }
+      unsigned long long red[7] = {s_in, q_in, n_out, f32[0], f32[1], f32[2], f32[3]};
+      grp_sum<LANES, 7>(red, scr);
+      if (probe) {
+        unsigned long long f[4] = {red[3], red[4], red[5], red[6]};
+#pragma unroll
+        for (int i = 0; i < 4; i++) f[i] -= npad * (unsigned long long)(ms.pts[i] > 255 ? 255 : ms.pts[i]);
+        med_update(ms, f, T);
+        r_med = med_finish<LANES>(ms, st, g.nch, T, npad, scr, gl);
+      }
+      S = red[0] + red[2] * r_med;
+      Q = red[1] + red[2] * r_med * r_med;
     }
-    if (!last) {
-      long long d[2] = {ds, dq};
-      block_sum<long long, 2>(d, reinterpret_cast<long long*>(red64));
-      S = (unsigned long long)((long long)S + d[0]);
-      Q = (unsigned long long)((long long)Q + d[1]);
+    if (I == 1)
+      r_med = median ? med_finish<LANES>(ms, st, g.nch, T, npad, scr, gl)
+                     : udiv_q((unsigned)(2 * S + (unsigned long long)T), 2u * (unsigned)T, rcp2T);
+  } else {
+    for (int it = 0; it < I; it++) {
+      int lo, hi;
+      tdsc_keep_warp(S, Q, T, rcpT, cut.k2, lo, hi);
+      const unsigned r = udiv_q((unsigned)(2 * S + (unsigned long long)T), 2u * (unsigned)T, rcp2T);
+      lo_i[it] = lo;
+      hi_i[it] = hi;
+      kp_i[it] = make_keep(lo, hi);
+      r4_i[it] = splat4(r);
+      if (it == I - 1) break;
+      // mean: replay iterations 0..it on every value
+      unsigned s2 = 0;
+      unsigned long long q2 = 0;
+      for (int k = gl; k < g.nch; k += LANES) {
+        const uint4 w = st[k];
+        const uint4 vm = (k == 0 || k == g.nch - 1) ? chunk_valid(g, k) : make_uint4(~0u, ~0u, ~0u, ~0u);
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+          uint32_t y = word_of(w, i);
+          const uint32_t m = word_of(vm, i);
+          for (int j = 0; j <= it; j++) y = sel_bytes(y, r4_i[j], outside_exact(y, kp_i[j]) & m);
+          s2 = dp4a_u(y, 0x01010101u, s2);
+          q2 += dp4a_u(y, y, 0u);
+        }
+      }
+      unsigned long long d[2] = {s2, q2};
+      grp_sum<LANES, 2>(d, scr);
+      S = d[0];
+      Q = d[1];
     }
   }
 
-  // ---- write the row
+  // ---- final pass: output and flags
   const bool same_align = (((uintptr_t)rout) & 15) == (uintptr_t)g.head;
-  uint8_t* ob = rout - g.head;  // chunk grid of the output (16-aligned if same_align)
+  uint8_t* ob = rout - g.head;
+  const int W32 = (T + 31) >> 5;
+  uint32_t* mrow = (P.mask_kind == MASK_BITS && J.mask) ? static_cast<uint32_t*>(J.mask) + (size_t)row * W32 : nullptr;
+  uint8_t* mrowb = (P.mask_kind == MASK_BYTES && J.mask) ? static_cast<uint8_t*>(J.mask) + (size_t)row * T : nullptr;
+  const bool mb_align = mrowb && ((((uintptr_t)mrowb) & 15) == (uintptr_t)g.head);
+  uint8_t* mbb = mrowb ? mrowb - g.head : nullptr;
+  const ByteKeep kk = make_keep(klo, khi);
+  const uint32_t rm4 = r_med * 0x01010101u;
+  uint16_t* f16 = reinterpret_cast<uint16_t*>(st);  // flag bits of chunk k overwrite consumed staged bytes
+  auto final_chunk = [&](const int k) -> uint32_t {
+    uint32_t fb = 0;
+      const uint4 w = st[k];
+      const bool edge = (k == 0 || k == g.nch - 1);
+      const uint4 vm = edge ? chunk_valid(g, k) : make_uint4(~0u, ~0u, ~0u, ~0u);
+      uint4 y, f;
+      if (single) {
+        f = outside4(w, kk);
+        if (edge) f = and4(f, vm);
+        y = make_uint4(sel8(w.x, rm4, wide8(f.x)), sel8(w.y, rm4, wide8(f.y)), sel8(w.z, rm4, wide8(f.z)),
+                       sel8(w.w, rm4, wide8(f.w)));
+      } else {
+        uint32_t yy[4], ff[4];
 #pragma unroll
-  for (int j = 0; j < NCH; j++) {
-    const int k = threadIdx.x + j * NT;
-    if (k < g.nch) {
-      const int clo = chunk_lo(g, k), chi = chunk_hi(g, k);
-      if (same_align && clo == 0 && chi == 16)
-        *reinterpret_cast<uint4*>(ob + 16 * k) = v[j];
-      else
-        store16_partial(ob + 16 * k, v[j], clo, chi);
+        for (int i = 0; i < 4; i++) {
+          uint32_t v = word_of(w, i), fl = 0;
+          const uint32_t m = word_of(vm, i);
+          for (int j = 0; j < I; j++) {
+            const uint32_t fj = outside_exact(v, kp_i[j]) & m;
+            v = sel_bytes(v, r4_i[j], fj);
+            fl |= fj;
+          }
+          yy[i] = v;
+          ff[i] = fl;
+        }
+        y = make_uint4(yy[0], yy[1], yy[2], yy[3]);
+        f = make_uint4(ff[0], ff[1], ff[2], ff[3]);
+      }
+      fb = chunk_bits16(f);
+      if (same_align && !edge) {
+        *reinterpret_cast<uint4*>(ob + 16 * k) = y;
+      } else {
+        const int clo = k == 0 ? g.head : 0, chi = k == g.nch - 1 ? g.tail : 16;
+        store16_partial(ob + 16 * k, y, clo, chi);
+      }
+      if (mrowb) {
+        const uint4 fbytes = make_uint4(bytes_from_bits4(fb), bytes_from_bits4(fb >> 4), bytes_from_bits4(fb >> 8),
+                                        bytes_from_bits4(fb >> 12));
+        if (mb_align && !edge) {
+          *reinterpret_cast<uint4*>(mbb + 16 * k) = fbytes;
+        } else {
+          const int clo = k == 0 ? g.head : 0, chi = k == g.nch - 1 ? g.tail : 16;
+          store16_partial(mbb + 16 * k, fbytes, clo, chi);
+        }
+      }
+    return fb;
+  };
+  for (int base = 0; base < g.nch; base += 2 * LANES) {
+    const int ka = base + gl, kb = base + LANES + gl;
+    uint32_t fa = 0, fbb = 0;
+    if (ka < g.nch) fa = final_chunk(ka);
+    if (kb < g.nch) fbb = final_chunk(kb);
+    if (mrow) {
+      grp_sync<LANES>();  // every chunk <= kb of this round has been read
+      if (ka < g.nch) f16[ka] = (uint16_t)fa;
+      if (kb < g.nch) f16[kb] = (uint16_t)fbb;
     }
   }
-  if (P.mask_kind == MASK_BITS && J.mask) {
-    uint16_t* f16 = reinterpret_cast<uint16_t*>(smem);
-#pragma unroll
-    for (int j = 0; j < NCH; j++) {
-      const int k = threadIdx.x + j * NT;
-      if (k < g.nch) f16[k] = (uint16_t)fl[j];
-    }
-    __syncthreads();
-    const int W32 = (T + 31) >> 5;
-    uint32_t* mrow = static_cast<uint32_t*>(J.mask) + (size_t)row * W32;
-    for (int w = threadIdx.x; w < W32; w += NT) {
-      const int o = g.head + 32 * w;
-      const int k0 = o >> 4, sh = o & 15;
+  if (mrow) {
+    grp_sync<LANES>();
+    // word w covers chunk-grid bytes [head + 32 w, head + 32 w + 32): chunks 2w .. 2w+2
+    for (int wi = gl; wi < W32; wi += LANES) {
+      const int k0 = 2 * wi;
       unsigned long long bits = f16[k0];
       if (k0 + 1 < g.nch) bits |= (unsigned long long)f16[k0 + 1] << 16;
       if (k0 + 2 < g.nch) bits |= (unsigned long long)f16[k0 + 2] << 32;
-      uint32_t word = (uint32_t)(bits >> sh);
-      const int valid = T - 32 * w;
+      uint32_t word = (uint32_t)(bits >> g.head);
+      const int valid = T - 32 * wi;
       if (valid < 32) word &= (1u << valid) - 1u;
-      mrow[w] = word;
-    }
-    __syncthreads();
-  } else if (P.mask_kind == MASK_BYTES && J.mask) {
-    uint8_t* mrowb = static_cast<uint8_t*>(J.mask) + (size_t)row * T;
-    const bool ma = (((uintptr_t)mrowb) & 15) == (uintptr_t)g.head;
-    uint8_t* mb = mrowb - g.head;
-#pragma unroll
-    for (int j = 0; j < NCH; j++) {
-      const int k = threadIdx.x + j * NT;
-      if (k < g.nch) {
-        const uint32_t f = fl[j];
-        const uint4 fb = make_uint4(bytes_from_bits4(f), bytes_from_bits4(f >> 4), bytes_from_bits4(f >> 8),
-                                    bytes_from_bits4(f >> 12));
-        const int clo = chunk_lo(g, k), chi = chunk_hi(g, k);
-        if (ma && clo == 0 && chi == 16)
-          *reinterpret_cast<uint4*>(mb + 16 * k) = fb;
-        else
-          store16_partial(mb + 16 * k, fb, clo, chi);
-      }
+      mrow[wi] = word;
     }
   }
 }
 
 // ---------------------------------------------------------------------------
 // FDSC on one item: 32 time samples x C channels, tile [t][c] in shared memory
+//
+// Tile addressing: row t holds the C channels of time sample t (pitch bytes,
+// a multiple of 128).  Its 16-byte units are XOR-swizzled by (t >> 2) & 7, so
+//  - the load/store units (4 channels x 4 samples, lanes along time so that
+//    every global access is a contiguous 32-byte run of a row) write and read
+//    32 distinct banks, and
+//  - the 8 lanes of a column reading 32-byte bins (two 16-byte loads, halves
+//    ordered by lane) touch 8 distinct bank groups.
 // ---------------------------------------------------------------------------
 struct FdLayout {
   uint8_t* tile;          // ws rows x pitch bytes
-  unsigned* Sg;           // ws x nb bin sums
-  uint16_t* med;          // ws x nb cached bin medians (0xFFFF unknown)
+  unsigned* Sg;           // ws x nbp bin sums
+  uint16_t* med;          // ws x nbp cached bin medians (0xFFFF unknown)
   unsigned long long* V;  // ws: sum of D^2 per column
   unsigned* A;            // ws x 2: keep half-widths per bin-size class
   unsigned* fmask;        // C: FDSC flag bits of the item (bit = t - t_item)
-  unsigned* list;         // ws x nb flagged pairs
-  unsigned* cnt;
+  unsigned* list;         // ws x nb flagged (t, bin) pairs, one segment per warp
+  unsigned* cnt;          // per-warp list lengths
 };
-
 
 __device__ __forceinline__ FdLayout fd_layout(unsigned char* smem, int ws, int pitch, int nb, int C) {
   FdLayout L;
+  const int nbp = fd_nbp(nb);
   unsigned char* p = smem;
   L.tile = p;
   p += ws * pitch;
   L.Sg = reinterpret_cast<unsigned*>(p);
-  p += align16i(ws * nb * 4);
+  p += align16i(ws * nbp * 4);
   L.med = reinterpret_cast<uint16_t*>(p);
-  p += align16i(ws * nb * 2);
+  p += align16i(ws * nbp * 2);
   L.V = reinterpret_cast<unsigned long long*>(p);
   p += align16i(ws * 8);
   L.A = reinterpret_cast<unsigned*>(p);
@@ -388,43 +652,41 @@ __device__ __forceinline__ FdLayout fd_layout(unsigned char* smem, int ws, int p
   return L;
 }
 
-// S and Q of one bin row: channels [c0, c0 + n) of tile row `row`.
-__device__ __forceinline__ void bin_sums(const uint8_t* row, int c0, int n, bool words, unsigned& S, unsigned& Q) {
-  unsigned s = 0, q = 0;
-  if (words) {  // c0 % 4 == 0; bytes past C in the last word are 0
-    const uint32_t* w = reinterpret_cast<const uint32_t*>(row + c0);
-    const int nw = (n + 3) >> 2;
-    for (int i = 0; i < nw; i++) {
-      const uint32_t x = w[i];
-      s = dp4a_u(x, 0x01010101u, s);
-      q = dp4a_u(x, x, q);
-    }
-  } else {
-    for (int i = 0; i < n; i++) {
-      const unsigned x = row[c0 + i];
-      s += x;
-      q += x * x;
-    }
-  }
-  S = s;
-  Q = q;
+// byte offset of channel c of tile row r
+__device__ __forceinline__ int toff(int r, int c, int pitch) {
+  return r * pitch + ((((c >> 4) ^ ((r >> 2) & 7)) << 4) | (c & 15));
 }
 
-// Lower median of bytes [c0, c0+n) of a tile row (n <= 255*...): counting search.
-__device__ unsigned bin_median(const uint8_t* row, int c0, int n, bool words) {
-  const int need = (n + 1) >> 1;
-  int lo = 0, hi = 255;
+__device__ __forceinline__ unsigned long long fd_contrib(unsigned long long m, unsigned gsz, unsigned S, unsigned Q) {
+  // sum over the bin of D^2 = m^2 * G * (G Q - S^2)
+  return m * m * (unsigned long long)gsz * ((unsigned long long)gsz * Q - (unsigned long long)S * S);
+}
+
+// Channels [c0, c0+n) of tile row r, read as words (c0 % 4 == 0; bytes past C are 0).
+struct BinView {
+  uint8_t* tile;
+  int r, c0, n, pitch;
+  __device__ __forceinline__ uint32_t& word(int i) const {
+    return *reinterpret_cast<uint32_t*>(tile + toff(r, c0 + 4 * i, pitch));
+  }
+  __device__ __forceinline__ uint8_t& byte(int i) const { return tile[toff(r, c0 + i, pitch)]; }
+};
+
+// Lower median of a bin: counting search (SAD sums) over [lo, hi].
+__device__ unsigned bin_median(const BinView& bv, bool words, int lo, int hi) {
+  const int n = bv.n, need = (n + 1) >> 1;
   if (words) {
-    const uint32_t* w = reinterpret_cast<const uint32_t*>(row + c0);
     const int nw = (n + 3) >> 2;
-    const unsigned npad = 4u * nw - n;  // zero bytes (channels >= C)
+    const uint32_t tailmask = (n & 3) ? ((1u << (8 * (n & 3))) - 1u) : 0xffffffffu;
+    const unsigned npad = 4u * nw - n;  // masked bytes count as 0
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
-      const uint32_t pa = (uint32_t)mid * 0x01010101u, pb = (uint32_t)(mid + 1) * 0x01010101u;
+      const uint32_t pa = splat4((uint32_t)mid), pb = splat4((uint32_t)(mid + 1));
       unsigned fa = 0, fb = 0;
       for (int i = 0; i < nw; i++) {
-        fa = sad4(w[i], pa, fa);
-        fb = sad4(w[i], pb, fb);
+        const uint32_t x = (i == nw - 1) ? (bv.word(i) & tailmask) : bv.word(i);
+        fa = sad4(x, pa, fa);
+        fb = sad4(x, pb, fb);
       }
       fa -= npad * (unsigned)mid;
       fb -= npad * (unsigned)(mid + 1);
@@ -436,7 +698,7 @@ __device__ unsigned bin_median(const uint8_t* row, int c0, int n, bool words) {
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
       int cnt = 0;
-      for (int i = 0; i < n; i++) cnt += row[c0 + i] <= mid;
+      for (int i = 0; i < n; i++) cnt += bv.byte(i) <= mid;
       if (cnt >= need) hi = mid;
       else lo = mid + 1;
     }
@@ -444,16 +706,84 @@ __device__ unsigned bin_median(const uint8_t* row, int c0, int n, bool words) {
   return (unsigned)lo;
 }
 
-__device__ __forceinline__ unsigned long long fd_contrib(unsigned long long m, unsigned gsz, unsigned S, unsigned Q) {
-  // sum over the bin of D^2 = m^2 * G * (G Q - S^2)
-  return m * m * (unsigned long long)gsz * ((unsigned long long)gsz * Q - (unsigned long long)S * S);
+// Lower median of the 32 bytes held in w, searched in [lo, hi] (SAD counting).
+__device__ __forceinline__ unsigned median32_regs(const uint32_t (&w)[8], int lo, int hi) {
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const uint32_t pa = splat4((uint32_t)mid), pb = splat4((uint32_t)(mid + 1));
+    unsigned fa = 0, fb = 0, fa1 = 0, fb1 = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i += 2) {
+      fa = sad4(w[i], pa, fa);
+      fb = sad4(w[i], pb, fb);
+      fa1 = sad4(w[i + 1], pa, fa1);
+      fb1 = sad4(w[i + 1], pb, fb1);
+    }
+    // #(x <= mid) = (32 + f(mid+1) - f(mid)) / 2 >= 16
+    if ((int)(fb + fb1) - (int)(fa + fa1) >= 0) hi = mid;
+    else lo = mid + 1;
+  }
+  return (unsigned)lo;
 }
 
-__device__ __forceinline__ void fd_keep(unsigned S, unsigned A, unsigned gsz, int& lo, int& hi) {
-  const long long ln = (long long)S - (long long)A;
-  lo = ln <= 0 ? 0 : (int)((ln + gsz - 1) / gsz);
-  const unsigned hv = (S + A) / gsz;
-  hi = hv > 255 ? 255 : (int)hv;
+// The 8 words of 32-channel bin gi of tile row r (two 16-byte units).  With
+// sw = 1 the halves are fetched in the other order (bank spreading).
+__device__ __forceinline__ void load_bin32(const uint8_t* tile, int r, int gi, int pitch, int sw, uint32_t (&w)[8]) {
+  const int s = (r >> 2) & 7;
+  const uint8_t* row = tile + r * pitch;
+  const uint4* p0 = reinterpret_cast<const uint4*>(row + (((2 * gi) ^ s) << 4));
+  const uint4* p1 = reinterpret_cast<const uint4*>(row + (((2 * gi + 1) ^ s) << 4));
+  uint4 lo, hi;
+  if (sw) {
+    hi = *p1;
+    lo = *p0;
+  } else {
+    lo = *p0;
+    hi = *p1;
+  }
+  w[0] = lo.x;
+  w[1] = lo.y;
+  w[2] = lo.z;
+  w[3] = lo.w;
+  w[4] = hi.x;
+  w[5] = hi.y;
+  w[6] = hi.z;
+  w[7] = hi.w;
+}
+
+__device__ __forceinline__ void store_bin32(uint8_t* tile, int r, int gi, int pitch, const uint32_t (&w)[8]) {
+  const int s = (r >> 2) & 7;
+  uint8_t* row = tile + r * pitch;
+  *reinterpret_cast<uint4*>(row + (((2 * gi) ^ s) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
+  *reinterpret_cast<uint4*>(row + (((2 * gi + 1) ^ s) << 4)) = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+// 4 bytes of a row at global address a (n <= 4 valid), reads only inside [lo, hi)
+__device__ __forceinline__ uint32_t load4_row(const uint8_t* a, int n, const uint8_t* lo, const uint8_t* hi) {
+  const uintptr_t ia = (uintptr_t)a;
+  if (n == 4 && a >= lo && a + 4 <= hi) {
+    if ((ia & 3) == 0) return *reinterpret_cast<const uint32_t*>(a);
+    const int off = (int)(ia & 3);
+    const uint8_t* al = a - off;
+    if (al + 8 <= hi) {
+      const uint32_t* p = reinterpret_cast<const uint32_t*>(al);
+      return __funnelshift_r(p[0], p[1], 8 * off);
+    }
+  }
+  uint32_t w = 0;
+  for (int b = 0; b < n; b++) {
+    const uint8_t* p = a + b;
+    if (p >= lo && p < hi) w |= (uint32_t)(*p) << (8 * b);
+  }
+  return w;
+}
+
+__device__ __forceinline__ void store4_row(uint8_t* a, uint32_t w, int n) {
+  if (n == 4 && (((uintptr_t)a) & 3) == 0) {
+    *reinterpret_cast<uint32_t*>(a) = w;
+    return;
+  }
+  for (int b = 0; b < n; b++) a[b] = (uint8_t)(w >> (8 * b));
 }
 
 __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned char* smem) {
@@ -466,151 +796,328 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
   uint8_t* dst = static_cast<uint8_t*>(J.out);
   const uint8_t* blo = src;
   const uint8_t* bhi = src + (size_t)C * T;
-  const bool words = (G & 3) == 0;
+  const bool words = (G & 3) == 0;  // bins start on 4-byte boundaries of a tile row
   const unsigned long long mf = J.m_full, ml = J.m_last;
   FdLayout L = fd_layout(smem, Ws, pitch, NB, C);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // column ownership: LPC lanes per column, each warp owns 32 / LPC columns
+  const int LPC = NT / Ws;  // Ws in {8, 16, 32} -> 32, 16, 8 lanes per column
+  const int cpw = 32 / LPC;
+  const int sl = lane % LPC;
+  const int tcol = warp * cpw + lane / LPC;
+  unsigned* wlist = L.list + warp * (cpw * NB);
+  unsigned* wcnt = L.cnt + warp;
+  const float rcpG = 1.0f / (float)G, rcpL = 1.0f / (float)Gl;
+  const int NBP = fd_nbp(NB);
+  const bool fast32 = G == 32;  // whole bins are two 16-byte tile units
+  const bool rows4 = ((((uintptr_t)src) | (uintptr_t)T) & 3) == 0;
+  const bool out4 = ((((uintptr_t)dst) | (uintptr_t)T) & 3) == 0;
+  const unsigned long long multF = (unsigned long long)C * mf * mf;
+  const unsigned long long multL = (unsigned long long)C * ml * ml;
 
   for (int c = threadIdx.x; c < C; c += NT) L.fmask[c] = 0;
 
   for (int t0 = t_item; t0 < t_end; t0 += Ws) {
     const int ws = min(Ws, t_end - t0);
     const int nt4 = (ws + 3) >> 2, nq = (C + 3) >> 2;
-    // ---- load (transposed into [t][c])
+    // ---- load: units of 4 channels x 4 samples, lanes along time, transposed into [t][c]
     for (int u = threadIdx.x; u < nq * nt4; u += NT) {
       const int tq = u % nt4, cq = u / nt4;
-      const int tt = 4 * tq;
+      const int c = 4 * cq, tt = 4 * tq;
       const int nv = min(4, ws - tt);
-      uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;
-      const int c = 4 * cq;
+      uint32_t a0, a1, a2, a3;
       const uint8_t* a = src + (size_t)c * T + t0 + tt;
-      if (c + 0 < C) w0 = load4_any(a, nv, blo, bhi);
-      if (c + 1 < C) w1 = load4_any(a + T, nv, blo, bhi);
-      if (c + 2 < C) w2 = load4_any(a + 2 * (size_t)T, nv, blo, bhi);
-      if (c + 3 < C) w3 = load4_any(a + 3 * (size_t)T, nv, blo, bhi);
-      transpose4x4(w0, w1, w2, w3);
-      uint8_t* trow = L.tile + (size_t)tt * pitch + c;
-      *reinterpret_cast<uint32_t*>(trow) = w0;
-      if (nv > 1) *reinterpret_cast<uint32_t*>(trow + pitch) = w1;
-      if (nv > 2) *reinterpret_cast<uint32_t*>(trow + 2 * pitch) = w2;
-      if (nv > 3) *reinterpret_cast<uint32_t*>(trow + 3 * pitch) = w3;
+      if (nv == 4 && c + 3 < C && rows4) {
+        a0 = *reinterpret_cast<const uint32_t*>(a);
+        a1 = *reinterpret_cast<const uint32_t*>(a + T);
+        a2 = *reinterpret_cast<const uint32_t*>(a + 2 * (size_t)T);
+        a3 = *reinterpret_cast<const uint32_t*>(a + 3 * (size_t)T);
+      } else {
+        a0 = load4_row(a, nv, blo, bhi);
+        a1 = c + 1 < C ? load4_row(a + T, nv, blo, bhi) : 0u;
+        a2 = c + 2 < C ? load4_row(a + 2 * (size_t)T, nv, blo, bhi) : 0u;
+        a3 = c + 3 < C ? load4_row(a + 3 * (size_t)T, nv, blo, bhi) : 0u;
+      }
+      transpose4x4(a0, a1, a2, a3);
+      *reinterpret_cast<uint32_t*>(L.tile + toff(tt, c, pitch)) = a0;
+      if (nv > 1) *reinterpret_cast<uint32_t*>(L.tile + toff(tt + 1, c, pitch)) = a1;
+      if (nv > 2) *reinterpret_cast<uint32_t*>(L.tile + toff(tt + 2, c, pitch)) = a2;
+      if (nv > 3) *reinterpret_cast<uint32_t*>(L.tile + toff(tt + 3, c, pitch)) = a3;
     }
-    for (int t = threadIdx.x; t < Ws; t += NT) L.V[t] = 0;
-    for (int i = threadIdx.x; i < Ws * NB; i += NT) L.med[i] = 0xFFFFu;
-    if (threadIdx.x == 0) *L.cnt = 0;
+    for (int i = threadIdx.x; i < Ws * NBP; i += NT) L.med[i] = 0xFFFFu;
     __syncthreads();
 
-    // ---- pass A: bin sums
-    const int npairs = ws * NB;
-    for (int p = threadIdx.x; p < npairs; p += NT) {
-      const int t = p % ws, gi = p / ws;
-      const unsigned gsz = gi == NB - 1 ? (unsigned)Gl : (unsigned)G;
-      unsigned S, Q;
-      bin_sums(L.tile + (size_t)t * pitch, gi * G, gsz, words, S, Q);
-      L.Sg[t * NB + gi] = S;
-      atomicAdd(&L.V[t], fd_contrib(gi == NB - 1 ? ml : mf, gsz, S, Q));
+    // ---- per-warp column work, no CTA barrier until the store
+    const bool own = tcol < ws;
+    {
+      unsigned long long v = 0;
+      if (own) {
+        const int t = tcol;
+        for (int gi = sl; gi < NB; gi += LPC) {
+          const unsigned gsz = gi == NB - 1 ? (unsigned)Gl : (unsigned)G;
+          unsigned s = 0, q = 0;
+          if (fast32 && gsz == 32) {
+            uint32_t w[8];
+            load_bin32(L.tile, t, gi, pitch, (sl >> 2) & 1, w);
+            unsigned s1 = 0, q1 = 0;
+#pragma unroll
+            for (int i = 0; i < 8; i += 2) {
+              s = dp4a_u(w[i], 0x01010101u, s);
+              q = dp4a_u(w[i], w[i], q);
+              s1 = dp4a_u(w[i + 1], 0x01010101u, s1);
+              q1 = dp4a_u(w[i + 1], w[i + 1], q1);
+            }
+            s += s1;
+            q += q1;
+          } else if (words) {
+            const BinView bv{L.tile, t, gi * G, (int)gsz, pitch};
+            const int nw = (gsz + 3) >> 2;  // bytes past C in the tile are zero
+            for (int i = 0; i < nw; i++) {
+              const uint32_t x = bv.word(i);
+              s = dp4a_u(x, 0x01010101u, s);
+              q = dp4a_u(x, x, q);
+            }
+          } else {
+            const BinView bv{L.tile, t, gi * G, (int)gsz, pitch};
+            for (unsigned i = 0; i < gsz; i++) {
+              const unsigned x = bv.byte(i);
+              s += x;
+              q += x * x;
+            }
+          }
+          L.Sg[t * NBP + gi] = s;
+          v += fd_contrib(gi == NB - 1 ? ml : mf, gsz, s, q);
+        }
+      }
+      for (int o = 1; o < LPC; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (own && sl == 0) L.V[tcol] = v;
     }
-    __syncthreads();
+    __syncwarp();
 
     for (int it = 0; it < cut.iterations; it++) {
-      // ---- per-column keep half-widths
-      for (int t = threadIdx.x; t < ws; t += NT) {
-        const unsigned long long Vt = L.V[t];
-        L.A[2 * t] = max_keep(Vt, (unsigned long long)C * mf * mf, 255u * (unsigned)G, cut.k2);
-        L.A[2 * t + 1] = (Gl == G) ? L.A[2 * t]
-                                   : max_keep(Vt, (unsigned long long)C * ml * ml, 255u * (unsigned)Gl, cut.k2);
+      // per-column keep half-widths (8-lane candidate groups)
+      const unsigned long long Vt = own ? L.V[tcol] : 0ull;
+      const unsigned Af = max_keep_grp<8>(Vt, multF, own ? 255u * (unsigned)G : 0u, cut.k2);
+      const unsigned Al = (Gl == G) ? Af : max_keep_grp<8>(Vt, multL, own ? 255u * (unsigned)Gl : 0u, cut.k2);
+      if (own && sl == 0) {
+        L.A[2 * tcol] = Af;
+        L.A[2 * tcol + 1] = Al;
       }
-      __syncthreads();
-      // ---- pass B: find bins with a byte outside their keep interval
-      for (int p = threadIdx.x; p < npairs; p += NT) {
-        const int t = p % ws, gi = p / ws;
-        const bool lastbin = gi == NB - 1;
-        const unsigned gsz = lastbin ? (unsigned)Gl : (unsigned)G;
-        int lo, hi;
-        fd_keep(L.Sg[t * NB + gi], L.A[2 * t + (lastbin ? 1 : 0)], gsz, lo, hi);
-        bool any;
-        if (lo == 0 && hi == 255) {
-          any = false;
-        } else if (words) {
-          const ByteKeep kp = make_keep(lo, hi);
-          const uint32_t* w = reinterpret_cast<const uint32_t*>(L.tile + (size_t)t * pitch + gi * G);
-          const int nw = (gsz + 3) >> 2;
-          uint32_t acc = 0;
-          for (int i = 0; i < nw; i++) acc |= outside_fast(w[i], kp);
-          any = (acc & 0x80808080u) != 0;
-        } else {
-          any = false;
-          const uint8_t* rr = L.tile + (size_t)t * pitch + gi * G;
-          for (unsigned i = 0; i < gsz; i++) any |= (rr[i] < lo) | (rr[i] > hi);
+      if (lane == 0) *wcnt = 0;
+      __syncwarp();
+      // pass B: bins with a byte outside their keep interval
+      const int nsteps = (NB + LPC - 1) / LPC;
+      for (int stp = 0; stp < nsteps; stp++) {
+        const int gi = sl + stp * LPC;
+        bool any = false;
+        if (own && gi < NB) {
+          const bool lastbin = gi == NB - 1;
+          const unsigned gsz = lastbin ? (unsigned)Gl : (unsigned)G;
+          int lo, hi;
+          const unsigned S = L.Sg[tcol * NBP + gi];
+          if (fast32 && gsz == 32) {
+            const unsigned A = lastbin ? Al : Af;
+            lo = S <= A ? 0 : (int)((S - A + 31) >> 5);
+            const unsigned hv = (S + A) >> 5;
+            hi = hv > 255 ? 255 : (int)hv;
+          } else {
+            keep_from(S, lastbin ? Al : Af, gsz, lastbin ? rcpL : rcpG, lo, hi);
+          }
+          if (!(lo == 0 && hi == 255)) {
+            if (fast32 && gsz == 32) {
+              uint32_t w[8];
+              load_bin32(L.tile, tcol, gi, pitch, (sl >> 2) & 1, w);
+              const ByteKeep kp = make_keep(lo, hi);
+              uint32_t acc = 0;
+#pragma unroll
+              for (int i = 0; i < 8; i++) acc |= outside_fast(w[i], kp);
+              any = (acc & 0x80808080u) != 0;
+            } else if (words) {
+              const BinView bv{L.tile, tcol, gi * G, (int)gsz, pitch};
+              const ByteKeep kp = make_keep(lo, hi);
+              const int nw = (gsz + 3) >> 2;
+              uint32_t acc = 0;
+              for (int i = 0; i < nw; i++) acc |= outside_fast(bv.word(i), kp);
+              any = (acc & 0x80808080u) != 0;
+            } else {
+              const BinView bv{L.tile, tcol, gi * G, (int)gsz, pitch};
+              for (unsigned i = 0; i < gsz; i++) any |= ((int)bv.byte(i) < lo) | ((int)bv.byte(i) > hi);
+            }
+          }
         }
-        if (any) L.list[atomicAdd(L.cnt, 1u)] = (unsigned)p;
+        const unsigned b = __ballot_sync(0xffffffffu, any);
+        const unsigned n0 = *wcnt;
+        if (any) wlist[n0 + __popc(b & ((1u << lane) - 1u))] = (unsigned)(tcol * NB + gi);
+        __syncwarp();
+        if (lane == 0) *wcnt = n0 + __popc(b);
+        __syncwarp();
       }
-      __syncthreads();
-      const unsigned n = *L.cnt;
-      // ---- flagged bins: exact flags, replacement, statistics update
-      for (unsigned e = threadIdx.x; e < n; e += NT) {
-        const int p = (int)L.list[e];
-        const int t = p % ws, gi = p / ws;
+      const unsigned n = *wcnt;
+      // resolve the flagged bins of this warp's columns, one per lane
+      for (unsigned e = lane; e < n; e += 32) {
+        const int pair = (int)wlist[e];
+        const int t = pair / NB, gi = pair % NB;
         const bool lastbin = gi == NB - 1;
         const unsigned gsz = lastbin ? (unsigned)Gl : (unsigned)G;
-        const unsigned S = L.Sg[t * NB + gi];
+        const unsigned bit = 1u << (t0 + t - t_item);
+        const unsigned long long mm = lastbin ? ml : mf;
+        if (fast32 && gsz == 32) {
+          // the bin in registers: two 16-byte loads, half order staggered by lane
+          uint32_t w[8];
+          load_bin32(L.tile, t, gi, pitch, lane & 1, w);
+          unsigned s_old = 0, q_old = 0, s1 = 0, q1 = 0;
+#pragma unroll
+          for (int i = 0; i < 8; i += 2) {
+            s_old = dp4a_u(w[i], 0x01010101u, s_old);
+            q_old = dp4a_u(w[i], w[i], q_old);
+            s1 = dp4a_u(w[i + 1], 0x01010101u, s1);
+            q1 = dp4a_u(w[i + 1], w[i + 1], q1);
+          }
+          s_old += s1;
+          q_old += q1;
+          const unsigned A = L.A[2 * t + (lastbin ? 1 : 0)];
+          const int lo = s_old <= A ? 0 : (int)((s_old - A + 31) >> 5);
+          const unsigned hv = (s_old + A) >> 5;
+          const int hi = hv > 255 ? 255 : (int)hv;
+          unsigned r;
+          if (cut.replace == REP_MEDIAN) {
+            unsigned m = L.med[t * NBP + gi];
+            if (m == 0xFFFFu) {
+              // the lower median lies within one standard deviation of the bin mean
+              const float mu = (float)s_old * (1.0f / 32.0f);
+              const float var = (float)q_old * (1.0f / 32.0f) - mu * mu;
+              const float sd = sqrtf(var > 0.f ? var : 0.f);
+              m = median32_regs(w, max(0, (int)floorf(mu - sd) - 1), min(255, (int)ceilf(mu + sd) + 1));
+              L.med[t * NBP + gi] = (uint16_t)m;
+            }
+            r = m;
+          } else {
+            r = (s_old + 16) >> 5;  // floor((2 S + 32) / 64)
+          }
+          const ByteKeep kp = make_keep(lo, hi);
+          const uint32_t r4 = splat4(r);
+          unsigned s_new = 0, q_new = 0;
+          bool changed = false;
+#pragma unroll
+          for (int i = 0; i < 8; i++) {
+            const uint32_t f = outside_exact(w[i], kp);
+            const uint32_t y = w[i] ^ ((w[i] ^ r4) & ((f >> 7) * 0xFFu));
+            if (f) {
+              changed |= (y != w[i]);
+              uint32_t ff = f;
+              while (ff) {
+                const int byte = (__ffs(ff) - 1) >> 3;
+                ff &= ff - 1;
+                atomicOr(&L.fmask[gi * 32 + 4 * i + byte], bit);
+              }
+            }
+            w[i] = y;
+            s_new = dp4a_u(y, 0x01010101u, s_new);
+            q_new = dp4a_u(y, y, q_new);
+          }
+          if (changed) {
+            store_bin32(L.tile, t, gi, pitch, w);
+            L.Sg[t * NBP + gi] = s_new;
+            atomicAdd(&L.V[t], fd_contrib(mm, 32u, s_new, q_new) - fd_contrib(mm, 32u, s_old, q_old));
+          }
+          continue;
+        }
+        const unsigned S = L.Sg[t * NBP + gi];
+        const BinView bv{L.tile, t, gi * G, (int)gsz, pitch};
         int lo, hi;
-        fd_keep(S, L.A[2 * t + (lastbin ? 1 : 0)], gsz, lo, hi);
-        uint8_t* rr = L.tile + (size_t)t * pitch + gi * G;
+        keep_from(S, L.A[2 * t + (lastbin ? 1 : 0)], gsz, lastbin ? rcpL : rcpG, lo, hi);
         unsigned r;
         if (cut.replace == REP_MEDIAN) {
-          unsigned m = L.med[t * NB + gi];
+          unsigned m = L.med[t * NBP + gi];
           if (m == 0xFFFFu) {
-            m = bin_median(L.tile + (size_t)t * pitch, gi * G, gsz, words);
-            L.med[t * NB + gi] = (uint16_t)m;
+            int wlo = 0, whi = 255;
+            if (words) {
+              const int nw = (gsz + 3) >> 2;
+              unsigned q = 0;
+              for (int i = 0; i < nw; i++) q = dp4a_u(bv.word(i), bv.word(i), q);  // bytes past the bin are 0
+              const float mu = (float)S / (float)gsz;
+              float var = (float)q / (float)gsz - mu * mu;
+              const float sd = sqrtf(var > 0.f ? var : 0.f);
+              wlo = max(0, (int)floorf(mu - sd) - 1);
+              whi = min(255, (int)ceilf(mu + sd) + 1);
+            }
+            m = bin_median(bv, words, wlo, whi);
+            L.med[t * NBP + gi] = (uint16_t)m;
           }
           r = m;
         } else {
-          r = (2 * S + gsz) / (2 * gsz);
+          r = udiv_q(2 * S + gsz, 2 * gsz, 0.5f * (lastbin ? rcpL : rcpG));
         }
         unsigned s_old = 0, q_old = 0, s_new = 0, q_new = 0;
-        const unsigned bit = 1u << (t0 + t - t_item);
-        for (unsigned i = 0; i < gsz; i++) {
-          const unsigned x = rr[i];
-          s_old += x;
-          q_old += x * x;
-          unsigned y = x;
-          if ((int)x < lo || (int)x > hi) {
-            y = r;
-            rr[i] = (uint8_t)r;
-            atomicOr(&L.fmask[gi * G + i], bit);
+        if (words) {
+          const ByteKeep kp = make_keep(lo, hi);
+          const uint32_t r4 = splat4(r);
+          const int nw = (gsz + 3) >> 2;
+          for (int i = 0; i < nw; i++) {
+            const uint32_t x = bv.word(i);
+            uint32_t f = outside_exact(x, kp);
+            if (i == nw - 1 && (gsz & 3)) f &= (1u << (8 * (gsz & 3))) - 1u;  // bytes past the bin
+            s_old = dp4a_u(x, 0x01010101u, s_old);
+            q_old = dp4a_u(x, x, q_old);
+            const uint32_t y = sel_bytes(x, r4, f);
+            s_new = dp4a_u(y, 0x01010101u, s_new);
+            q_new = dp4a_u(y, y, q_new);
+            if (f) {
+              bv.word(i) = y;
+              uint32_t ff = f;
+              while (ff) {
+                const int byte = (__ffs(ff) - 1) >> 3;
+                ff &= ff - 1;
+                atomicOr(&L.fmask[gi * G + 4 * i + byte], bit);
+              }
+            }
           }
-          s_new += y;
-          q_new += y * y;
+        } else {
+          for (unsigned i = 0; i < gsz; i++) {
+            const unsigned x = bv.byte(i);
+            s_old += x;
+            q_old += x * x;
+            unsigned y = x;
+            if ((int)x < lo || (int)x > hi) {
+              y = r;
+              bv.byte(i) = (uint8_t)r;
+              atomicOr(&L.fmask[gi * G + i], bit);
+            }
+            s_new += y;
+            q_new += y * y;
+          }
         }
         if (s_new != s_old || q_new != q_old) {
-          const unsigned long long m = lastbin ? ml : mf;
-          L.Sg[t * NB + gi] = s_new;
-          atomicAdd(&L.V[t], fd_contrib(m, gsz, s_new, q_new) - fd_contrib(m, gsz, s_old, q_old));
+          L.Sg[t * NBP + gi] = s_new;
+          atomicAdd(&L.V[t], fd_contrib(mm, gsz, s_new, q_new) - fd_contrib(mm, gsz, s_old, q_old));
         }
       }
-      __syncthreads();
-      if (threadIdx.x == 0) *L.cnt = 0;
-      // the next iteration's first __syncthreads orders this reset before pass B
+      __syncwarp();
     }
     __syncthreads();
 
-    // ---- store the slab (transpose back to [c][t])
+    // ---- store: transpose back to [c][t], lanes along time
     for (int u = threadIdx.x; u < nq * nt4; u += NT) {
       const int tq = u % nt4, cq = u / nt4;
-      const int tt = 4 * tq;
+      const int c = 4 * cq, tt = 4 * tq;
       const int nv = min(4, ws - tt);
-      const uint8_t* trow = L.tile + (size_t)tt * pitch + 4 * cq;
-      uint32_t w0 = *reinterpret_cast<const uint32_t*>(trow);
-      uint32_t w1 = nv > 1 ? *reinterpret_cast<const uint32_t*>(trow + pitch) : 0u;
-      uint32_t w2 = nv > 2 ? *reinterpret_cast<const uint32_t*>(trow + 2 * pitch) : 0u;
-      uint32_t w3 = nv > 3 ? *reinterpret_cast<const uint32_t*>(trow + 3 * pitch) : 0u;
-      transpose4x4(w0, w1, w2, w3);
-      const int c = 4 * cq;
+      uint32_t a0 = *reinterpret_cast<const uint32_t*>(L.tile + toff(tt, c, pitch));
+      uint32_t a1 = nv > 1 ? *reinterpret_cast<const uint32_t*>(L.tile + toff(tt + 1, c, pitch)) : 0u;
+      uint32_t a2 = nv > 2 ? *reinterpret_cast<const uint32_t*>(L.tile + toff(tt + 2, c, pitch)) : 0u;
+      uint32_t a3 = nv > 3 ? *reinterpret_cast<const uint32_t*>(L.tile + toff(tt + 3, c, pitch)) : 0u;
+      transpose4x4(a0, a1, a2, a3);
       uint8_t* a = dst + (size_t)c * T + t0 + tt;
-      if (c + 0 < C) store4_any(a, w0, nv);
-      if (c + 1 < C) store4_any(a + T, w1, nv);
-      if (c + 2 < C) store4_any(a + 2 * (size_t)T, w2, nv);
-      if (c + 3 < C) store4_any(a + 3 * (size_t)T, w3, nv);
+      if (nv == 4 && c + 3 < C && out4) {
+        *reinterpret_cast<uint32_t*>(a) = a0;
+        *reinterpret_cast<uint32_t*>(a + T) = a1;
+        *reinterpret_cast<uint32_t*>(a + 2 * (size_t)T) = a2;
+        *reinterpret_cast<uint32_t*>(a + 3 * (size_t)T) = a3;
+      } else {
+        store4_row(a, a0, nv);
+        if (c + 1 < C) store4_row(a + T, a1, nv);
+        if (c + 2 < C) store4_row(a + 2 * (size_t)T, a2, nv);
+        if (c + 3 < C) store4_row(a + 3 * (size_t)T, a3, nv);
+      }
     }
     __syncthreads();
   }
@@ -649,7 +1156,7 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
 // ---------------------------------------------------------------------------
 // persistent engine
 // ---------------------------------------------------------------------------
-__device__ bool wait_rows(const Params& P, int job, unsigned need, int* bc) {
+__device__ bool wait_rows(const Params& P, int job, unsigned need, int* flag) {
   if (threadIdx.x == 0) {
     int good = 1;
     const unsigned* ctr = P.counters + 1 + job;
@@ -664,21 +1171,18 @@ __device__ bool wait_rows(const Params& P, int job, unsigned need, int* bc) {
         __nanosleep(128);
       }
     }
-    bc[3] = good;
+    *flag = good;
   }
   __syncthreads();
-  const bool ok = bc[3] != 0;
+  const bool ok = *flag != 0;
   __syncthreads();
   return ok;
 }
 
-template <int NCH>
-__global__ void __launch_bounds__(NT) k_engine_u8(const __grid_constant__ Params P) {
+__global__ void __launch_bounds__(NT, 2) k_engine_u8(const __grid_constant__ Params P) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ unsigned long long red64[2 * (NT / 32)];
-  __shared__ unsigned red32[4 * (NT / 32)];
-  __shared__ int bc[4];
-  __shared__ int s_item;
+  __shared__ unsigned long long scr[4 * (NT / 32)];
+  __shared__ int s_item, s_flag;
   for (;;) {
     if (threadIdx.x == 0) s_item = (int)atomicAdd(P.counters, 1u);
     __syncthreads();
@@ -695,58 +1199,55 @@ __global__ void __launch_bounds__(NT) k_engine_u8(const __grid_constant__ Params
     const int idx = item - sg.start;
     const Job& J = P.jobs[sg.job];
     if (sg.kind == 0) {
-      tdsc_row_u8<NCH>(P, J, idx, smem, red64, red32, bc);
+      unsigned done;
+      if (J.td_mode == 0) {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int row = idx * TD_ROWS_PER_ITEM + warp;
+        if (row < J.rows)
+          tdsc_row_u8<32>(P, J, row, reinterpret_cast<uint4*>(smem + warp * TD_WARP_STAGE), scr, lane);
+        const int left = J.rows - idx * TD_ROWS_PER_ITEM;
+        done = (unsigned)(left < TD_ROWS_PER_ITEM ? left : TD_ROWS_PER_ITEM);
+      } else {
+        tdsc_row_u8<NT>(P, J, idx, reinterpret_cast<uint4*>(smem), scr, threadIdx.x);
+        done = 1;
+      }
       __syncthreads();
       if (threadIdx.x == 0) {
         __threadfence();
-        if (sg.job != P.withhold_job) atomicAdd(P.counters + 1 + sg.job, 1u);
+        if (sg.job != P.withhold_job) atomicAdd(P.counters + 1 + sg.job, done);
       }
     } else {
-      if (P.wait_tdsc && !wait_rows(P, sg.job, (unsigned)J.rows, bc)) continue;
+      if (P.wait_tdsc && !wait_rows(P, sg.job, (unsigned)J.rows, &s_flag)) continue;
       fdsc_item_u8(P, J, idx, smem);
     }
   }
 }
 
 // ---------------------------------------------------------------------------
-// host-side helpers for this translation unit
+// host-side helpers
 // ---------------------------------------------------------------------------
-int engine_nch_for(int max_T) {
-  const int nch = (max_T + 30) / 16 + 1;  // worst-case head offset of 15
-  const int per = (nch + NT - 1) / NT;
-  if (per <= 1) return 1;
-  if (per <= 2) return 2;
-  if (per <= 4) return 4;
-  if (per <= 8) return 8;
-  if (per <= 16) return 16;
-  return -1;
-}
-
-int engine_smem_u8(const Params& p, int nch) {
-  int s = nch * NT * 2 + 16;  // TDSC: per-chunk flag bits
+int engine_smem_u8(const Params& p) {
+  int s = 16;
   for (int j = 0; j < p.n_jobs; j++) {
     const Job& J = p.jobs[j];
-    if (p.fd.iterations > 0) s = s > fd_smem_bytes(J.ws, J.pitch, J.nb, J.C) ? s : fd_smem_bytes(J.ws, J.pitch, J.nb, J.C);
+    if (p.td.iterations > 0) {
+      const int td = J.td_mode == 0 ? TD_WARP_STAGE * TD_ROWS_PER_ITEM : TD_CTA_CHUNKS * 16;
+      s = s > td ? s : td;
+    }
+    if (p.fd.iterations > 0) {
+      const int fd = fd_smem_bytes(J.ws, J.pitch, J.nb, J.C);
+      s = s > fd ? s : fd;
+    }
   }
   return align16i(s);
 }
 
-void* engine_kernel_u8(int nch) {
-  switch (nch) {
-    case 1: return (void*)k_engine_u8<1>;
-    case 2: return (void*)k_engine_u8<2>;
-    case 4: return (void*)k_engine_u8<4>;
-    case 8: return (void*)k_engine_u8<8>;
-    case 16: return (void*)k_engine_u8<16>;
-  }
-  return nullptr;
-}
+void* engine_kernel_u8() { return (void*)k_engine_u8; }
 
 int launch_engine_u8(const Params& p, const LaunchCfg& cfg, void* stream) {
-  void* fn = engine_kernel_u8(cfg.nch);
-  if (!fn) return (int)cudaErrorInvalidValue;
   void* args[] = {const_cast<Params*>(&p)};
-  return (int)cudaLaunchKernel(fn, dim3(cfg.grid), dim3(NT), args, (size_t)cfg.smem, (cudaStream_t)stream);
+  return (int)cudaLaunchKernel((void*)k_engine_u8, dim3(cfg.grid), dim3(NT), args, (size_t)cfg.smem,
+                               (cudaStream_t)stream);
 }
 
 }  // namespace rfim

@@ -163,7 +163,7 @@ def test_schedules_agree(oracle, ctx):
     want, wf = oracle.clean(x, "bct", tdsc=td, fdsc=fd)
     try:
         for opts in ({"schedule": 2}, {"schedule": 1, "fused_lag": 0}, {"schedule": 1, "fused_lag": 3},
-                     {"tile_samples": 8}, {"tile_samples": 4}, {"ctas_per_sm": 1}, {"smem_target": 40000}):
+                     {"tile_samples": 8}, {"tile_samples": 16}, {"ctas_per_sm": 1}, {"smem_target": 40000}):
             for k, v in opts.items():
                 ctx.set_option(k, v)
             got, gf = run_gpu(ctx, x, tdsc=td, fdsc=fd)
