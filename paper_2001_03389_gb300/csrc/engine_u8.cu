@@ -375,6 +375,36 @@ __device__ unsigned med_finish(MedSearch& m, const uint4* st, int nch, int T, un
   return (unsigned)m.lo;
 }
 
+// One statistics pass over a staged row (single-replacement mode): sums of the
+// kept samples, number of flagged samples and, with PROBE, the SAD sums of the
+// median probes.  Padding bytes of the edge chunks are 0; the caller corrects
+// the flagged count for them.
+template <int LANES, bool ODD, bool PROBE>
+__device__ __forceinline__ void td_stats_pass(const uint4* st, int nch, int gl, const ByteKeep& kp,
+                                              const uint32_t (&p4)[4], unsigned (&f32)[4], unsigned& s_in,
+                                              unsigned long long& q_in, unsigned& n_out) {
+  for (int k = gl; k < nch; k += LANES) {
+    const uint4 w = st[k];
+    if (PROBE) {
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        f32[i] = sad4(w.x, p4[i], f32[i]);
+        f32[i] = sad4(w.y, p4[i], f32[i]);
+        f32[i] = sad4(w.z, p4[i], f32[i]);
+        f32[i] = sad4(w.w, p4[i], f32[i]);
+      }
+    }
+    const uint32_t f0 = outside_ne<ODD>(w.x, kp), f1 = outside_ne<ODD>(w.y, kp);
+    const uint32_t f2 = outside_ne<ODD>(w.z, kp), f3 = outside_ne<ODD>(w.w, kp);
+    const uint32_t i0 = w.x & ~wide8(f0), i1 = w.y & ~wide8(f1);
+    const uint32_t i2 = w.z & ~wide8(f2), i3 = w.w & ~wide8(f3);
+    s_in += dp4a_u(i0, 0x01010101u, 0u) + dp4a_u(i1, 0x01010101u, 0u) + dp4a_u(i2, 0x01010101u, 0u) +
+            dp4a_u(i3, 0x01010101u, 0u);
+    q_in += dp4a_u(i0, i0, 0u) + dp4a_u(i1, i1, 0u) + dp4a_u(i2, i2, 0u) + dp4a_u(i3, i3, 0u);
+    n_out += (__popc(f0) + __popc(f1)) + (__popc(f2) + __popc(f3));
+  }
+}
+
 template <int LANES>
 __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, unsigned long long* scr, int gl) {
   const CutDev& cut = P.td;
@@ -391,30 +421,32 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
   g.nch = (g.head + T + 15) >> 4;
   g.tail = g.head + T - ((g.nch - 1) << 4);
 
-  // ---- pass 1: load (8 chunks in flight per lane), stage, S and Q
+  // ---- pass 1: stage the row with asynchronous copies (every chunk in flight at
+  //      once, no registers held), fix up the edge chunks, then S and Q
+  for (int k = gl; k < g.nch; k += LANES) {
+    const uint8_t* a = g.cb + 16 * k;
+    if (a >= blo && a + 16 <= bhi) {
+      const unsigned sdst = (unsigned)__cvta_generic_to_shared(st + k);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sdst), "l"(a) : "memory");
+    } else {
+      st[k] = load16_guarded(a, blo, bhi);
+    }
+  }
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+  grp_sync<LANES>();
   unsigned long long sq[2];
   {
     unsigned s = 0;
     unsigned long long q = 0;
-    for (int k0 = gl; k0 < g.nch; k0 += 8 * LANES) {
-      uint4 v[8];
-#pragma unroll
-      for (int u = 0; u < 8; u++) {
-        const int k = k0 + u * LANES;
-        if (k < g.nch) v[u] = load16_guarded(g.cb + 16 * k, blo, bhi);
+    for (int k = gl; k < g.nch; k += LANES) {
+      uint4 w = st[k];
+      if (k == 0 || k == g.nch - 1) {
+        w = and4(w, chunk_valid(g, k));
+        st[k] = w;
       }
-#pragma unroll
-      for (int u = 0; u < 8; u++) {
-        const int k = k0 + u * LANES;
-        if (k < g.nch) {
-          uint4 w = v[u];
-          if (k == 0 || k == g.nch - 1) w = and4(w, chunk_valid(g, k));
-          s = dp4a_u(w.x, 0x01010101u, s) + dp4a_u(w.y, 0x01010101u, 0u) + dp4a_u(w.z, 0x01010101u, 0u) +
-              dp4a_u(w.w, 0x01010101u, 0u);
-          q += dp4a_u(w.x, w.x, 0u) + dp4a_u(w.y, w.y, 0u) + dp4a_u(w.z, w.z, 0u) + dp4a_u(w.w, w.w, 0u);
-          st[k] = w;
-        }
-      }
+      s = dp4a_u(w.x, 0x01010101u, s) + dp4a_u(w.y, 0x01010101u, 0u) + dp4a_u(w.z, 0x01010101u, 0u) +
+          dp4a_u(w.w, 0x01010101u, 0u);
+      q += dp4a_u(w.x, w.x, 0u) + dp4a_u(w.y, w.y, 0u) + dp4a_u(w.z, w.z, 0u) + dp4a_u(w.w, w.w, 0u);
     }
     sq[0] = s;
     sq[1] = q;
@@ -456,28 +488,24 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
       unsigned f32[4] = {0, 0, 0, 0};
       unsigned s_in = 0, n_out = 0;
       unsigned long long q_in = 0;
-      for (int k = gl; k < g.nch; k += LANES) {
-        const uint4 w = st[k];
-        if (probe) {
-#pragma unroll
-          for (int i = 0; i < 4; i++) {
-            f32[i] = sad4(w.x, p4[i], f32[i]);
-            f32[i] = sad4(w.y, p4[i], f32[i]);
-            f32[i] = sad4(w.z, p4[i], f32[i]);
-            f32[i] = sad4(w.w, p4[i], f32[i]);
-          }
+      if (kp.all) {
+        // empty keep interval: every sample is flagged
+        if (probe) td_stats_pass<LANES, false, true>(st, g.nch, gl, make_keep(0, 255), p4, f32, s_in, q_in, n_out);
+        s_in = 0;
+        q_in = 0;
+        n_out = (gl == 0) ? (unsigned)T : 0u;
+      } else {
+        if (kp.odd) {
+          if (probe) td_stats_pass<LANES, true, true>(st, g.nch, gl, kp, p4, f32, s_in, q_in, n_out);
+          else td_stats_pass<LANES, true, false>(st, g.nch, gl, kp, p4, f32, s_in, q_in, n_out);
+        } else {
+          if (probe) td_stats_pass<LANES, false, true>(st, g.nch, gl, kp, p4, f32, s_in, q_in, n_out);
+          else td_stats_pass<LANES, false, false>(st, g.nch, gl, kp, p4, f32, s_in, q_in, n_out);
         }
-        uint4 f = outside4(w, kp);
-        if (k == 0 || k == g.nch - 1) f = and4(f, chunk_valid(g, k));
-        const uint32_t i0 = w.x & ~wide8(f.x), i1 = w.y & ~wide8(f.y);
-        const uint32_t i2 = w.z & ~wide8(f.z), i3 = w.w & ~wide8(f.w);
-        s_in += dp4a_u(i0, 0x01010101u, 0u) + dp4a_u(i1, 0x01010101u, 0u) + dp4a_u(i2, 0x01010101u, 0u) +
-                dp4a_u(i3, 0x01010101u, 0u);
-        q_in += dp4a_u(i0, i0, 0u) + dp4a_u(i1, i1, 0u) + dp4a_u(i2, i2, 0u) + dp4a_u(i3, i3, 0u);
-        n_out += __popc(f.x) + __popc(f.y) + __popc(f.z) + __popc(f.w);
       }
       unsigned long long red[7] = {s_in, q_in, n_out, f32[0], f32[1], f32[2], f32[3]};
       grp_sum<LANES, 7>(red, scr);
+      if (!kp.all && klo > 0) red[2] -= npad;  // the zero padding bytes were counted as flagged
       if (probe) {
         unsigned long long f[4] = {red[3], red[4], red[5], red[6]};
 #pragma unroll
@@ -538,11 +566,12 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
     uint32_t fb = 0;
       const uint4 w = st[k];
       const bool edge = (k == 0 || k == g.nch - 1);
-      const uint4 vm = edge ? chunk_valid(g, k) : make_uint4(~0u, ~0u, ~0u, ~0u);
+      const uint4 vm = (edge && !single) ? chunk_valid(g, k) : make_uint4(~0u, ~0u, ~0u, ~0u);
       uint4 y, f;
       if (single) {
+        // padding bytes of edge chunks are never stored and their flag bits fall
+        // outside the row's mask words, so no masking is needed here
         f = outside4(w, kk);
-        if (edge) f = and4(f, vm);
         y = make_uint4(sel8(w.x, rm4, wide8(f.x)), sel8(w.y, rm4, wide8(f.y)), sel8(w.z, rm4, wide8(f.z)),
                        sel8(w.w, rm4, wide8(f.w)));
       } else {
@@ -820,29 +849,49 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
   for (int t0 = t_item; t0 < t_end; t0 += Ws) {
     const int ws = min(Ws, t_end - t0);
     const int nt4 = (ws + 3) >> 2, nq = (C + 3) >> 2;
-    // ---- load: units of 4 channels x 4 samples, lanes along time, transposed into [t][c]
-    for (int u = threadIdx.x; u < nq * nt4; u += NT) {
-      const int tq = u % nt4, cq = u / nt4;
-      const int c = 4 * cq, tt = 4 * tq;
-      const int nv = min(4, ws - tt);
-      uint32_t a0, a1, a2, a3;
-      const uint8_t* a = src + (size_t)c * T + t0 + tt;
-      if (nv == 4 && c + 3 < C && rows4) {
-        a0 = *reinterpret_cast<const uint32_t*>(a);
-        a1 = *reinterpret_cast<const uint32_t*>(a + T);
-        a2 = *reinterpret_cast<const uint32_t*>(a + 2 * (size_t)T);
-        a3 = *reinterpret_cast<const uint32_t*>(a + 3 * (size_t)T);
-      } else {
-        a0 = load4_row(a, nv, blo, bhi);
-        a1 = c + 1 < C ? load4_row(a + T, nv, blo, bhi) : 0u;
-        a2 = c + 2 < C ? load4_row(a + 2 * (size_t)T, nv, blo, bhi) : 0u;
-        a3 = c + 3 < C ? load4_row(a + 3 * (size_t)T, nv, blo, bhi) : 0u;
+    // ---- load: units of 4 channels x 4 samples, lanes along time, transposed into [t][c];
+    //      four units per thread are in flight at a time
+    {
+      const int nunits = nq * nt4;
+      for (int ub = threadIdx.x; ub < nunits; ub += 4 * NT) {
+        uint32_t a[4][4];
+#pragma unroll
+        for (int kk = 0; kk < 4; kk++) {
+          const int u = ub + kk * NT;
+          if (u < nunits) {
+            const int tq = u % nt4, cq = u / nt4;
+            const int c = 4 * cq, tt = 4 * tq;
+            const int nv = min(4, ws - tt);
+            const uint8_t* ap = src + (size_t)c * T + t0 + tt;
+            if (nv == 4 && c + 3 < C && rows4) {
+              a[kk][0] = *reinterpret_cast<const uint32_t*>(ap);
+              a[kk][1] = *reinterpret_cast<const uint32_t*>(ap + T);
+              a[kk][2] = *reinterpret_cast<const uint32_t*>(ap + 2 * (size_t)T);
+              a[kk][3] = *reinterpret_cast<const uint32_t*>(ap + 3 * (size_t)T);
+            } else {
+              a[kk][0] = load4_row(ap, nv, blo, bhi);
+              a[kk][1] = c + 1 < C ? load4_row(ap + T, nv, blo, bhi) : 0u;
+              a[kk][2] = c + 2 < C ? load4_row(ap + 2 * (size_t)T, nv, blo, bhi) : 0u;
+              a[kk][3] = c + 3 < C ? load4_row(ap + 3 * (size_t)T, nv, blo, bhi) : 0u;
+            }
+          }
+        }
+#pragma unroll
+        for (int kk = 0; kk < 4; kk++) {
+          const int u = ub + kk * NT;
+          if (u < nunits) {
+            const int tq = u % nt4, cq = u / nt4;
+            const int c = 4 * cq, tt = 4 * tq;
+            const int nv = min(4, ws - tt);
+            uint32_t a0 = a[kk][0], a1 = a[kk][1], a2 = a[kk][2], a3 = a[kk][3];
+            transpose4x4(a0, a1, a2, a3);
+            *reinterpret_cast<uint32_t*>(L.tile + toff(tt, c, pitch)) = a0;
+            if (nv > 1) *reinterpret_cast<uint32_t*>(L.tile + toff(tt + 1, c, pitch)) = a1;
+            if (nv > 2) *reinterpret_cast<uint32_t*>(L.tile + toff(tt + 2, c, pitch)) = a2;
+            if (nv > 3) *reinterpret_cast<uint32_t*>(L.tile + toff(tt + 3, c, pitch)) = a3;
+          }
+        }
       }
-      transpose4x4(a0, a1, a2, a3);
-      *reinterpret_cast<uint32_t*>(L.tile + toff(tt, c, pitch)) = a0;
-      if (nv > 1) *reinterpret_cast<uint32_t*>(L.tile + toff(tt + 1, c, pitch)) = a1;
-      if (nv > 2) *reinterpret_cast<uint32_t*>(L.tile + toff(tt + 2, c, pitch)) = a2;
-      if (nv > 3) *reinterpret_cast<uint32_t*>(L.tile + toff(tt + 3, c, pitch)) = a3;
     }
     for (int i = threadIdx.x; i < Ws * NBP; i += NT) L.med[i] = 0xFFFFu;
     __syncthreads();
