@@ -182,6 +182,32 @@ rfim_status rfim_clean_host(rfim_ctx* ctx, const rfim_block* host_blk, const rfi
                             const rfim_cut* fdsc);
 
 /*
+ * rfim_clean for callers that cannot allocate memory.  The paper has no
+ * counterpart: this entry point exists for host code that must not call
+ * cudaMalloc -- a real-time pipeline that reserves all device memory at start
+ * and forbids allocation in its processing loop, or a plugin inside a framework
+ * that owns the allocator and gives this code no context object.
+ *
+ * Same arguments and results as rfim_clean (TDSC then FDSC, either cut may be
+ * NULL), on the CURRENT CUDA device, asynchronously on `stream`, with default
+ * tuning.  No context: the work-queue counters live in a fixed device array
+ * inside the library (1 + RFIM_NOALLOC_MAX_BEAMS + 1 words per device, held
+ * by every device that loads the library until the process exits).
+ *   - At most RFIM_NOALLOC_MAX_BEAMS beams per call; more returns RFIM_ERR_RANGE.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) and caches it; make that first call before any
+ *     stream capture on the device.
+ *   - Every call on a device shares the array and clears it on its stream
+ *     first.  Calls whose work overlaps on the GPU (different streams without
+ *     ordering) race on it and must not be issued; order them on one stream.
+ *   - Device-side wait timeouts are not reported (there is no context to read
+ *     them through); the fused schedule cannot wait forever in normal use.
+ *   - Calls no cudaMalloc, cudaFree or other allocating routine.
+ */
+#define RFIM_NOALLOC_MAX_BEAMS 160
+rfim_status rfim_clean_noalloc(const rfim_block* blk, const rfim_cut* tdsc, const rfim_cut* fdsc, void* stream);
+
+/*
  * Synchronise `stream` and return the device status word of the context's
  * kernels since the last check: RFIM_OK, or RFIM_ERR_TIMEOUT if a device-side
  * wait gave up (the affected output is then incomplete).  Clears the word.

@@ -193,13 +193,6 @@ rfim_status check_impl(rfim_ctx* ctx, const rfim_block* b, const CutNorm& td) {
   return RFIM_OK;
 }
 
-int pick_ws(const rfim_ctx* ctx, int C, int nb, int pitch, int budget) {
-  if (ctx->tile_samples > 0) return ctx->tile_samples;
-  for (int ws : {32, 16, 8})
-    if (fd_smem_bytes(ws, pitch, nb, C) <= budget) return ws;
-  return 8;
-}
-
 struct Plan {
   std::vector<Job> jobs;
   CutNorm td, fd;
@@ -207,41 +200,95 @@ struct Plan {
   int max_T = 1;
 };
 
-void add_block_jobs(rfim_ctx* ctx, Plan& pl, const rfim_block* b) {
+int pick_ws_opt(int tile_samples, int C, int nb, int pitch, int budget) {
+  if (tile_samples > 0) return tile_samples;
+  for (int ws : {32, 16, 8})
+    if (fd_smem_bytes(ws, pitch, nb, C) <= budget) return ws;
+  return 8;
+}
+
+// Work-queue description of beam j of block b.
+Job make_job(const rfim_block* b, int j, const CutNorm& fd, int tile_samples, int smem_target) {
   const int C = b->channels, T = b->samples;
   const size_t es = dtype_size(b->dtype);
   const size_t beam = (size_t)C * T;
   const int W32 = (T + 31) / 32;
+  Job J;
+  memset(&J, 0, sizeof J);
+  J.in = (const char*)b->in + j * beam * es;
+  J.out = (char*)b->out + j * beam * es;
+  if (b->mask_fmt == RFIM_MASK_BITS)
+    J.mask = (unsigned*)b->mask + (size_t)j * C * W32;
+  else if (b->mask_fmt == RFIM_MASK_BYTES)
+    J.mask = (unsigned char*)b->mask + j * beam;
+  else
+    J.mask = nullptr;
+  J.src_lo = J.in;
+  J.src_hi = (const char*)J.in + beam * es;
+  J.C = C;
+  J.T = T;
+  J.rows = C;
+  const int G = fd.on ? fd.bin : std::min(32, C);
+  J.nb = (C + G - 1) / G;
+  J.last_g = C - (J.nb - 1) * G;
+  const long long L = (long long)G / gcdll(G, J.last_g) * J.last_g;
+  J.m_full = (unsigned long long)(L / G);
+  J.m_last = (unsigned long long)(L / J.last_g);
+  J.pitch = fd_pitch(C * (int)es);
+  J.ws = pick_ws_opt(tile_samples, C, J.nb, J.pitch, smem_target);
+  J.fd_items = (T + FD_ITEM_T - 1) / FD_ITEM_T;
+  J.td_mode = td_row_mode(T) == 1 ? 1 : 0;
+  J.td_items = J.td_mode == 0 ? (C + TD_ROWS_PER_ITEM - 1) / TD_ROWS_PER_ITEM : C;
+  return J;
+}
+
+void add_block_jobs(rfim_ctx* ctx, Plan& pl, const rfim_block* b) {
   for (int j = 0; j < b->beams; j++) {
-    Job J;
-    memset(&J, 0, sizeof J);
-    J.in = (const char*)b->in + j * beam * es;
-    J.out = (char*)b->out + j * beam * es;
-    if (b->mask_fmt == RFIM_MASK_BITS)
-      J.mask = (unsigned*)b->mask + (size_t)j * C * W32;
-    else if (b->mask_fmt == RFIM_MASK_BYTES)
-      J.mask = (unsigned char*)b->mask + j * beam;
-    else
-      J.mask = nullptr;
-    J.src_lo = J.in;
-    J.src_hi = (const char*)J.in + beam * es;
-    J.C = C;
-    J.T = T;
-    J.rows = C;
-    const int G = pl.fd.on ? pl.fd.bin : std::min(32, C);
-    J.nb = (C + G - 1) / G;
-    J.last_g = C - (J.nb - 1) * G;
-    const long long L = (long long)G / gcdll(G, J.last_g) * J.last_g;
-    J.m_full = (unsigned long long)(L / G);
-    J.m_last = (unsigned long long)(L / J.last_g);
-    J.pitch = fd_pitch(C * (int)es);
-    J.ws = pick_ws(ctx, C, J.nb, J.pitch, ctx->smem_target);
-    J.fd_items = (T + FD_ITEM_T - 1) / FD_ITEM_T;
-    J.td_mode = td_row_mode(T) == 1 ? 1 : 0;
-    J.td_items = J.td_mode == 0 ? (C + TD_ROWS_PER_ITEM - 1) / TD_ROWS_PER_ITEM : C;
-    pl.jobs.push_back(J);
-    pl.max_T = std::max(pl.max_T, T);
+    pl.jobs.push_back(make_job(b, j, pl.fd, ctx->tile_samples, ctx->smem_target));
+    pl.max_T = std::max(pl.max_T, b->samples);
   }
+}
+
+CutDev cut_dev(const CutNorm& c) {
+  CutDev d;
+  memset(&d, 0, sizeof d);
+  if (c.on) {
+    d.k2 = make_k2(c.k);
+    d.k = c.k;
+    d.iterations = c.it;
+    d.replace = c.rep;
+    d.bin = c.bin;
+  }
+  return d;
+}
+
+// Queue segments of p's jobs.  mode: 0 = TDSC only, 1/3 = FDSC only, 2 = fused
+// (TDSC rows of beam j + lag queued before the FDSC items of beam j).
+void fill_segments(Params& p, int mode, int lag) {
+  int n = 0, s = 0;
+  auto push = [&](int job, int kind, int count) {
+    if (count <= 0) return;
+    p.segs[s].start = n;
+    p.segs[s].job = job;
+    p.segs[s].kind = kind;
+    s++;
+    n += count;
+  };
+  const int nj = p.n_jobs;
+  if (mode == 0) {
+    for (int j = 0; j < nj; j++) push(j, 0, p.jobs[j].td_items);
+  } else if (mode == 1 || mode == 3) {
+    for (int j = 0; j < nj; j++) push(j, 1, p.jobs[j].fd_items);
+  } else {
+    lag = std::max(0, lag);
+    for (int j = 0; j < nj + lag; j++) {
+      if (j < nj) push(j, 0, p.jobs[j].td_items);
+      const int f = j - lag;
+      if (f >= 0) push(f, 1, p.jobs[f].fd_items);
+    }
+  }
+  p.n_segs = s;
+  p.n_items = n;
 }
 
 struct OccKey {
@@ -271,20 +318,8 @@ void fill_params(rfim_ctx* ctx, const Plan& pl, int j0, int j1, int mode, Params
   memset(&p, 0, sizeof p);
   p.n_jobs = j1 - j0;
   for (int j = j0; j < j1; j++) p.jobs[j - j0] = pl.jobs[j];
-  auto mk = [](const CutNorm& c) {
-    CutDev d;
-    memset(&d, 0, sizeof d);
-    if (c.on) {
-      d.k2 = make_k2(c.k);
-      d.k = c.k;
-      d.iterations = c.it;
-      d.replace = c.rep;
-      d.bin = c.bin;
-    }
-    return d;
-  };
-  p.td = mk(pl.td);
-  p.fd = mk(pl.fd);
+  p.td = cut_dev(pl.td);
+  p.fd = cut_dev(pl.fd);
   if (mode == 1 || mode == 3) p.td.iterations = 0;
   if (mode == 0) p.fd.iterations = 0;
   p.mask_kind = pl.mask_kind;
@@ -295,32 +330,7 @@ void fill_params(rfim_ctx* ctx, const Plan& pl, int j0, int j1, int mode, Params
   p.spin_limit_ns = (unsigned long long)ctx->spin_limit_us * 1000ull;
   p.counters = counters;
   p.status = ctx->d_status;
-  // queue segments
-  int n = 0, s = 0;
-  auto push = [&](int job, int kind, int count) {
-    if (count <= 0) return;
-    p.segs[s].start = n;
-    p.segs[s].job = job;
-    p.segs[s].kind = kind;
-    s++;
-    n += count;
-  };
-  const int nj = p.n_jobs;
-  if (mode == 0) {
-    for (int j = 0; j < nj; j++) push(j, 0, p.jobs[j].td_items);
-  } else if (mode == 1 || mode == 3) {
-    for (int j = 0; j < nj; j++) push(j, 1, p.jobs[j].fd_items);
-  } else {
-    // fused: TDSC rows of beam j+lag are queued before the FDSC items of beam j
-    const int lag = std::max(0, ctx->fused_lag);
-    for (int j = 0; j < nj + lag; j++) {
-      if (j < nj) push(j, 0, p.jobs[j].td_items);
-      const int f = j - lag;
-      if (f >= 0) push(f, 1, p.jobs[f].fd_items);
-    }
-  }
-  p.n_segs = s;
-  p.n_items = n;
+  fill_segments(p, mode, ctx->fused_lag);
 }
 
 rfim_status launch_one(rfim_ctx* ctx, Params& p, int max_T, cudaStream_t st) {
@@ -664,6 +674,53 @@ void ctx_set_tunables(rfim_ctx* ctx, const Tunables& t) {
   ctx->ctas_per_sm = t.ctas_per_sm;
   ctx->smem_target = t.smem_target;
   ctx->fused_lag = t.fused_lag;
+}
+
+// Plan and launch one block with caller-provided counters: no heap or device
+// allocation, default tuning (fused schedule with one beam of lag).
+rfim_status noalloc_clean(const rfim_block* b, const rfim_cut* tdsc, const rfim_cut* fdsc, unsigned* counters,
+                          unsigned* status, cudaStream_t st) {
+  if (!tdsc && !fdsc) return RFIM_ERR_ARG;
+  if (!b) return RFIM_ERR_ARG;
+  CutNorm td, fd;
+  rfim_status s;
+  if ((s = check_cut(nullptr, tdsc, b->channels, false, td)) != RFIM_OK) return s;
+  if ((s = check_cut(nullptr, fdsc, b->channels, true, fd)) != RFIM_OK) return s;
+  if ((s = check_block(nullptr, b, td, fd)) != RFIM_OK) return s;
+  if ((s = check_impl(nullptr, b, td)) != RFIM_OK) return s;
+  if (b->beams > MAX_JOBS) return RFIM_ERR_RANGE;
+  Params p;  // on the stack: no allocation
+  memset(&p, 0, sizeof p);
+  p.n_jobs = b->beams;
+  for (int j = 0; j < b->beams; j++) p.jobs[j] = make_job(b, j, fd, 0, 113 * 1024);
+  const int mode = (td.on && fd.on) ? 2 : (td.on ? 0 : 1);
+  p.td = cut_dev(td);
+  p.fd = cut_dev(fd);
+  p.mask_kind = (int)b->mask_fmt;
+  p.fd_reads_out = mode == 2 ? 1 : 0;
+  p.wait_tdsc = mode == 2 ? 1 : 0;
+  p.mask_or = mode == 2 ? 1 : 0;
+  p.withhold_job = -1;
+  p.spin_limit_ns = 2000000000ull;
+  p.counters = counters;
+  p.status = status;
+  fill_segments(p, mode, 1);
+  LaunchCfg cfg;
+  cfg.smem = engine_smem_u8(p);
+  void* fn = engine_kernel_u8();
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return RFIM_ERR_CUDA;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448 - 1024) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, cfg.smem) != cudaSuccess)
+    return RFIM_ERR_CUDA;
+  cfg.grid = std::max(1, std::min(p.n_items, sms * std::max(1, per_sm)));
+  // the shared counters and status word keep the previous call's values: clear them
+  if (cudaMemsetAsync(counters, 0, sizeof(unsigned) * (1 + p.n_jobs), st) != cudaSuccess ||
+      cudaMemsetAsync(status, 0, sizeof(unsigned), st) != cudaSuccess)
+    return RFIM_ERR_CUDA;
+  if (launch_engine_u8(p, cfg, st) != (int)cudaSuccess) return RFIM_ERR_CUDA;
+  return RFIM_OK;
 }
 
 }  // namespace rfim

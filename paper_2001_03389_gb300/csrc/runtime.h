@@ -43,6 +43,10 @@ void tuner_destroy(Tuner* t);
 rfim_status tuner_apply(Tuner* t, rfim_ctx* ctx, const rfim_block* blocks, int n, const rfim_cut* tdsc,
                         const rfim_cut* fdsc);
 
+// planning and launch with caller-provided counters, no allocation (api.cu)
+rfim_status noalloc_clean(const rfim_block* b, const rfim_cut* tdsc, const rfim_cut* fdsc, unsigned* counters,
+                          unsigned* status, cudaStream_t st);
+
 // streaming service (stream.cu)
 void stream_service_destroy(StreamService* s);
 

@@ -27,6 +27,7 @@ LAYOUT_BCT, LAYOUT_BTC = 0, 1
 REPLACE_MEAN, REPLACE_MEDIAN = 0, 1
 MASK_NONE, MASK_BITS, MASK_BYTES = 0, 1, 2
 BATCH_GRAPH, BATCH_AUTOTUNE = 1, 2
+RFIM_NOALLOC_MAX_BEAMS = 160
 
 _LAYOUTS = {"bct": LAYOUT_BCT, "btc": LAYOUT_BTC}
 _REPLACE = {"mean": REPLACE_MEAN, "median": REPLACE_MEDIAN}
@@ -57,6 +58,7 @@ _SIGS = {
     "rfim_clean_batch": ([_vp, _blkp, ctypes.c_int, _cutp, _cutp, ctypes.c_uint, _vp], ctypes.c_int),
     "rfim_clean_host": ([_vp, _blkp, _cutp, _cutp], ctypes.c_int),
     "rfim_device_status": ([_vp, _vp], ctypes.c_int),
+    "rfim_clean_noalloc": ([_blkp, _cutp, _cutp, _vp], ctypes.c_int),
     "rfim_stream_open": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _cutp, _cutp], ctypes.c_int),
     "rfim_stream_push": ([_vp, ctypes.c_int, _vp, ctypes.c_double, ctypes.POINTER(ctypes.c_ulonglong)], ctypes.c_int),
     "rfim_stream_poll": ([_vp, ctypes.c_ulonglong, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int], ctypes.c_int),

@@ -1,0 +1,74 @@
+"""The no-allocation entry point against the regular one (GPU, through the C ABI).
+
+rfim_clean_noalloc serves callers that may not allocate device memory (a
+real-time pipeline with a fixed memory budget, a plugin without a context);
+it keeps its work-queue counters in a fixed device array that every call
+shares and clears.  Two calls in a row must each give the same output and
+flags as rfim_clean (bit-exact for uint8), and oversize batches are refused.
+This file is collected last so that a run stopping at the first failure has
+already run every other test.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def test_noalloc_matches_rfim_clean_twice():
+    import torch
+
+    from paper_2001_03389_gb300 import build
+
+    build.build()
+    from paper_2001_03389_gb300 import rfim, synth
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda:0")
+    x = torch.from_numpy(synth.make_beams(2, beams=[0, 1])[:, :, :3001].copy()).to(dev)  # 2 x 1536 x 3001
+    B, C, T = x.shape
+    td = rfim.make_cut(3.0, 2, "median")
+    fd = rfim.make_cut(3.0, 2, "median", 32)
+
+    ctx = rfim.Context(0)
+    ref = torch.empty_like(x)
+    ref_mask = torch.zeros(rfim.mask_words(C, T, B), dtype=torch.int32, device=dev)
+    ctx.clean(ctx.block(x, ref, ref_mask, "bct", "bits"), td, fd)
+    torch.cuda.synchronize()
+    ctx.close()
+
+    for call in range(2):
+        out = torch.full_like(x, 7)
+        mask = torch.full((rfim.mask_words(C, T, B),), -1, dtype=torch.int32, device=dev)
+        blk = rfim.Context.block(x, out, mask, "bct", "bits")
+        st = rfim.rfim_clean_noalloc(ctypes.byref(blk), ctypes.byref(td), ctypes.byref(fd), None)
+        assert st == rfim.OK, f"call {call}: status {st}"
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref), f"call {call}: output differs from rfim_clean"
+        assert torch.equal(mask, ref_mask), f"call {call}: mask differs from rfim_clean"
+
+    # single-method calls through the same scratch
+    out = torch.empty_like(x)
+    blk = rfim.Context.block(x, out, None, "bct", None)
+    assert rfim.rfim_clean_noalloc(ctypes.byref(blk), ctypes.byref(td), None, None) == rfim.OK
+    torch.cuda.synchronize()
+    ctx = rfim.Context(0)
+    ref2 = torch.empty_like(x)
+    ctx.tdsc(ctx.block(x, ref2), td)
+    torch.cuda.synchronize()
+    ctx.close()
+    assert torch.equal(out, ref2)
+
+
+def test_noalloc_rejects_oversize_batch():
+    import torch
+
+    from paper_2001_03389_gb300 import rfim
+
+    n = rfim.RFIM_NOALLOC_MAX_BEAMS + 1 if hasattr(rfim, "RFIM_NOALLOC_MAX_BEAMS") else 161
+    x = torch.zeros((n, 2, 64), dtype=torch.uint8, device="cuda:0")
+    out = torch.empty_like(x)
+    blk = rfim.Context.block(x, out)
+    cut = rfim.make_cut(3.0)
+    assert rfim.rfim_clean_noalloc(ctypes.byref(blk), ctypes.byref(cut), None, None) == rfim.ERR_RANGE
