@@ -314,7 +314,7 @@ def run_gpu(args):
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": f"{peak_kind} copy (MEASURED_PEAKS.json hbm_gbs)",
                          "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS,
-                         "kernel": "k_engine_u8<4> (fused TDSC->FDSC persistent work queue)",
+                         "kernel": "k_engine_u8 (fused TDSC->FDSC persistent work queue)",
                          "alg_bytes_per_launch": alg, "avg_launch_ms": avg_launch_ms},
             "e2e": e2e, "e2e_matches_device": ok,
             "gpu_launches": K,
@@ -352,12 +352,16 @@ def profiled_traffic():
         return None
 
 
+ENGINE_SOURCES = ("common.cuh", "engine.h", "engine_u8.cu")
+
+
 def source_hash():
+    """Hash of the sources the engine kernel is compiled from."""
     import hashlib
 
     h = hashlib.sha256()
     cs = os.path.join(ROOT, "paper_2001_03389_gb300", "csrc")
-    for f in sorted(os.listdir(cs)):
+    for f in ENGINE_SOURCES:
         with open(os.path.join(cs, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -185,11 +185,17 @@ rfim_status check_block(rfim_ctx* ctx, const rfim_block* b, const CutNorm& td, c
 }
 
 // Engine limits of this build.
-rfim_status check_impl(rfim_ctx* ctx, const rfim_block* b, const CutNorm& td) {
+rfim_status check_impl(rfim_ctx* ctx, const rfim_block* b, const CutNorm& td, const CutNorm& fd) {
   if (b->dtype != RFIM_U8) return fail(ctx, RFIM_ERR_ARG, "float32 blocks are not available in this build");
   if (b->layout != RFIM_LAYOUT_BCT) return fail(ctx, RFIM_ERR_ARG, "BTC layout is not available in this build");
   if (td.on && td_row_mode(b->samples) < 0)
-    return fail(ctx, RFIM_ERR_ARG, "TDSC rows longer than 98274 samples are not available in this build");
+    return fail(ctx, RFIM_ERR_ARG, "TDSC rows longer than 98273 samples are not available in this build");
+  if (fd.on) {
+    // the smallest FDSC tile (8 samples x all channels) must fit one CTA's shared memory
+    const int C = b->channels, nb = (C + fd.bin - 1) / fd.bin;
+    if (fd_smem_bytes(8, fd_pitch(C), nb, C) > MAX_SMEM_PER_CTA)
+      return fail(ctx, RFIM_ERR_RANGE, "FDSC: %d channels do not fit the on-chip tile", C);
+  }
   return RFIM_OK;
 }
 
@@ -337,7 +343,7 @@ rfim_status launch_one(rfim_ctx* ctx, Params& p, int max_T, cudaStream_t st) {
   (void)max_T;
   LaunchCfg cfg;
   cfg.smem = engine_smem_u8(p);
-  if (cfg.smem > 232448 - 2048) return fail(ctx, RFIM_ERR_ARG, "tile does not fit in shared memory (%d bytes)", cfg.smem);
+  if (cfg.smem > MAX_SMEM_PER_CTA) return fail(ctx, RFIM_ERR_ARG, "tile does not fit in shared memory (%d bytes)", cfg.smem);
   void* fn = engine_kernel_u8();
   int per_sm = occupancy(fn, cfg.smem);
   if (ctx->ctas_per_sm > 0) per_sm = std::min(per_sm, ctx->ctas_per_sm);
@@ -396,7 +402,7 @@ rfim_status make_plan(rfim_ctx* ctx, const rfim_block* blocks, int n, const rfim
     if ((s = check_cut(ctx, tdsc, b->channels, false, td)) != RFIM_OK) return s;
     if ((s = check_cut(ctx, fdsc, b->channels, true, fd)) != RFIM_OK) return s;
     if ((s = check_block(ctx, b, td, fd)) != RFIM_OK) return s;
-    if ((s = check_impl(ctx, b, td)) != RFIM_OK) return s;
+    if ((s = check_impl(ctx, b, td, fd)) != RFIM_OK) return s;
     if (i == 0) {
       pl.td = td;
       pl.fd = fd;
@@ -687,7 +693,7 @@ rfim_status noalloc_clean(const rfim_block* b, const rfim_cut* tdsc, const rfim_
   if ((s = check_cut(nullptr, tdsc, b->channels, false, td)) != RFIM_OK) return s;
   if ((s = check_cut(nullptr, fdsc, b->channels, true, fd)) != RFIM_OK) return s;
   if ((s = check_block(nullptr, b, td, fd)) != RFIM_OK) return s;
-  if ((s = check_impl(nullptr, b, td)) != RFIM_OK) return s;
+  if ((s = check_impl(nullptr, b, td, fd)) != RFIM_OK) return s;
   if (b->beams > MAX_JOBS) return RFIM_ERR_RANGE;
   Params p;  // on the stack: no allocation
   memset(&p, 0, sizeof p);

@@ -86,6 +86,10 @@ __host__ __device__ inline int fd_pitch(int C_bytes) { return ((C_bytes + 127) /
 // TDSC row staging: a warp stages rows of up to TD_WARP_CHUNKS 16-byte chunks
 // (8 warps share TD_WARP_STAGE * 8 bytes); longer rows, up to TD_CTA_CHUNKS
 // chunks, are staged and processed by the whole CTA.
+// Dynamic shared memory one CTA of the engine may use (227 KB opt-in on sm_103a,
+// less 2 KB kept for the kernel's static shared variables).
+constexpr int MAX_SMEM_PER_CTA = 232448 - 2048;
+
 constexpr int TD_WARP_CHUNKS = 800;
 constexpr int TD_WARP_STAGE = TD_WARP_CHUNKS * 16;
 constexpr int TD_CTA_CHUNKS = 6144;

@@ -237,8 +237,11 @@ __device__ __forceinline__ uint32_t chunk_bits(const uint4& f) {
 // ---------------------------------------------------------------------------
 // group reductions: LANES = 32 (one warp per row) or NT (the CTA)
 // ---------------------------------------------------------------------------
+constexpr int GRP_SUM_MAX = 8;  // values one grp_sum may reduce (scratch: GRP_SUM_MAX * NT/32 words)
+
 template <int LANES, int N>
 __device__ __forceinline__ void grp_sum(unsigned long long (&v)[N], unsigned long long* scr) {
+  static_assert(N <= GRP_SUM_MAX, "grp_sum scratch holds GRP_SUM_MAX values per warp");
 #pragma unroll
   for (int i = 0; i < N; i++) v[i] = warp_sum(v[i]);
   if (LANES == 32) return;
@@ -1230,7 +1233,7 @@ __device__ bool wait_rows(const Params& P, int job, unsigned need, int* flag) {
 
 __global__ void __launch_bounds__(NT, 2) k_engine_u8(const __grid_constant__ Params P) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ unsigned long long scr[4 * (NT / 32)];
+  __shared__ unsigned long long scr[GRP_SUM_MAX * (NT / 32)];
   __shared__ int s_item, s_flag;
   for (;;) {
     if (threadIdx.x == 0) s_item = (int)atomicAdd(P.counters, 1u);

@@ -178,3 +178,56 @@ def stream_chunk(beam: int, chunk: int, C: int = 1536, T: int = 1250) -> np.ndar
     """Chunk `chunk` of streaming beam `beam` (config-2 model), shape (C, T)."""
     rng_seed = seed_of(5) * 1_000_003 + beam
     return beam_u8(rng_seed, chunk, C, T, cfg2_model())
+
+
+# ---------------------------------------------------------------------------
+# On-device generation for the multi-gigabyte workloads (ragged batch,
+# streaming): the same noise and RFI model, drawn with a seeded torch CUDA
+# generator so that gigabytes need not be produced on the host.  (Different
+# numbers than the numpy recipe above; results are checked against the CPU
+# oracle on copies of these bytes.)
+# ---------------------------------------------------------------------------
+
+def torch_beam_u8(gen, C: int, T: int, model: RFIModel, device):
+    """One uint8 beam (C, T) on `device`: round(N(128, 16^2) + RFI) clipped."""
+    import math
+
+    import torch
+
+    x = torch.randn((C, T), generator=gen, device=device, dtype=torch.float32)
+    x.mul_(16.0).add_(128.0)
+    n_nb = model.nb_count if model.nb_count is not None else int(round(model.nb_frac * C))
+    if n_nb > 0:
+        chans = torch.randperm(C, generator=gen, device=device)[:n_nb]
+        t = torch.arange(T, device=device, dtype=torch.float32)
+        if model.nb_sine:
+            P = 500.0 + 4500.0 * torch.rand((n_nb, 1), generator=gen, device=device)
+            phi = 2 * math.pi * torch.rand((n_nb, 1), generator=gen, device=device)
+            x[chans] += model.nb_amp * (1.0 + 0.5 * torch.sin(2 * math.pi * t[None, :] / P + phi))
+        else:
+            x[chans] += model.nb_amp
+    n_bb = model.bb_count if model.bb_count is not None else int(round(model.bb_frac * T / max(model.bb_width, 1)))
+    if n_bb > 0:
+        starts = torch.randperm(max(T - model.bb_width + 1, 1), generator=gen, device=device)[:n_bb]
+        for w in range(model.bb_width):
+            x[:, starts + w] += model.bb_amp
+    if model.disp_amp:
+        t0 = int(torch.randint(0, max(T // 2, 1), (1,), generator=gen, device=device).item())
+        delays = torch.from_numpy(_dispersion_delays(C, model.disp_span)).to(device)
+        ts = t0 + delays
+        ok = ts < T
+        x[torch.arange(C, device=device)[ok], ts[ok]] += model.disp_amp
+    return x.round_().clamp_(0, 255).to(torch.uint8)
+
+
+def torch_ragged_batch(shapes, seed: int, device, layout: str = "bct"):
+    """Beams of the given (C, T) shapes, config-2 model, as separate device tensors."""
+    import torch
+
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    out = []
+    for C, T in shapes:
+        b = torch_beam_u8(gen, C, T, cfg2_model(), device)
+        out.append(b.t().contiguous() if layout == "btc" else b)
+    return out

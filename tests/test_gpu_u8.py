@@ -48,7 +48,7 @@ def test_cfg1_paper_canvas(oracle, ctx):
 
 
 @pytest.mark.parametrize("C,T", [(1, 1), (1, 33), (3, 5), (7, 31), (37, 32), (64, 100), (100, 257), (130, 1000),
-                                 (33, 4099), (5, 12500)])
+                                 (33, 4099), (5, 12500), (3, 12769), (3, 12770), (2, 25000), (1, 98273)])
 @pytest.mark.parametrize("rep", ["mean", "median"])
 def test_tdsc_shapes(oracle, ctx, C, T, rep):
     rng = np.random.default_rng(C * 1000 + T)
@@ -200,6 +200,10 @@ def test_validation_errors(ctx):
     with pytest.raises(rfim.RfimError) as e:
         ctx.tdsc(blk2, rfim.make_cut(3.0))
     assert e.value.status == rfim.ERR_ARG  # partial overlap of out and in
+    row = torch.zeros((1, 1, 98274), dtype=torch.uint8, device="cuda:0")
+    with pytest.raises(rfim.RfimError) as e:
+        ctx.tdsc(ctx.block(row, torch.empty_like(row)), rfim.make_cut(3.0))
+    assert e.value.status == rfim.ERR_ARG  # longer than the on-chip row stage
     long_row = torch.zeros((1, 1, 372200), dtype=torch.uint8, device="cuda:0")
     with pytest.raises(rfim.RfimError) as e:
         ctx.tdsc(ctx.block(long_row, torch.empty_like(long_row)), rfim.make_cut(3.0))
