@@ -143,16 +143,22 @@ def oracle_time_sample(x_beam, spec, T_sample):
 
 
 def cpu_baseline(spec, budget_s=15.0):
+    """The oracle on whole beams of the batch, one after another, until about
+    `budget_s` seconds of CPU work (single-threaded)."""
+    from oracle import oracle
     from paper_2001_03389_gb300 import synth
 
-    x = synth.make_beams(CFG, beams=[0])
-    t_small, b_small = oracle_time_sample(x, spec, 256)
-    rate = b_small / t_small
-    T_s = int(min(spec["T"], max(256, rate * budget_s / spec["C"])))
-    dt, nbytes = oracle_time_sample(x, spec, T_s)
-    return {"value": nbytes / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"1 beam x {spec['C']} channels x {T_s} of {spec['T']} samples, full TDSC+FDSC, "
-                      f"single-threaded C oracle, {dt:.1f} s"}
+    tot_t, tot_b, nb = 0.0, 0, 0
+    while nb < spec["B"] and tot_t < budget_s:
+        x = synth.make_beams(CFG, beams=[nb])
+        t0 = time.perf_counter()
+        oracle.clean(x, "bct", tdsc=spec["tdsc"], fdsc=spec["fdsc"])
+        tot_t += time.perf_counter() - t0
+        tot_b += x.nbytes
+        nb += 1
+    return {"value": tot_b / tot_t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{nb} of {spec['B']} beams x {spec['C']} channels x {spec['T']} samples, full TDSC+FDSC, "
+                      f"single-threaded C oracle, {tot_t:.1f} s"}
 
 
 def run_reference(args):
