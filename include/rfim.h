@@ -27,6 +27,13 @@
  *     FDSC flags iff (double)(C D^2) > fl(k2 * (double)sum D^2),
  *       D = (L / G_g)(G_g x - S_g), L = lcm of the bin sizes,
  *     where k2 = fl(k * k) and fl() is one IEEE double rounding;
+ *   - float32 decisions are those of the IEEE double expression
+ *       fabs((double)x - mu) > k * sigma,   sigma = sqrt(sum (x - mu)^2 / n)
+ *     (FDSC: x - mu replaced by the deviation from the bin mean, whose mean
+ *     over the channels is 0); the library takes its sums in compensated
+ *     float32 arithmetic and evaluates samples near the threshold in double,
+ *     so it agrees with a plain double evaluation except for samples within
+ *     about 1e-12 relative of k sigma.  float32 input must be finite;
  *   - uint8 mean replacement rounds half up, floor((2S + n) / (2n));
  *     float32 mean replacement is (float) of the double mean;
  *   - the median is the lower median (rank floor((n-1)/2), 0-based) of the
@@ -131,7 +138,8 @@ rfim_status rfim_destroy(rfim_ctx* ctx);
  *   "spin_limit_us"   limit of every device-side wait, microseconds (default 2e6);
  *   "schedule"        0 = auto, 1 = fused persistent (L2-resident re-read),
  *                     2 = separate launches (TDSC pass, then FDSC pass);
- *   "tile_samples"    FDSC tile width in time samples: 0 (automatic), 8, 16 or 32;
+ *   "tile_samples"    FDSC tile width in time samples: 0 (automatic) or 1, 2, 4, 8, 16, 32
+ *                     (uint8 tiles use at least 8, float32 tiles at most 8);
  *   "smem_target"     shared memory an FDSC tile may use, bytes (sets the automatic width);
  *   "fused_lag"       beams of TDSC rows queued ahead of a beam's FDSC items (0..8);
  *   "ctas_per_sm"     persistent-kernel CTAs per SM (0 = occupancy maximum);

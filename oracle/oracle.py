@@ -61,6 +61,9 @@ def lib():
         L.orc_clean_u8.restype = ctypes.c_int
         L.orc_clean_f32.argtypes = [f32p, f32p, u8p, i64, i64, i64, ctypes.c_int, cutp, cutp]
         L.orc_clean_f32.restype = ctypes.c_int
+        f64p = ctypes.POINTER(ctypes.c_double)
+        L.orc_clean_f32m.argtypes = [f32p, f32p, u8p, f64p, i64, i64, i64, ctypes.c_int, cutp, cutp]
+        L.orc_clean_f32m.restype = ctypes.c_int
         L.orc_tdsc_row_u8.argtypes = [u8p, u8p, i64, ctypes.c_double, ctypes.c_int, ctypes.c_int]
         L.orc_fdsc_col_u8.argtypes = [u8p, u8p, i64, ctypes.c_double, ctypes.c_int, ctypes.c_int, i64]
         L.orc_tdsc_row_f32.argtypes = [f32p, u8p, i64, ctypes.c_double, ctypes.c_int, ctypes.c_int]
@@ -159,3 +162,25 @@ def lower_median(v: np.ndarray):
         return int(L.orc_lower_median_u8(_ptr(v, ctypes.c_uint8), v.shape[0]))
     v = v.astype(np.float32)
     return float(L.orc_lower_median_f32(_ptr(v, ctypes.c_float), v.shape[0]))
+
+
+def clean_f32_margin(x: np.ndarray, layout: str = "bct", tdsc: dict | None = None, fdsc: dict | None = None):
+    """clean() of a float32 block that also returns, per sample, the relative
+    distance |(|x - mu| - k sigma)| / (k sigma) of its closest decision (inf
+    where sigma = 0): the measure the float32 tolerance is stated in."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    if layout == "bct":
+        B, C, T = x.shape
+    else:
+        B, T, C = x.shape
+    tc = make_cut(tdsc)
+    fc = make_cut(fdsc, bin_default=min(32, C))
+    out = np.empty_like(x)
+    flags = np.zeros(x.shape, dtype=np.uint8)
+    margin = np.empty(x.shape, dtype=np.float64)
+    rc = lib().orc_clean_f32m(_ptr(x, ctypes.c_float), _ptr(out, ctypes.c_float), _ptr(flags, ctypes.c_uint8),
+                              _ptr(margin, ctypes.c_double), B, C, T, LAYOUT[layout], ctypes.byref(tc),
+                              ctypes.byref(fc))
+    if rc != 0:
+        raise OracleError(rc)
+    return out, flags, margin

@@ -152,7 +152,19 @@ void orc_fdsc_col_u8(uint8_t* x, uint8_t* f, int64_t n, double k, int iters, int
 /* float32 versions: the same definitions evaluated in IEEE double,     */
 /* two-pass statistics summed in index order.                          */
 /* ------------------------------------------------------------------ */
+/* Relative distance of one decision from its threshold, |(|x - mu| - thr)| / thr,
+ * folded into *m as a minimum (diagnostic output for tolerance checks only). */
+static void note_margin(double* m, double dist, double thr) {
+  if (!m) return;
+  const double r = thr > 0.0 ? fabs(dist - thr) / thr : INFINITY;
+  if (r < *m) *m = r;
+}
+
 void orc_tdsc_row_f32(float* x, uint8_t* f, int64_t n, double k, int iters, int replace) {
+  orc_tdsc_row_f32m(x, f, NULL, n, k, iters, replace);
+}
+
+void orc_tdsc_row_f32m(float* x, uint8_t* f, double* margin, int64_t n, double k, int iters, int replace) {
   for (int it = 0; it < iters; it++) {
     double s = 0.0;
     for (int64_t t = 0; t < n; t++) s += (double)x[t];
@@ -166,6 +178,7 @@ void orc_tdsc_row_f32(float* x, uint8_t* f, int64_t n, double k, int iters, int 
     const double thr = k * sigma;
     const float r = (replace == ORC_REPLACE_MEDIAN) ? orc_lower_median_f32(x, n) : (float)mu;
     for (int64_t t = 0; t < n; t++) {
+      if (margin) note_margin(margin + t, fabs((double)x[t] - mu), thr);
       if (fabs((double)x[t] - mu) > thr) {
         x[t] = r;
         if (f) f[t] |= 1;
@@ -175,6 +188,11 @@ void orc_tdsc_row_f32(float* x, uint8_t* f, int64_t n, double k, int iters, int 
 }
 
 void orc_fdsc_col_f32(float* x, uint8_t* f, int64_t n, double k, int iters, int replace, int64_t bin) {
+  orc_fdsc_col_f32m(x, f, NULL, n, k, iters, replace, bin);
+}
+
+void orc_fdsc_col_f32m(float* x, uint8_t* f, double* margin, int64_t n, double k, int iters, int replace,
+                       int64_t bin) {
   const int64_t nb = (n + bin - 1) / bin;
   double* m = (double*)malloc((size_t)nb * sizeof(double));
   double* d = (double*)malloc((size_t)n * sizeof(double));
@@ -200,6 +218,7 @@ void orc_fdsc_col_f32(float* x, uint8_t* f, int64_t n, double k, int iters, int 
     }
     const double thr = k * sqrt(ss / (double)n);
     for (int64_t c = 0; c < n; c++) {
+      if (margin) note_margin(margin + c, fabs(d[c] - mu), thr);
       if (fabs(d[c] - mu) > thr) {
         x[c] = r[c / bin];
         if (f) f[c] |= 2;
@@ -293,25 +312,35 @@ int orc_clean_u8(const uint8_t* in, uint8_t* out, uint8_t* flags, int64_t B, int
 
 int orc_clean_f32(const float* in, float* out, uint8_t* flags, int64_t B, int64_t C, int64_t T,
                   int layout, const orc_cut* tdsc, const orc_cut* fdsc) {
+  return orc_clean_f32m(in, out, flags, NULL, B, C, T, layout, tdsc, fdsc);
+}
+
+int orc_clean_f32m(const float* in, float* out, uint8_t* flags, double* margin, int64_t B, int64_t C, int64_t T,
+                   int layout, const orc_cut* tdsc, const orc_cut* fdsc) {
   int rc = check_block(B, C, T, layout, tdsc, fdsc);
   if (rc) return rc;
   const int64_t N = B * C * T;
   if (out != in) memmove(out, in, (size_t)N * sizeof(float));
   if (flags) memset(flags, 0, (size_t)N);
+  if (margin)
+    for (int64_t i = 0; i < N; i++) margin[i] = INFINITY;
   const int64_t M = C > T ? C : T;
   float* v = (float*)malloc((size_t)M * sizeof(float));
   uint8_t* fl = (uint8_t*)malloc((size_t)M);
+  double* mg = margin ? (double*)malloc((size_t)M * sizeof(double)) : NULL;
   if (tdsc && tdsc->enabled) {
     for (int64_t b = 0; b < B; b++)
       for (int64_t c = 0; c < C; c++) {
         for (int64_t t = 0; t < T; t++) {
           v[t] = out[at(b, c, t, C, T, layout)];
           fl[t] = 0;
+          if (mg) mg[t] = INFINITY;
         }
-        orc_tdsc_row_f32(v, fl, T, tdsc->k, tdsc->iterations, tdsc->replace);
+        orc_tdsc_row_f32m(v, fl, mg, T, tdsc->k, tdsc->iterations, tdsc->replace);
         for (int64_t t = 0; t < T; t++) {
           out[at(b, c, t, C, T, layout)] = v[t];
           if (flags) flags[at(b, c, t, C, T, layout)] |= fl[t];
+          if (mg && mg[t] < margin[at(b, c, t, C, T, layout)]) margin[at(b, c, t, C, T, layout)] = mg[t];
         }
       }
   }
@@ -321,15 +350,18 @@ int orc_clean_f32(const float* in, float* out, uint8_t* flags, int64_t B, int64_
         for (int64_t c = 0; c < C; c++) {
           v[c] = out[at(b, c, t, C, T, layout)];
           fl[c] = 0;
+          if (mg) mg[c] = INFINITY;
         }
-        orc_fdsc_col_f32(v, fl, C, fdsc->k, fdsc->iterations, fdsc->replace, fdsc->bin);
+        orc_fdsc_col_f32m(v, fl, mg, C, fdsc->k, fdsc->iterations, fdsc->replace, fdsc->bin);
         for (int64_t c = 0; c < C; c++) {
           out[at(b, c, t, C, T, layout)] = v[c];
           if (flags) flags[at(b, c, t, C, T, layout)] |= fl[c];
+          if (mg && mg[c] < margin[at(b, c, t, C, T, layout)]) margin[at(b, c, t, C, T, layout)] = mg[c];
         }
       }
   }
   free(v);
   free(fl);
+  free(mg);
   return ORC_OK;
 }

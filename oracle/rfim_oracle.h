@@ -80,6 +80,16 @@ void orc_tdsc_row_u8(uint8_t* x, uint8_t* f, int64_t n, double k, int iters, int
 void orc_fdsc_col_u8(uint8_t* x, uint8_t* f, int64_t n, double k, int iters, int replace, int64_t bin);
 void orc_tdsc_row_f32(float* x, uint8_t* f, int64_t n, double k, int iters, int replace);
 void orc_fdsc_col_f32(float* x, uint8_t* f, int64_t n, double k, int iters, int replace, int64_t bin);
+
+/* The same float32 cuts with a diagnostic output (nullable): margin[i] is the
+ * minimum over the sample's decisions of |(|x - mu| - k sigma)| / (k sigma),
+ * its relative distance from the nearest threshold (INFINITY where sigma = 0). */
+int orc_clean_f32m(const float* in, float* out, uint8_t* flags, double* margin,
+                   int64_t B, int64_t C, int64_t T, int layout,
+                   const orc_cut* tdsc, const orc_cut* fdsc);
+void orc_tdsc_row_f32m(float* x, uint8_t* f, double* margin, int64_t n, double k, int iters, int replace);
+void orc_fdsc_col_f32m(float* x, uint8_t* f, double* margin, int64_t n, double k, int iters, int replace,
+                       int64_t bin);
 uint8_t orc_lower_median_u8(const uint8_t* x, int64_t n);
 float orc_lower_median_f32(const float* x, int64_t n);
 

@@ -186,8 +186,18 @@ rfim_status check_block(rfim_ctx* ctx, const rfim_block* b, const CutNorm& td, c
 
 // Engine limits of this build.
 rfim_status check_impl(rfim_ctx* ctx, const rfim_block* b, const CutNorm& td, const CutNorm& fd) {
-  if (b->dtype != RFIM_U8) return fail(ctx, RFIM_ERR_ARG, "float32 blocks are not available in this build");
   if (b->layout != RFIM_LAYOUT_BCT) return fail(ctx, RFIM_ERR_ARG, "BTC layout is not available in this build");
+  if (b->dtype == RFIM_F32) {
+    if (td.on && b->samples > TD32_MAX_T)
+      return fail(ctx, RFIM_ERR_ARG, "float32 TDSC rows longer than %d samples are not available in this build",
+                  TD32_MAX_T);
+    if (fd.on) {
+      const int C = b->channels, nb = (C + fd.bin - 1) / fd.bin;
+      if (fd32_smem_bytes(1, C, nb) > MAX_SMEM_PER_CTA)
+        return fail(ctx, RFIM_ERR_RANGE, "FDSC: %d float32 channels do not fit the on-chip tile", C);
+    }
+    return RFIM_OK;
+  }
   if (td.on && td_row_mode(b->samples) < 0)
     return fail(ctx, RFIM_ERR_ARG, "TDSC rows longer than 98273 samples are not available in this build");
   if (fd.on) {
@@ -204,10 +214,11 @@ struct Plan {
   CutNorm td, fd;
   int mask_kind = 0;
   int max_T = 1;
+  rfim_dtype dtype = RFIM_U8;
 };
 
 int pick_ws_opt(int tile_samples, int C, int nb, int pitch, int budget) {
-  if (tile_samples > 0) return tile_samples;
+  if (tile_samples > 0) return tile_samples < 8 ? 8 : tile_samples;  // uint8 tiles are 8, 16 or 32 wide
   for (int ws : {32, 16, 8})
     if (fd_smem_bytes(ws, pitch, nb, C) <= budget) return ws;
   return 8;
@@ -245,6 +256,17 @@ Job make_job(const rfim_block* b, int j, const CutNorm& fd, int tile_samples, in
   J.fd_items = (T + FD_ITEM_T - 1) / FD_ITEM_T;
   J.td_mode = td_row_mode(T) == 1 ? 1 : 0;
   J.td_items = J.td_mode == 0 ? (C + TD_ROWS_PER_ITEM - 1) / TD_ROWS_PER_ITEM : C;
+  if (b->dtype == RFIM_F32) {
+    // float32: one CTA per TDSC row; FDSC sub-slab of 8, 4, 2 or 1 samples
+    J.td_mode = 1;
+    J.td_items = C;
+    J.ws = 1;
+    for (int ws : {8, 4, 2})
+      if ((tile_samples == 0 || ws <= tile_samples) && fd32_smem_bytes(ws, C, J.nb) <= smem_target) {
+        J.ws = ws;
+        break;
+      }
+  }
   return J;
 }
 
@@ -336,21 +358,22 @@ void fill_params(rfim_ctx* ctx, const Plan& pl, int j0, int j1, int mode, Params
   p.spin_limit_ns = (unsigned long long)ctx->spin_limit_us * 1000ull;
   p.counters = counters;
   p.status = ctx->d_status;
+  p.dtype = pl.dtype == RFIM_F32 ? 1 : 0;
   fill_segments(p, mode, ctx->fused_lag);
 }
 
 rfim_status launch_one(rfim_ctx* ctx, Params& p, int max_T, cudaStream_t st) {
   (void)max_T;
   LaunchCfg cfg;
-  cfg.smem = engine_smem_u8(p);
+  cfg.smem = engine_smem(p);
   if (cfg.smem > MAX_SMEM_PER_CTA) return fail(ctx, RFIM_ERR_ARG, "tile does not fit in shared memory (%d bytes)", cfg.smem);
-  void* fn = engine_kernel_u8();
+  void* fn = engine_kernel(p);
   int per_sm = occupancy(fn, cfg.smem);
   if (ctx->ctas_per_sm > 0) per_sm = std::min(per_sm, ctx->ctas_per_sm);
   cfg.grid = std::max(1, std::min(p.n_items, ctx->sms * per_sm));
   cudaError_t e = cudaMemsetAsync(p.counters, 0, sizeof(unsigned) * (1 + p.n_jobs), st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync");
-  e = (cudaError_t)launch_engine_u8(p, cfg, st);
+  e = (cudaError_t)launch_engine(p, cfg, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "engine launch");
   return RFIM_OK;
 }
@@ -407,6 +430,7 @@ rfim_status make_plan(rfim_ctx* ctx, const rfim_block* blocks, int n, const rfim
       pl.td = td;
       pl.fd = fd;
       pl.mask_kind = (int)b->mask_fmt;
+      pl.dtype = b->dtype;
     } else {
       if (b->dtype != blocks[0].dtype || b->layout != blocks[0].layout)
         return fail(ctx, RFIM_ERR_ARG, "all blocks of a batch must share dtype and layout");
@@ -484,8 +508,8 @@ rfim_status rfim_set_option(rfim_ctx* ctx, const char* key, long long value) {
     if (value < 0 || value > 2) return fail(ctx, RFIM_ERR_ARG, "schedule must be 0, 1 or 2");
     ctx->schedule = (int)value;
   } else if (k == "tile_samples") {
-    if (value != 0 && value != 8 && value != 16 && value != 32)
-      return fail(ctx, RFIM_ERR_ARG, "tile_samples must be 0, 8, 16 or 32");
+    if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 && value != 16 && value != 32)
+      return fail(ctx, RFIM_ERR_ARG, "tile_samples must be 0, 1, 2, 4, 8, 16 or 32");
     ctx->tile_samples = (int)value;
   } else if (k == "ctas_per_sm") {
     if (value < 0 || value > 32) return fail(ctx, RFIM_ERR_ARG, "ctas_per_sm must be in 0..32");
@@ -710,10 +734,12 @@ rfim_status noalloc_clean(const rfim_block* b, const rfim_cut* tdsc, const rfim_
   p.spin_limit_ns = 2000000000ull;
   p.counters = counters;
   p.status = status;
+  p.dtype = b->dtype == RFIM_F32 ? 1 : 0;
   fill_segments(p, mode, 1);
   LaunchCfg cfg;
-  cfg.smem = engine_smem_u8(p);
-  void* fn = engine_kernel_u8();
+  cfg.smem = engine_smem(p);
+  if (cfg.smem > MAX_SMEM_PER_CTA) return RFIM_ERR_ARG;
+  void* fn = engine_kernel(p);
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return RFIM_ERR_CUDA;
@@ -725,7 +751,7 @@ rfim_status noalloc_clean(const rfim_block* b, const rfim_cut* tdsc, const rfim_
   if (cudaMemsetAsync(counters, 0, sizeof(unsigned) * (1 + p.n_jobs), st) != cudaSuccess ||
       cudaMemsetAsync(status, 0, sizeof(unsigned), st) != cudaSuccess)
     return RFIM_ERR_CUDA;
-  if (launch_engine_u8(p, cfg, st) != (int)cudaSuccess) return RFIM_ERR_CUDA;
+  if (launch_engine(p, cfg, st) != (int)cudaSuccess) return RFIM_ERR_CUDA;
   return RFIM_OK;
 }
 

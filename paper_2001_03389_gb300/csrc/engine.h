@@ -62,6 +62,7 @@ struct Params {
   unsigned long long spin_limit_ns;
   unsigned* counters;   // [0] queue head, [1 + j] TDSC rows done for job j
   unsigned* status;     // device status word (0 = ok, 5 = timeout)
+  int dtype;            // 0 = uint8 (k_engine_u8), 1 = float32 (k_engine_f32)
 };
 
 __host__ __device__ inline int align16i(int x) { return (x + 15) & ~15; }
@@ -111,5 +112,28 @@ struct LaunchCfg {
 int engine_smem_u8(const Params& p);
 void* engine_kernel_u8();
 int launch_engine_u8(const Params& p, const LaunchCfg& cfg, void* stream);
+
+// float32 engine: TDSC rows of up to TD32_MAX_T samples staged per CTA; FDSC tile
+// of ws x C floats plus per-(t, bin) and per-column scratch.
+constexpr int TD32_LIST = 1024;  // replaced values kept per iteration for the statistics update
+constexpr int TD32_MAX_T = 52000;
+__host__ __device__ inline int td32_smem_bytes(int T) {
+  const int nch = (T + 6) / 4 + 1;
+  return 16 * nch + align16i(nch) + 4 * TD32_LIST;
+}
+__host__ __device__ inline int fd32_smem_bytes(int ws, int C, int nb) {
+  const int U = ws * nb;
+  return align16i(ws * C * 4) + align16i(C * 4) + align16i(U * 8) * 2 + align16i(U * 4) + align16i(ws * 8) +
+         align16i(ws * 4) * 3;
+}
+int engine_smem_f32(const Params& p);
+void* engine_kernel_f32();
+int launch_engine_f32(const Params& p, const LaunchCfg& cfg, void* stream);
+
+inline int engine_smem(const Params& p) { return p.dtype ? engine_smem_f32(p) : engine_smem_u8(p); }
+inline void* engine_kernel(const Params& p) { return p.dtype ? engine_kernel_f32() : engine_kernel_u8(); }
+inline int launch_engine(const Params& p, const LaunchCfg& cfg, void* stream) {
+  return p.dtype ? launch_engine_f32(p, cfg, stream) : launch_engine_u8(p, cfg, stream);
+}
 
 }  // namespace rfim

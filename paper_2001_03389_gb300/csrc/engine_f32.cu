@@ -1,0 +1,762 @@
+// engine_f32.cu -- float32 TDSC and FDSC (Sec. IV of arXiv:2001.03389) on sm_103a.
+//
+// Same persistent work queue as the uint8 engine: TDSC items are whole rows
+// (one CTA per (beam, channel) row, staged in shared memory), FDSC items are
+// 32 time samples x all channels of a beam, processed in sub-slabs of ws
+// samples held as a [channel][time] tile in shared memory.
+//
+// Precision.  The decision |x - mu| > k sigma must agree with an FP64
+// evaluation except within ~1e-9 relative of the threshold, but an FP64 warp
+// instruction costs ~20 SM cycles on this part.  So:
+//  - sums and sums of squares are accumulated per thread in float-float
+//    (TwoSum compensation, exact products by FMA) and merged in float-float;
+//    only the per-row / per-column finish (mean, variance, sqrt) is FP64;
+//  - the variance is Q/n - mu^2 from those sums; when that cancels badly
+//    (mu^2 > 1000 sigma^2) the row or column is redone with an FP64 two-pass;
+//  - each sample is decided in FP32 against bounds widened by 2^-20 (and by
+//    the rounding of the mean to float); a sample inside the band is decided
+//    by the FP64 expression fabs((double)x - mu) > k * sigma.
+#include <cuda_runtime.h>
+
+#include "engine.h"
+
+namespace rfim {
+
+// ---------------------------------------------------------------------------
+// float-float arithmetic (no contraction: explicit _rn intrinsics)
+// ---------------------------------------------------------------------------
+struct FF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float z = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
+__device__ __forceinline__ void ff_acc(FF& a, float y) {
+  float s, e;
+  two_sum(a.hi, y, s, e);
+  a.hi = s;
+  a.lo = __fadd_rn(a.lo, e);
+}
+
+__device__ __forceinline__ void ff_acc_sq(FF& a, float y) {
+  const float p = __fmul_rn(y, y);
+  const float pe = __fmaf_rn(y, y, -p);  // y*y = p + pe exactly
+  float s, e;
+  two_sum(a.hi, p, s, e);
+  a.hi = s;
+  a.lo = __fadd_rn(a.lo, __fadd_rn(e, pe));
+}
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  FF r;
+  r.hi = __fadd_rn(s, e);
+  r.lo = __fsub_rn(e, __fsub_rn(r.hi, s));
+  return r;
+}
+
+__device__ __forceinline__ FF ff_neg(FF a) { return FF{-a.hi, -a.lo}; }
+
+// a * b for float-float a, b (error ~ u^2 relative)
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  FF r;
+  r.hi = __fadd_rn(p, e);
+  r.lo = __fsub_rn(e, __fsub_rn(r.hi, p));
+  return r;
+}
+
+// a / g for a positive integer g
+__device__ __forceinline__ FF ff_div_int(FF a, int g) {
+  if ((g & (g - 1)) == 0) {  // power of two: exact scaling
+    const float s = __frcp_rn((float)g);
+    return FF{__fmul_rn(a.hi, s), __fmul_rn(a.lo, s)};
+  }
+  const float gf = (float)g;
+  const float q1 = __fdiv_rn(a.hi, gf);
+  const float p = __fmul_rn(q1, gf);
+  const float pe = __fmaf_rn(q1, gf, -p);
+  // remainder a - q1 * g: hi - p is exact (p is within one rounding of hi)
+  const float rem = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), pe), a.lo);
+  const float q2 = __fdiv_rn(rem, gf);
+  FF r;
+  r.hi = __fadd_rn(q1, q2);
+  r.lo = __fsub_rn(q2, __fsub_rn(r.hi, q1));
+  return r;
+}
+
+__device__ __forceinline__ double ff_d(FF a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ FF shfl_ff(FF a, int o) {
+  return FF{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+
+__device__ __forceinline__ FF warp_ff(FF a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a = ff_add(a, shfl_ff(a, o));
+  return a;
+}
+
+// ---------------------------------------------------------------------------
+// Decisions
+// ---------------------------------------------------------------------------
+// One cut of one iteration of one row or (column, bin): samples y with
+// |y - mu| > thr are flagged.  mu_f = (float)mu; [lo_f, hi_f] is the band in
+// which the FP32 value |y - mu_f| cannot decide.
+struct Cut32 {
+  float mu_f, lo_f, hi_f;
+  double mu, thr;
+};
+
+// thr and the rounding error dm = |mu - mu_f| (both >= 0) -> FP32 bounds.
+// |fl(y - mu_f)| = a satisfies |y - mu_f| in [a / (1 + u), a / (1 - u)], u = 2^-24,
+// and | |y - mu| - |y - mu_f| | <= dm, so a > (thr + dm)(1 + 2^-20) proves a flag
+// and a <= (thr - dm)(1 - 2^-20) proves a keep.
+__device__ __forceinline__ void band_bounds(double thr, double dm, float& lo_f, float& hi_f) {
+  hi_f = __double2float_ru((thr + dm) * (1.0 + 0x1p-20));
+  lo_f = __double2float_rd((thr - dm) * (1.0 - 0x1p-20));
+}
+
+// The same bounds from FP32 inputs: thr_hi >= thr >= thr_lo (float bounds of
+// the FP64 threshold) and dm >= |mu - mu_f|.
+__device__ __forceinline__ void band_bounds_f(float thr_lo, float thr_hi, float dm, float& lo_f, float& hi_f) {
+  const float h = __fadd_ru(thr_hi, dm);
+  hi_f = __fmul_ru(h, 1.0f + 0x1p-20f);
+  const float l = __fsub_rd(thr_lo, dm);
+  lo_f = __fmul_rd(l, 1.0f - 0x1p-20f);
+}
+
+__device__ __forceinline__ bool flag32(float y, const Cut32& c) {
+  const float a = fabsf(__fsub_rn(y, c.mu_f));
+  if (a > c.hi_f) return true;
+  if (!(a > c.lo_f)) return false;
+  return fabs((double)y - c.mu) > c.thr;  // inside the band: the FP64 expression
+}
+
+// Total order of floats as unsigned keys (-0 before +0).
+__device__ __forceinline__ unsigned fkey(float f) {
+  const unsigned b = __float_as_uint(f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float key_f(unsigned k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
+// ---------------------------------------------------------------------------
+// CTA reductions (NT threads)
+// ---------------------------------------------------------------------------
+struct Red32 {
+  float f[2 * (NT / 32) * 2];
+  double d[2 * (NT / 32)];
+  int i[NT / 32];
+  int flag;
+};
+
+// (a, b) summed over the CTA; every thread gets the result
+__device__ __forceinline__ void block_ff2(FF& a, FF& b, Red32* r) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  a = warp_ff(a);
+  b = warp_ff(b);
+  __syncthreads();
+  if (lane == 0) {
+    r->f[4 * warp + 0] = a.hi;
+    r->f[4 * warp + 1] = a.lo;
+    r->f[4 * warp + 2] = b.hi;
+    r->f[4 * warp + 3] = b.lo;
+  }
+  __syncthreads();
+  FF sa{0.f, 0.f}, sb{0.f, 0.f};
+#pragma unroll
+  for (int w = 0; w < NT / 32; w++) {
+    sa = ff_add(sa, FF{r->f[4 * w + 0], r->f[4 * w + 1]});
+    sb = ff_add(sb, FF{r->f[4 * w + 2], r->f[4 * w + 3]});
+  }
+  a = sa;
+  b = sb;
+}
+
+__device__ __forceinline__ double block_dsum(double v, Red32* r) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) r->d[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+#pragma unroll
+  for (int w = 0; w < NT / 32; w++) s += r->d[w];
+  return s;
+}
+
+__device__ __forceinline__ int block_isum(int v, Red32* r) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = __reduce_add_sync(0xffffffffu, v);
+  __syncthreads();
+  if (lane == 0) r->i[warp] = v;
+  __syncthreads();
+  int s = 0;
+#pragma unroll
+  for (int w = 0; w < NT / 32; w++) s += r->i[w];
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// TDSC on one float32 row (the whole CTA)
+// ---------------------------------------------------------------------------
+// Shared memory: the row's 16-byte chunk grid (element i of the row at
+// st[head + i]), one flag nibble per chunk, the list of replaced values of the
+// current iteration.
+__device__ __forceinline__ float4 ld_f4_na(const float* p) {
+  float4 v;
+  asm volatile("ld.global.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
+}
+
+__device__ __forceinline__ float f4_get(const float4& v, int i) {
+  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ void f4_set(float4& v, int i, float x) {
+  if (i == 0) v.x = x;
+  else if (i == 1) v.y = x;
+  else if (i == 2) v.z = x;
+  else v.w = x;
+}
+
+// Lower median (rank floor((n-1)/2)) of the valid elements of the staged row:
+// bitwise search over the order keys, one bit per CTA-wide count.
+__device__ float row_median_f32(const float4* st, int nch, int head, int tail, int n, Red32* red) {
+  const int rank = (n - 1) >> 1;
+  unsigned prefix = 0;
+  for (int b = 31; b >= 0; b--) {
+    const unsigned test = prefix | (1u << b);
+    int cnt = 0;
+    for (int k = threadIdx.x; k < nch; k += NT) {
+      const float4 v = st[k];
+      const int lo = k == 0 ? head : 0, hi = k == nch - 1 ? tail : 4;
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+        if (i >= lo && i < hi) cnt += fkey(f4_get(v, i)) < test;
+    }
+    cnt = block_isum(cnt, red);
+    if (cnt <= rank) prefix = test;
+  }
+  return key_f(prefix);
+}
+
+__device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned char* smem, Red32* red) {
+  const CutDev& cut = P.td;
+  const int T = J.T;
+  const float* beam_in = static_cast<const float*>(J.in);
+  const float* rin = beam_in + (size_t)row * T;
+  float* rout = static_cast<float*>(J.out) + (size_t)row * T;
+  const float* blo = static_cast<const float*>(J.src_lo);
+  const float* bhi = static_cast<const float*>(J.src_hi);
+
+  const int head = (int)(((uintptr_t)rin & 15) >> 2);
+  const float* cb = rin - head;
+  const int nch = (head + T + 3) >> 2;
+  const int tail = head + T - 4 * (nch - 1);  // valid elements of the last chunk (1..4)
+
+  float4* st = reinterpret_cast<float4*>(smem);
+  unsigned char* fl4 = smem + 16 * nch;
+  float* lst = reinterpret_cast<float*>(smem + 16 * nch + align16i(nch));
+  __shared__ int s_nlist;
+
+  // ---- stage the row (edge chunks through guarded loads, padding zeroed)
+  for (int k = threadIdx.x; k < nch; k += NT) {
+    const float* a = cb + 4 * k;
+    if (k > 0 && k < nch - 1) {
+      const unsigned sdst = (unsigned)__cvta_generic_to_shared(st + k);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sdst), "l"(a) : "memory");
+    } else {
+      const int lo = k == 0 ? head : 0, hi = k == nch - 1 ? tail : 4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+        if (i >= lo && i < hi && a + i >= blo && a + i < bhi) f4_set(v, i, a[i]);
+      st[k] = v;
+    }
+    fl4[k] = 0;
+  }
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+
+  // ---- sums of the staged row (padding zeros add nothing)
+  FF S{0.f, 0.f}, Q{0.f, 0.f};
+  for (int k = threadIdx.x; k < nch; k += NT) {
+    const float4 v = st[k];
+    ff_acc(S, v.x);
+    ff_acc_sq(Q, v.x);
+    ff_acc(S, v.y);
+    ff_acc_sq(Q, v.y);
+    ff_acc(S, v.z);
+    ff_acc_sq(Q, v.z);
+    ff_acc(S, v.w);
+    ff_acc_sq(Q, v.w);
+  }
+  block_ff2(S, Q, red);
+  double Sd = ff_d(S), Qd = ff_d(Q);
+  const double Tn = (double)T;
+  const int I = cut.iterations;
+
+  for (int it = 0; it < I; it++) {
+    // statistics of the current values (every thread computes the same doubles)
+    const double mu = Sd / Tn;
+    double var = Qd / Tn - mu * mu;
+    if (!(var >= 1e-3 * (Qd / Tn))) {
+      // cancellation (or a constant row): FP64 two-pass over the current values
+      double s = 0.0;
+      for (int k = threadIdx.x; k < nch; k += NT) {
+        const float4 v = st[k];
+        s += ((double)v.x + (double)v.y) + ((double)v.z + (double)v.w);  // padding is 0
+      }
+      s = block_dsum(s, red);
+      const double m2 = s / Tn;
+      double ss = 0.0;
+      for (int k = threadIdx.x; k < nch; k += NT) {
+        const float4 v = st[k];
+        const int lo = k == 0 ? head : 0, hi = k == nch - 1 ? tail : 4;
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+          if (i >= lo && i < hi) {
+            const double d = (double)f4_get(v, i) - m2;
+            ss += d * d;
+          }
+      }
+      ss = block_dsum(ss, red);
+      var = ss / Tn;
+      // use the two-pass mean too
+      Sd = s;
+    }
+    const double mu_use = Sd / Tn;
+    const double thr = cut.k * sqrt(var > 0.0 ? var : 0.0);
+    Cut32 c;
+    c.mu = mu_use;
+    c.thr = thr;
+    c.mu_f = __double2float_rn(mu_use);
+    band_bounds(thr, fabs(mu_use - (double)c.mu_f), c.lo_f, c.hi_f);
+    const float r = cut.replace == REP_MEDIAN ? row_median_f32(st, nch, head, tail, T, red) : c.mu_f;
+
+    // decide and replace; the replaced values go to a list for the statistics update
+    if (threadIdx.x == 0) s_nlist = 0;
+    __syncthreads();
+    for (int k = threadIdx.x; k < nch; k += NT) {
+      float4 v = st[k];
+      const int lo = k == 0 ? head : 0, hi = k == nch - 1 ? tail : 4;
+      unsigned nib = 0;
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        const float y = f4_get(v, i);
+        if (i >= lo && i < hi && flag32(y, c)) {
+          nib |= 1u << i;
+          f4_set(v, i, r);
+          const int pos = atomicAdd(&s_nlist, 1);
+          if (pos < TD32_LIST) lst[pos] = y;
+        }
+      }
+      if (nib) {
+        st[k] = v;
+        fl4[k] |= (unsigned char)nib;
+      }
+    }
+    if (it == I - 1) break;
+    __syncthreads();
+    // statistics of the next iteration: S' = S - sum(replaced) + nf r (same for Q)
+    const int nflag = s_nlist;
+    FF rs{0.f, 0.f}, rq{0.f, 0.f};
+    if (nflag <= TD32_LIST) {
+      for (int i = threadIdx.x; i < nflag; i += NT) {
+        ff_acc(rs, lst[i]);
+        ff_acc_sq(rq, lst[i]);
+      }
+      block_ff2(rs, rq, red);
+      const double rd = (double)r;
+      Sd = Sd - ff_d(rs) + (double)nflag * rd;
+      Qd = Qd - ff_d(rq) + (double)nflag * rd * rd;
+    } else {
+      // many replacements: sum the current row again
+      for (int k = threadIdx.x; k < nch; k += NT) {
+        const float4 v = st[k];
+        ff_acc(rs, v.x);
+        ff_acc_sq(rq, v.x);
+        ff_acc(rs, v.y);
+        ff_acc_sq(rq, v.y);
+        ff_acc(rs, v.z);
+        ff_acc_sq(rq, v.z);
+        ff_acc(rs, v.w);
+        ff_acc_sq(rq, v.w);
+      }
+      block_ff2(rs, rq, red);
+      Sd = ff_d(rs);
+      Qd = ff_d(rq);
+    }
+  }
+  __syncthreads();
+
+  // ---- write the row and its mask
+  const bool same_align = (((uintptr_t)rout) & 15) == (((uintptr_t)rin) & 15);
+  float* ob = rout - head;
+  for (int k = threadIdx.x; k < nch; k += NT) {
+    const float4 v = st[k];
+    const int lo = k == 0 ? head : 0, hi = k == nch - 1 ? tail : 4;
+    if (same_align && lo == 0 && hi == 4) {
+      *reinterpret_cast<float4*>(ob + 4 * k) = v;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+        if (i >= lo && i < hi) ob[4 * k + i] = f4_get(v, i);
+    }
+  }
+  if (P.mask_kind == MASK_BITS && J.mask) {
+    const int W32 = (T + 31) >> 5;
+    unsigned* mrow = static_cast<unsigned*>(J.mask) + (size_t)row * W32;
+    // word w covers chunk-grid positions head + 32 w ... head + 32 w + 31: chunks 8w .. 8w + 8
+    for (int w = threadIdx.x; w < W32; w += NT) {
+      unsigned long long bits = 0;
+#pragma unroll
+      for (int j = 0; j < 9; j++) {
+        const int k = 8 * w + j;
+        if (k < nch) bits |= (unsigned long long)(fl4[k] & 0xF) << (4 * j);
+      }
+      unsigned word = (unsigned)(bits >> head);
+      const int valid = T - 32 * w;
+      if (valid < 32) word &= (1u << valid) - 1u;
+      mrow[w] = word;
+    }
+  } else if (P.mask_kind == MASK_BYTES && J.mask) {
+    unsigned char* mb = static_cast<unsigned char*>(J.mask) + (size_t)row * T;
+    for (int t = threadIdx.x; t < T; t += NT) {
+      const int p = head + t;
+      mb[t] = (unsigned char)((fl4[p >> 2] >> (p & 3)) & 1u);
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// FDSC on one item: FD_ITEM_T time samples x C channels of a float32 beam
+// ---------------------------------------------------------------------------
+// Tile [c][t] (pitch ws floats).  Work units are (t, bin) pairs, one thread
+// each, t fastest; a unit walks its bin starting at a rotation of (bin mod 32)
+// channels so that the lanes of a warp hit distinct banks.
+struct Fd32Layout {
+  float* tile;    // C x ws
+  unsigned* fm;   // C: FDSC flag bits of the item (bit = t - t_item)
+  float2* um;     // units: bin mean as float-float
+  float2* uv;     // units: sum of squared deviations as float-float
+  float* uq;      // units: sum of squares (cancellation check)
+  double* thr;    // ws: column thresholds k * sigma'
+  float* thr_lo;  // ws
+  float* thr_hi;  // ws
+  int* prec;      // ws: column needs the FP64 two-pass
+};
+
+__device__ __forceinline__ Fd32Layout fd32_layout(unsigned char* smem, int ws, int C, int nb) {
+  const int U = ws * nb;
+  Fd32Layout L;
+  unsigned char* p = smem;
+  L.tile = reinterpret_cast<float*>(p);
+  p += align16i(ws * C * 4);
+  L.fm = reinterpret_cast<unsigned*>(p);
+  p += align16i(C * 4);
+  L.um = reinterpret_cast<float2*>(p);
+  p += align16i(U * 8);
+  L.uv = reinterpret_cast<float2*>(p);
+  p += align16i(U * 8);
+  L.uq = reinterpret_cast<float*>(p);
+  p += align16i(U * 4);
+  L.thr = reinterpret_cast<double*>(p);
+  p += align16i(ws * 8);
+  L.thr_lo = reinterpret_cast<float*>(p);
+  p += align16i(ws * 4);
+  L.thr_hi = reinterpret_cast<float*>(p);
+  p += align16i(ws * 4);
+  L.prec = reinterpret_cast<int*>(p);
+  return L;
+}
+
+// Lower median of the n values tile[(c0 + j) * ws + t], j < n (one thread).
+__device__ float bin_median_f32(const float* tile, int c0, int n, int ws, int t) {
+  const int rank = (n - 1) >> 1;
+  unsigned prefix = 0;
+  for (int b = 31; b >= 0; b--) {
+    const unsigned test = prefix | (1u << b);
+    int cnt = 0;
+    for (int j = 0; j < n; j++) cnt += fkey(tile[(c0 + j) * ws + t]) < test;
+    if (cnt <= rank) prefix = test;
+  }
+  return key_f(prefix);
+}
+
+__device__ void fdsc_item_f32(const Params& P, const Job& J, int item, unsigned char* smem, Red32* red) {
+  const CutDev& cut = P.fd;
+  const int C = J.C, T = J.T, G = cut.bin, NB = J.nb, Gl = J.last_g;
+  const int t_item = item * FD_ITEM_T;
+  const int t_end = min(t_item + FD_ITEM_T, T);
+  const int Ws = J.ws;
+  const float* src = static_cast<const float*>(P.fd_reads_out ? J.out : J.in);
+  float* dst = static_cast<float*>(J.out);
+  const Fd32Layout L = fd32_layout(smem, Ws, C, NB);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool vec = ((((uintptr_t)src) | ((uintptr_t)dst)) & 15) == 0 && (T & 3) == 0;
+  const double Cn = (double)C;
+
+  for (int c = threadIdx.x; c < C; c += NT) L.fm[c] = 0;
+
+  for (int t0 = t_item; t0 < t_end; t0 += Ws) {
+    const int w = min(Ws, t_end - t0);
+    // ---- load the sub-slab: thread per channel
+    for (int c = threadIdx.x; c < C; c += NT) {
+      const float* a = src + (size_t)c * T + t0;
+      float* d = L.tile + c * Ws;
+      if (vec && w == Ws && Ws >= 4) {
+#pragma unroll 2
+        for (int j = 0; j < Ws; j += 4) *reinterpret_cast<float4*>(d + j) = ld_f4_na(a + j);
+      } else {
+        for (int j = 0; j < w; j++) d[j] = a[j];
+      }
+    }
+    __syncthreads();
+
+    const int U = w * NB;
+    for (int it = 0; it < cut.iterations; it++) {
+      // ---- per (t, bin): float-float sum and sum of squares, bin mean, M2
+      for (int u = threadIdx.x; u < U; u += NT) {
+        const int t = u % w, g = u / w;
+        const int c0 = g * G, n = g == NB - 1 ? Gl : G;
+        const int rot = g % n;
+        FF s{0.f, 0.f}, q{0.f, 0.f};
+        for (int j = 0; j < n; j++) {
+          int jj = j + rot;
+          if (jj >= n) jj -= n;
+          const float y = L.tile[(c0 + jj) * Ws + t];
+          ff_acc(s, y);
+          ff_acc_sq(q, y);
+        }
+        const FF m = ff_add(ff_div_int(s, n), FF{0.f, 0.f});  // normalised: m.hi = fl(mean)
+        const FF m2 = ff_add(q, ff_neg(ff_mul(s, m)));  // sum (x - m)^2 = Q - S m
+        L.um[u] = make_float2(m.hi, m.lo);
+        L.uv[u] = make_float2(m2.hi, m2.lo);
+        L.uq[u] = q.hi;
+      }
+      __syncthreads();
+      // ---- per column: sigma' over all channels (mu' = 0: every bin's deviations sum to 0)
+      for (int t = warp; t < w; t += NT / 32) {
+        FF v{0.f, 0.f};
+        float qs = 0.f;
+        for (int g = lane; g < NB; g += 32) {
+          const float2 a = L.uv[g * w + t];
+          v = ff_add(v, FF{a.x, a.y});
+          qs += L.uq[g * w + t];
+        }
+        v = warp_ff(v);
+        qs = warp_sum(qs);
+        if (lane == 0) {
+          const double V = ff_d(v);
+          const int prec = !(V >= 1e-3 * (double)qs);
+          L.prec[t] = prec;
+          const double thr = cut.k * sqrt((V > 0.0 ? V : 0.0) / Cn);
+          L.thr[t] = thr;
+          L.thr_lo[t] = __double2float_rd(thr);
+          L.thr_hi[t] = __double2float_ru(thr);
+        }
+      }
+      __syncthreads();
+      // ---- cancellation: the column's FP64 two-pass of the definition
+      for (int t = warp; t < w; t += NT / 32) {
+        if (!L.prec[t]) continue;
+        double sd = 0.0;
+        for (int c = lane; c < C; c += 32) {
+          const float2 m = L.um[(c / G) * w + t];
+          sd += (double)L.tile[c * Ws + t] - ((double)m.x + (double)m.y);
+        }
+        sd = warp_sum(sd);
+        const double mup = sd / Cn;
+        double ss = 0.0;
+        for (int c = lane; c < C; c += 32) {
+          const float2 m = L.um[(c / G) * w + t];
+          const double e = ((double)L.tile[c * Ws + t] - ((double)m.x + (double)m.y)) - mup;
+          ss += e * e;
+        }
+        ss = warp_sum(ss);
+        if (lane == 0) {
+          const double thr = cut.k * sqrt(ss / Cn);
+          L.thr[t] = thr;
+          L.thr_lo[t] = __double2float_rd(thr);
+          L.thr_hi[t] = __double2float_ru(thr);
+        }
+      }
+      __syncthreads();
+      // ---- decide and replace, per (t, bin)
+      for (int u = threadIdx.x; u < U; u += NT) {
+        const int t = u % w, g = u / w;
+        const int c0 = g * G, n = g == NB - 1 ? Gl : G;
+        const float2 m = L.um[u];
+        Cut32 cc;
+        cc.mu_f = m.x;
+        cc.mu = (double)m.x + (double)m.y;
+        cc.thr = L.thr[t];
+        band_bounds_f(L.thr_lo[t], L.thr_hi[t], fabsf(m.y), cc.lo_f, cc.hi_f);
+        const unsigned bit = 1u << (t0 + t - t_item);
+        const int rot = g % n;
+        float r = m.x;
+        if (cut.replace == REP_MEDIAN) {
+          // the median only where the bin has a flag
+          bool any = false;
+          for (int j = 0; j < n && !any; j++) any = flag32(L.tile[(c0 + j) * Ws + t], cc);
+          if (!any) continue;
+          r = bin_median_f32(L.tile, c0, n, Ws, t);
+        }
+        for (int j = 0; j < n; j++) {
+          int jj = j + rot;
+          if (jj >= n) jj -= n;
+          float* p = L.tile + (c0 + jj) * Ws + t;
+          if (flag32(*p, cc)) {
+            *p = r;
+            atomicOr(&L.fm[c0 + jj], bit);
+          }
+        }
+      }
+      __syncthreads();
+    }
+
+    // ---- store the sub-slab
+    for (int c = threadIdx.x; c < C; c += NT) {
+      float* a = dst + (size_t)c * T + t0;
+      const float* d = L.tile + c * Ws;
+      if (vec && w == Ws && Ws >= 4) {
+#pragma unroll 2
+        for (int j = 0; j < Ws; j += 4) *reinterpret_cast<float4*>(a + j) = *reinterpret_cast<const float4*>(d + j);
+      } else {
+        for (int j = 0; j < w; j++) a[j] = d[j];
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- flags
+  const int nt = t_end - t_item;
+  const unsigned valid = nt >= 32 ? 0xFFFFFFFFu : ((1u << nt) - 1u);
+  if (P.mask_kind == MASK_BITS && J.mask) {
+    const int W32 = (T + 31) >> 5;
+    unsigned* mb = static_cast<unsigned*>(J.mask) + item;
+    for (int c = threadIdx.x; c < C; c += NT) {
+      const unsigned f = L.fm[c] & valid;
+      unsigned* wp = mb + (size_t)c * W32;
+      if (P.mask_or) {
+        if (f) *wp = __ldcg(wp) | f;
+      } else {
+        *wp = f;
+      }
+    }
+  } else if (P.mask_kind == MASK_BYTES && J.mask) {
+    uint8_t* mb = static_cast<uint8_t*>(J.mask);
+    for (int u = threadIdx.x; u < C * nt; u += NT) {
+      const int c = u / nt, t = u % nt;
+      const unsigned f = (L.fm[c] >> t) & 1u;
+      uint8_t* bp = mb + (size_t)c * T + t_item + t;
+      if (P.mask_or) {
+        if (f) *bp = (uint8_t)(__ldcg(bp) | 2u);
+      } else {
+        *bp = (uint8_t)(f ? 2u : 0u);
+      }
+    }
+  }
+  __syncthreads();
+  (void)red;
+}
+
+// ---------------------------------------------------------------------------
+// persistent engine (float32)
+// ---------------------------------------------------------------------------
+__device__ bool wait_rows_f32(const Params& P, int job, unsigned need, int* flag) {
+  if (threadIdx.x == 0) {
+    int good = 1;
+    const unsigned* ctr = P.counters + 1 + job;
+    if (ld_acquire_u32(ctr) < need) {
+      const unsigned long long t0 = globaltimer_ns();
+      while (ld_acquire_u32(ctr) < need) {
+        if (globaltimer_ns() - t0 > P.spin_limit_ns) {
+          atomicExch(P.status, 5u);
+          good = 0;
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    *flag = good;
+  }
+  __syncthreads();
+  const bool ok = *flag != 0;
+  __syncthreads();
+  return ok;
+}
+
+__global__ void __launch_bounds__(NT, 2) k_engine_f32(const __grid_constant__ Params P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ Red32 red;
+  __shared__ int s_item, s_flag;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(P.counters, 1u);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= P.n_items) return;
+    int lo = 0, hi = P.n_segs - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (P.segs[mid].start <= item) lo = mid;
+      else hi = mid - 1;
+    }
+    const Seg sg = P.segs[lo];
+    const int idx = item - sg.start;
+    const Job& J = P.jobs[sg.job];
+    if (sg.kind == 0) {
+      tdsc_row_f32(P, J, idx, smem, &red);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        if (sg.job != P.withhold_job) atomicAdd(P.counters + 1 + sg.job, 1u);
+      }
+    } else {
+      if (P.wait_tdsc && !wait_rows_f32(P, sg.job, (unsigned)J.rows, &s_flag)) continue;
+      fdsc_item_f32(P, J, idx, smem, &red);
+    }
+  }
+}
+
+int engine_smem_f32(const Params& p) {
+  int s = 16;
+  for (int j = 0; j < p.n_jobs; j++) {
+    const Job& J = p.jobs[j];
+    if (p.td.iterations > 0) {
+      const int td = td32_smem_bytes(J.T);
+      s = s > td ? s : td;
+    }
+    if (p.fd.iterations > 0) {
+      const int fd = fd32_smem_bytes(J.ws, J.C, J.nb);
+      s = s > fd ? s : fd;
+    }
+  }
+  return s;
+}
+
+void* engine_kernel_f32() { return reinterpret_cast<void*>(&k_engine_f32); }
+
+int launch_engine_f32(const Params& p, const LaunchCfg& cfg, void* stream) {
+  k_engine_f32<<<cfg.grid, NT, cfg.smem, (cudaStream_t)stream>>>(p);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace rfim

@@ -1,0 +1,200 @@
+"""GPU parity of the float32 path against the CPU oracle.
+
+Tolerance (float32): a mask disagreement is allowed only where the oracle's
+decision lies within 1e-9 relative of its threshold, |(|x - mu| - k sigma)| <=
+1e-9 k sigma (the oracle reports that distance per sample); such
+disagreements are counted.  Samples neither side flags must be bit-identical
+to the input; samples both sides replace must agree within 1e-6 relative.
+Samples in a row or column after a counted disagreement are not compared
+value by value (the replacement changes later statistics of that row or column).
+"""
+import numpy as np
+import pytest
+
+from gpu_util import run_gpu
+
+pytestmark = pytest.mark.gpu
+
+MARGIN = 1e-9
+REL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch  # noqa: F401
+
+    from paper_2001_03389_gb300 import build
+
+    build.build()
+    from paper_2001_03389_gb300 import rfim
+
+    c = rfim.Context(0)
+    yield c
+    c.close()
+
+
+def check_f32(oracle, ctx, x, td=None, fd=None, mask_fmt="bits", **kw):
+    """Returns the number of (allowed) mask disagreements."""
+    want, wf, margin = oracle.clean_f32_margin(x, "bct", tdsc=td, fdsc=fd)
+    got, gf = run_gpu(ctx, x, tdsc=td, fdsc=fd, mask_fmt=mask_fmt, **kw)
+    wflag = wf > 0
+    if mask_fmt == "bits":
+        gflag = gf
+        dis = gflag != wflag
+    elif mask_fmt == "bytes":
+        gflag = gf > 0
+        dis = gf != wf
+    else:
+        gflag = got != x  # no mask: changed samples (a replaced value can equal the original)
+        dis = np.zeros_like(wflag)
+    nd = int(dis.sum())
+    if nd:
+        bad = dis & ~(margin <= MARGIN)
+        assert not bad.any(), (f"{int(bad.sum())} mask disagreements farther than {MARGIN} from the threshold, "
+                               f"first at {np.argwhere(bad)[:3].tolist()}, margins {margin[bad][:3]}")
+    # rows and columns touched by a disagreement are excluded from the value checks
+    ok = np.ones_like(wflag)
+    for b, c, t in np.argwhere(dis):
+        ok[b, c, :] = False
+        ok[b, :, t] = False
+    keep = ok & ~wflag & ~gflag if mask_fmt is not None else ok & ~wflag
+    assert np.array_equal(got[keep].view(np.uint32), x[keep].view(np.uint32)), "unflagged samples changed"
+    both = ok & wflag & (gflag if mask_fmt is not None else True)
+    if both.any():
+        err = np.abs(got[both].astype(np.float64) - want[both].astype(np.float64))
+        tol = REL * np.maximum(np.abs(want[both].astype(np.float64)), 1e-30)
+        assert np.all(err <= tol), f"replaced values differ: max rel {np.max(err / tol) * REL:.3g}"
+    return nd
+
+
+def chi2_block(rng, B, C, T, gain=True):
+    g = np.exp(rng.uniform(np.log(0.5), np.log(2.0), size=(B, C, 1))) if gain else np.ones((B, C, 1))
+    x = (rng.standard_exponential((B, C, T)) * 2.0 * g).astype(np.float32)
+    if x.size > 16:
+        flat = x.reshape(-1)
+        idx = rng.integers(0, flat.size, max(1, flat.size // 100))
+        flat[idx] *= 6.0
+        if C > 4:
+            x[:, C // 3, :] += 8.0 * g[:, C // 3]  # a narrowband channel
+    return x
+
+
+@pytest.mark.parametrize("C,T", [(1, 1), (1, 5), (3, 7), (5, 33), (37, 64), (64, 100), (100, 257), (33, 1031),
+                                 (4, 8192), (2, 20001)])
+@pytest.mark.parametrize("rep", ["mean", "median"])
+def test_tdsc_f32_shapes(oracle, ctx, C, T, rep):
+    rng = np.random.default_rng(C * 1000 + T + 7)
+    x = chi2_block(rng, 2, C, T)
+    for it, k in [(1, 3.0), (3, 2.5)]:
+        check_f32(oracle, ctx, x, td=dict(k=k, iterations=it, replace=rep), api="tdsc")
+
+
+@pytest.mark.parametrize("C,T,bin", [(1, 40, 1), (4, 33, 4), (32, 64, 32), (37, 70, 32), (64, 31, 7),
+                                     (100, 50, 3), (130, 96, 32), (96, 40, 96), (4096, 40, 32), (257, 33, 16)])
+@pytest.mark.parametrize("rep", ["mean", "median"])
+def test_fdsc_f32_shapes(oracle, ctx, C, T, bin, rep):
+    rng = np.random.default_rng(C * 7 + T + bin)
+    x = chi2_block(rng, 2, C, T)
+    for it, k in [(1, 3.0), (3, 2.5)]:
+        check_f32(oracle, ctx, x, fd=dict(k=k, iterations=it, replace=rep, bin=bin), api="fdsc")
+
+
+@pytest.mark.parametrize("C,T", [(64, 2048), (100, 777), (1536, 96), (48, 5003)])
+def test_clean_f32_fused(oracle, ctx, C, T):
+    rng = np.random.default_rng(C + T)
+    x = chi2_block(rng, 3, C, T)
+    for rep in ("mean", "median"):
+        td = dict(k=2.5, iterations=3, replace=rep)
+        fd = dict(k=2.5, iterations=3, replace=rep, bin=32)
+        check_f32(oracle, ctx, x, td=td, fd=fd)
+        check_f32(oracle, ctx, x, td=td, fd=fd, mask_fmt="bytes")
+        check_f32(oracle, ctx, x, td=td, fd=fd, mask_fmt=None)
+
+
+@pytest.mark.parametrize("in_off,out_off", [(4, 0), (12, 8), (8, 8), (0, 4)])
+def test_f32_misaligned_and_in_place(oracle, ctx, in_off, out_off):
+    rng = np.random.default_rng(in_off * 31 + out_off)
+    x = chi2_block(rng, 2, 40, 301)
+    td = dict(k=2.5, iterations=2, replace="median")
+    fd = dict(k=2.5, iterations=2, replace="mean", bin=8)
+    check_f32(oracle, ctx, x, td=td, fd=fd, in_off=in_off, out_off=out_off)
+    check_f32(oracle, ctx, x, td=td, fd=fd, in_place=True, in_off=in_off)
+
+
+def test_f32_value_distributions(oracle, ctx):
+    rng = np.random.default_rng(77)
+    td = dict(k=3.0, iterations=3, replace="mean")
+    fd = dict(k=3.0, iterations=3, replace="mean", bin=32)
+    cases = [
+        rng.normal(128.0, 16.0, (2, 64, 500)),          # offset data, mean/sigma = 8
+        rng.normal(0.0, 1.0, (2, 64, 500)),             # signed, zero mean
+        rng.normal(1.0e4, 1.0, (1, 64, 300)),           # mean/sigma = 1e4: the FP64 two-pass
+        rng.standard_cauchy((1, 64, 300)) * 10.0,       # heavy tails
+        np.round(rng.normal(100.0, 3.0, (1, 64, 300))),  # integer-valued with ties
+    ]
+    for x in cases:
+        check_f32(oracle, ctx, x.astype(np.float32), td=td, fd=fd)
+        check_f32(oracle, ctx, x.astype(np.float32), td=dict(td, replace="median"), fd=dict(fd, replace="median"))
+
+
+def test_f32_degenerate(oracle, ctx):
+    x = np.full((1, 16, 64), 2.5, np.float32)
+    check_f32(oracle, ctx, x, td=dict(k=3.0, iterations=3), fd=dict(k=3.0, iterations=3, bin=4))
+    x = np.zeros((1, 8, 40), np.float32)
+    check_f32(oracle, ctx, x, td=dict(k=1.0, iterations=2), fd=dict(k=1.0, iterations=2, bin=8))
+    x = np.tile(np.array([-1.0, 1.0], np.float32), (1, 6, 20))
+    check_f32(oracle, ctx, x, td=dict(k=0.5, iterations=2, replace="median"), fd=dict(k=0.6, iterations=2, bin=2))
+    x = np.zeros((1, 4, 10), np.float32)
+    x[0, :, 3] = -0.0
+    x[0, 1, :] = 7.0
+    check_f32(oracle, ctx, x, td=dict(k=0.3, iterations=2, replace="median"), fd=dict(k=0.4, iterations=2, bin=2))
+
+
+def test_f32_many_k(oracle, ctx):
+    rng = np.random.default_rng(5)
+    x = chi2_block(rng, 1, 24, 600)
+    for k in (0.3, 0.999, 1.0, 1.5, 2.0, 2.5, 3.25, 4.0, 7.5, 100.0):
+        check_f32(oracle, ctx, x, td=dict(k=k, iterations=2, replace="median"), fd=dict(k=k, iterations=2, bin=5))
+
+
+def test_cfg3_full_beam(oracle, ctx):
+    # one full beam of the float32 configuration: 4096 x 8192, fused, k = 2.5, 3 iterations, mean
+    from paper_2001_03389_gb300 import synth
+
+    spec = synth.CONFIGS[3]
+    x = synth.make_beams(3, beams=[0])
+    nd = check_f32(oracle, ctx, x, td=spec["tdsc"], fd=spec["fdsc"])
+    print(f"cfg3 beam 0: {nd} allowed mask disagreements")
+
+
+def test_f32_tile_widths(oracle, ctx):
+    rng = np.random.default_rng(21)
+    x = chi2_block(rng, 2, 300, 203)
+    td = dict(k=2.5, iterations=2, replace="mean")
+    fd = dict(k=2.5, iterations=2, replace="mean", bin=32)
+    try:
+        for ws in (8, 4, 2, 1):
+            ctx.set_option("tile_samples", ws)
+            check_f32(oracle, ctx, x, td=td, fd=fd)
+        ctx.set_option("tile_samples", 0)
+        for sch in (1, 2):
+            ctx.set_option("schedule", sch)
+            check_f32(oracle, ctx, x, td=td, fd=fd)
+    finally:
+        ctx.set_option("tile_samples", 0)
+        ctx.set_option("schedule", 0)
+
+
+def test_f32_validation(ctx):
+    import torch
+
+    from paper_2001_03389_gb300 import rfim
+
+    row = torch.zeros((1, 1, 60000), dtype=torch.float32, device="cuda:0")
+    with pytest.raises(rfim.RfimError) as e:
+        ctx.tdsc(ctx.block(row, torch.empty_like(row)), rfim.make_cut(3.0))
+    assert e.value.status == rfim.ERR_ARG
+    big = torch.zeros((1, 40000, 4), dtype=torch.float32, device="cuda:0")
+    with pytest.raises(rfim.RfimError) as e:
+        ctx.fdsc(ctx.block(big, torch.empty_like(big)), rfim.make_cut(3.0, bin=32))
+    assert e.value.status == rfim.ERR_RANGE

@@ -444,3 +444,22 @@ def test_paper_accuracy_claims_cfg1(oracle):
     on_bb = bb[ps]
     assert ft[cs[~on_bb], ps[~on_bb]].mean() < 0.2
     assert ff[cs[~on_bb], ps[~on_bb]].mean() < 0.2
+
+
+def test_f32_margin_diagnostic(oracle):
+    # Row [0, 0, 0, 4], k = 1, one iteration: mu = 1, sigma = sqrt(3) (population).
+    # |x - mu| is 1 for the zeros and 3 for the 4, so the relative distances from
+    # k sigma are |1 - sqrt 3| / sqrt 3 and |3 - sqrt 3| / sqrt 3; the 4 is flagged.
+    import math
+
+    x = np.array([[[0, 0, 0, 4]]], np.float32)
+    out, fl, mg = oracle.clean_f32_margin(x, "bct", tdsc=dict(k=1.0, iterations=1))
+    s3 = math.sqrt(3.0)
+    assert np.allclose(mg[0, 0], [abs(1 - s3) / s3] * 3 + [abs(3 - s3) / s3], rtol=1e-12)
+    assert fl[0, 0].tolist() == [0, 0, 0, 1]
+    want, wf = oracle.clean(x, "bct", tdsc=dict(k=1.0, iterations=1))
+    assert np.array_equal(out, want) and np.array_equal(fl, wf)
+    # a constant column: sigma = 0, no decision has a finite margin
+    y = np.full((1, 4, 3), 2.5, np.float32)
+    _, fl2, mg2 = oracle.clean_f32_margin(y, "bct", fdsc=dict(k=2.0, iterations=2, bin=2))
+    assert np.all(np.isinf(mg2)) and not fl2.any()
