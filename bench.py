@@ -30,11 +30,16 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-CFG = 2
+CFG = 2  # the ARTS batch; --config 3 times the float32 workload instead
 METRIC = "cleaned filterbank GB/s (TDSC+FDSC) & % HBM peak; p99 chunk latency"
 UNIT = "GB/s"
-ALG_BYTES_PER_SAMPLE = 1 + 1 + 1 / 8  # uint8 read + write + 1-bit mask
 NOMINAL_HBM_GBS = 8000.0
+
+
+def alg_bytes_per_sample(dtype):
+    """Read + write of the sample plus its mask bit: 2.125 B (uint8), 8.125 B (float32)."""
+    es = 1 if dtype == "u8" else 4
+    return es + es + 1 / 8
 
 
 def peaks():
@@ -61,12 +66,15 @@ def workload_config():
 
 
 def config_json(spec, n):
+    es = 1 if spec["dtype"] == "u8" else 4
+    mb = spec["B"] * spec["C"] * spec["T"] * es / 1e6
+    name = "arts" if CFG == 2 else "fp32"
     return {
-        "workload": f"arts_{spec['B']}x{spec['C']}x{spec['T']}_u8_bct_tdsc_then_fdsc",
-        "beams": spec["B"], "channels": spec["C"], "samples": spec["T"], "dtype": "u8", "layout": "BCT",
+        "workload": f"{name}_{spec['B']}x{spec['C']}x{spec['T']}_{spec['dtype']}_bct_tdsc_then_fdsc",
+        "beams": spec["B"], "channels": spec["C"], "samples": spec["T"], "dtype": spec["dtype"], "layout": "BCT",
         "tdsc": spec["tdsc"], "fdsc": spec["fdsc"], "mask": "bits",
         "global_batch": spec["B"] * n, "parallelism": f"replicas{n}" if n > 1 else "single",
-        "l2": "inputs larger than L2 (230.4 MB read + 230.4 MB written per step vs 135.5 MB L2)",
+        "l2": f"inputs larger than L2 ({mb:.1f} MB read + {mb:.1f} MB written per step vs 135.5 MB L2)",
     }
 
 
@@ -185,7 +193,7 @@ def run_reference(args):
     v = tot_b / tot_t / 1e9
     out = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
            "ms_per_step": tot_t / K * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "u8", "data": "synthetic", "impl": "reference",
+           "dtype": spec["dtype"], "data": "synthetic", "impl": "reference",
            "config": config_json(spec, 1),
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": f"per step: 1 beam x {spec['C']} channels x {T_s} samples, full TDSC+FDSC"},
@@ -217,14 +225,22 @@ def run_gpu(args):
         torch.distributed.barrier()
     from paper_2001_03389_gb300 import rfim, synth
 
-    spec = workload_config()
+    spec = dict(workload_config())
+    if args.beams:
+        spec["B"] = args.beams  # a smaller batch of the same beams (profiling captures)
     B, C, T = spec["B"], spec["C"], spec["T"]
-    x = synth.make_beams(CFG)
+    if spec["dtype"] == "u8":
+        x = synth.make_beams(CFG, beams=range(B))
+        xin = torch.from_numpy(x).to(dev)
+    else:
+        # 4.3 GB: drawn on the device (same model; the oracle timing uses the numpy beams)
+        xin = synth.torch_make_beams(CFG, B, synth.seed_of(CFG), dev)
+        x = xin.cpu().numpy()
     nbytes = x.nbytes
-    xin = torch.from_numpy(x).to(dev)
     out = torch.empty_like(xin)
     mask = torch.zeros(rfim.mask_words(C, T, B), dtype=torch.int32, device=dev)
     ctx = rfim.Context(local)
+    dt = rfim.U8 if spec["dtype"] == "u8" else rfim.F32
     td, fd = rfim.make_cut(**spec["tdsc"]), rfim.make_cut(**spec["fdsc"])
     blk = ctx.block(xin, out, mask, "bct", "bits")
     stream = torch.cuda.Stream(device=dev)
@@ -286,7 +302,7 @@ def run_gpu(args):
     hin = torch.from_numpy(x).pin_memory()
     hout = torch.empty_like(hin).pin_memory()
     hmask = torch.empty(rfim.mask_words(C, T, B), dtype=torch.int32).pin_memory()
-    hblk = rfim.rfim_block(hin.data_ptr(), hout.data_ptr(), hmask.data_ptr(), B, C, T, rfim.U8, rfim.LAYOUT_BCT,
+    hblk = rfim.rfim_block(hin.data_ptr(), hout.data_ptr(), hmask.data_ptr(), B, C, T, dt, rfim.LAYOUT_BCT,
                            rfim.MASK_BITS)
     for _ in range(2):
         ctx.clean_host(hblk, td, fd)
@@ -308,19 +324,19 @@ def run_gpu(args):
 
     if rank == 0:
         peak, peak_kind = peaks()
-        alg = ALG_BYTES_PER_SAMPLE * B * C * T
+        alg = alg_bytes_per_sample(spec["dtype"]) * B * C * T
         achieved = alg / (avg_launch_ms * 1e-3) / 1e9
         traffic = profiled_traffic()
         res = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
             "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "u8", "data": "synthetic", "config": config_json(spec, ws),
+            "dtype": spec["dtype"], "data": "synthetic", "config": config_json(spec, ws),
             "samples_per_s": B * C * T * K * ws / (total_ms * 1e-3),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": f"{peak_kind} copy (MEASURED_PEAKS.json hbm_gbs)",
                          "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS,
-                         "kernel": "k_engine_u8 (fused TDSC->FDSC persistent work queue)",
+                         "kernel": PROFILES[CFG][2],
                          "alg_bytes_per_launch": alg, "avg_launch_ms": avg_launch_ms},
             "e2e": e2e, "e2e_matches_device": ok,
             "gpu_launches": K,
@@ -336,10 +352,19 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
 
 
+# per workload: the committed ncu summary of its kernel, the kernel's sources, its name
+PROFILES = {
+    2: ("engine_u8_arts12.md", ("common.cuh", "engine.h", "engine_u8.cu"),
+        "k_engine_u8 (fused TDSC->FDSC persistent work queue)"),
+    3: ("engine_f32_fp32x32.md", ("common.cuh", "engine.h", "engine_f32.cu"),
+        "k_engine_f32 (fused TDSC->FDSC persistent work queue)"),
+}
+
+
 def profiled_traffic():
     """DRAM bytes per launch of the engine kernel from the committed ncu summary,
     or None when the kernel sources changed since that capture."""
-    prof = os.path.join(ROOT, "profiles", "engine_u8_arts12.md")
+    prof = os.path.join(ROOT, "profiles", PROFILES[CFG][0])
     if not os.path.exists(prof):
         return None
     vals = {}
@@ -358,16 +383,13 @@ def profiled_traffic():
         return None
 
 
-ENGINE_SOURCES = ("common.cuh", "engine.h", "engine_u8.cu")
-
-
 def source_hash():
-    """Hash of the sources the engine kernel is compiled from."""
+    """Hash of the sources the engine kernel of the workload is compiled from."""
     import hashlib
 
     h = hashlib.sha256()
     cs = os.path.join(ROOT, "paper_2001_03389_gb300", "csrc")
-    for f in ENGINE_SOURCES:
+    for f in PROFILES[CFG][1]:
         with open(os.path.join(cs, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -376,12 +398,19 @@ def source_hash():
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default 2000, or 300 with --config 3)")
+    ap.add_argument("--config", type=int, default=2, choices=[2, 3],
+                    help="2: the ARTS uint8 batch (the reported workload); 3: the float32 workload")
     ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--beams", type=int, default=None, help="clean only the first N beams (profiling captures)")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="warm-up and plain steps only (for ncu captures)")
     args = ap.parse_args()
+    global CFG
+    CFG = args.config
+    if args.steps is None:
+        args.steps = 2000 if CFG == 2 else 300
     if args.impl == "reference":
         run_reference(args)
     else:

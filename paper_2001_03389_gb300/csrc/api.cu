@@ -260,6 +260,7 @@ Job make_job(const rfim_block* b, int j, const CutNorm& fd, int tile_samples, in
     // float32: one CTA per TDSC row; FDSC sub-slab of 8, 4, 2 or 1 samples
     J.td_mode = 1;
     J.td_items = C;
+    J.fd_items = (T + FD32_ITEM_T - 1) / FD32_ITEM_T;
     J.ws = 1;
     for (int ws : {8, 4, 2})
       if ((tile_samples == 0 || ws <= tile_samples) && fd32_smem_bytes(ws, C, J.nb) <= smem_target) {

@@ -110,24 +110,19 @@ __device__ __forceinline__ FF warp_ff(FF a) {
 // Decisions
 // ---------------------------------------------------------------------------
 // One cut of one iteration of one row or (column, bin): samples y with
-// |y - mu| > thr are flagged.  mu_f = (float)mu; [lo_f, hi_f] is the band in
-// which the FP32 value |y - mu_f| cannot decide.
+// |y - mu| > thr are flagged, mu and thr doubles.  mu_f = (float)mu; [lo_f, hi_f]
+// is the band in which the float32 value |y - mu_f| cannot decide.  The
+// doubles are read only inside the band: mu = mu_hi + mu_lo (exact), thr at *thr.
 struct Cut32 {
-  float mu_f, lo_f, hi_f;
-  double mu, thr;
+  float mu_f, mu_lo, lo_f, hi_f;
+  const double* thr;
 };
 
-// thr and the rounding error dm = |mu - mu_f| (both >= 0) -> FP32 bounds.
+// thr and the rounding error dm = |mu - mu_f| (both >= 0) -> float32 bounds.
 // |fl(y - mu_f)| = a satisfies |y - mu_f| in [a / (1 + u), a / (1 - u)], u = 2^-24,
 // and | |y - mu| - |y - mu_f| | <= dm, so a > (thr + dm)(1 + 2^-20) proves a flag
-// and a <= (thr - dm)(1 - 2^-20) proves a keep.
-__device__ __forceinline__ void band_bounds(double thr, double dm, float& lo_f, float& hi_f) {
-  hi_f = __double2float_ru((thr + dm) * (1.0 + 0x1p-20));
-  lo_f = __double2float_rd((thr - dm) * (1.0 - 0x1p-20));
-}
-
-// The same bounds from FP32 inputs: thr_hi >= thr >= thr_lo (float bounds of
-// the FP64 threshold) and dm >= |mu - mu_f|.
+// and a <= (thr - dm)(1 - 2^-20) proves a keep.  thr_lo <= thr <= thr_hi are
+// float bounds of the double threshold.
 __device__ __forceinline__ void band_bounds_f(float thr_lo, float thr_hi, float dm, float& lo_f, float& hi_f) {
   const float h = __fadd_ru(thr_hi, dm);
   hi_f = __fmul_ru(h, 1.0f + 0x1p-20f);
@@ -135,11 +130,17 @@ __device__ __forceinline__ void band_bounds_f(float thr_lo, float thr_hi, float 
   lo_f = __fmul_rd(l, 1.0f - 0x1p-20f);
 }
 
+// The double expression, kept out of line so that it runs only inside the band.
+__device__ __noinline__ bool flag64(float y, float mu_hi, float mu_lo, const double* thr) {
+  const double mu = (double)mu_hi + (double)mu_lo;
+  return fabs((double)y - mu) > *thr;
+}
+
 __device__ __forceinline__ bool flag32(float y, const Cut32& c) {
   const float a = fabsf(__fsub_rn(y, c.mu_f));
   if (a > c.hi_f) return true;
   if (!(a > c.lo_f)) return false;
-  return fabs((double)y - c.mu) > c.thr;  // inside the band: the FP64 expression
+  return flag64(y, c.mu_f, c.mu_lo, c.thr);
 }
 
 // Total order of floats as unsigned keys (-0 before +0).
@@ -306,15 +307,33 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
     ff_acc_sq(Q, v.w);
   }
   block_ff2(S, Q, red);
-  double Sd = ff_d(S), Qd = ff_d(Q);
+  // running sums of the current values (used by thread 0 only)
+  double Sd = 0.0, Qd = 0.0;
+  if (threadIdx.x == 0) {
+    Sd = ff_d(S);
+    Qd = ff_d(Q);
+  }
+  struct RowStat {
+    double mu_thr[2];
+    double var;
+    float mu_f, mu_lo, lo_f, hi_f;
+    int prec;
+  };
+  __shared__ RowStat rs_s;
+  RowStat* rs_ = &rs_s;
   const double Tn = (double)T;
   const int I = cut.iterations;
 
   for (int it = 0; it < I; it++) {
-    // statistics of the current values (every thread computes the same doubles)
-    const double mu = Sd / Tn;
-    double var = Qd / Tn - mu * mu;
-    if (!(var >= 1e-3 * (Qd / Tn))) {
+    // statistics of the current values, finished in double by one thread
+    if (threadIdx.x == 0) {
+      const double mu = Sd / Tn;
+      const double var = Qd / Tn - mu * mu;
+      rs_->prec = !(var >= 1e-3 * (Qd / Tn));
+      rs_->var = var;
+    }
+    __syncthreads();
+    if (rs_->prec) {
       // cancellation (or a constant row): FP64 two-pass over the current values
       double s = 0.0;
       for (int k = threadIdx.x; k < nch; k += NT) {
@@ -335,17 +354,31 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
           }
       }
       ss = block_dsum(ss, red);
-      var = ss / Tn;
-      // use the two-pass mean too
-      Sd = s;
+      if (threadIdx.x == 0) {
+        rs_->var = ss / Tn;
+        Sd = s;  // the two-pass mean
+      }
     }
-    const double mu_use = Sd / Tn;
-    const double thr = cut.k * sqrt(var > 0.0 ? var : 0.0);
+    if (threadIdx.x == 0) {
+      const double mu = Sd / Tn;
+      const double var = rs_->var;
+      const double thr = cut.k * sqrt(var > 0.0 ? var : 0.0);
+      rs_->mu_thr[0] = mu;
+      rs_->mu_thr[1] = thr;
+      const float mu_f = __double2float_rn(mu);
+      rs_->mu_f = mu_f;
+      rs_->mu_lo = __double2float_rn(mu - (double)mu_f);
+      const double dm = fabs(mu - (double)mu_f);
+      rs_->hi_f = __double2float_ru((thr + dm) * (1.0 + 0x1p-20));
+      rs_->lo_f = __double2float_rd((thr - dm) * (1.0 - 0x1p-20));
+    }
+    __syncthreads();
     Cut32 c;
-    c.mu = mu_use;
-    c.thr = thr;
-    c.mu_f = __double2float_rn(mu_use);
-    band_bounds(thr, fabs(mu_use - (double)c.mu_f), c.lo_f, c.hi_f);
+    c.mu_f = rs_->mu_f;
+    c.mu_lo = rs_->mu_lo;
+    c.lo_f = rs_->lo_f;
+    c.hi_f = rs_->hi_f;
+    c.thr = &rs_->mu_thr[1];
     const float r = cut.replace == REP_MEDIAN ? row_median_f32(st, nch, head, tail, T, red) : c.mu_f;
 
     // decide and replace; the replaced values go to a list for the statistics update
@@ -381,9 +414,11 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
         ff_acc_sq(rq, lst[i]);
       }
       block_ff2(rs, rq, red);
-      const double rd = (double)r;
-      Sd = Sd - ff_d(rs) + (double)nflag * rd;
-      Qd = Qd - ff_d(rq) + (double)nflag * rd * rd;
+      if (threadIdx.x == 0) {
+        const double rd = (double)r;
+        Sd = Sd - ff_d(rs) + (double)nflag * rd;
+        Qd = Qd - ff_d(rq) + (double)nflag * rd * rd;
+      }
     } else {
       // many replacements: sum the current row again
       for (int k = threadIdx.x; k < nch; k += NT) {
@@ -398,8 +433,10 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
         ff_acc_sq(rq, v.w);
       }
       block_ff2(rs, rq, red);
-      Sd = ff_d(rs);
-      Qd = ff_d(rq);
+      if (threadIdx.x == 0) {
+        Sd = ff_d(rs);
+        Qd = ff_d(rq);
+      }
     }
   }
   __syncthreads();
@@ -445,7 +482,9 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
 }
 
 // ---------------------------------------------------------------------------
-// FDSC on one item: FD_ITEM_T time samples x C channels of a float32 beam
+// FDSC on one item: FD32_ITEM_T time samples x C channels of a float32 beam.
+// 16 samples are 64 bytes of each channel row: the lines an item touches stay
+// in L2 across its sub-slabs even with every SM's items in flight.
 // ---------------------------------------------------------------------------
 // Tile [c][t] (pitch ws floats).  Work units are (t, bin) pairs, one thread
 // each, t fastest; a unit walks its bin starting at a rotation of (bin mod 32)
@@ -502,8 +541,8 @@ __device__ float bin_median_f32(const float* tile, int c0, int n, int ws, int t)
 __device__ void fdsc_item_f32(const Params& P, const Job& J, int item, unsigned char* smem, Red32* red) {
   const CutDev& cut = P.fd;
   const int C = J.C, T = J.T, G = cut.bin, NB = J.nb, Gl = J.last_g;
-  const int t_item = item * FD_ITEM_T;
-  const int t_end = min(t_item + FD_ITEM_T, T);
+  const int t_item = item * FD32_ITEM_T;
+  const int t_end = min(t_item + FD32_ITEM_T, T);
   const int Ws = J.ws;
   const float* src = static_cast<const float*>(P.fd_reads_out ? J.out : J.in);
   float* dst = static_cast<float*>(J.out);
@@ -605,8 +644,8 @@ __device__ void fdsc_item_f32(const Params& P, const Job& J, int item, unsigned 
         const float2 m = L.um[u];
         Cut32 cc;
         cc.mu_f = m.x;
-        cc.mu = (double)m.x + (double)m.y;
-        cc.thr = L.thr[t];
+        cc.mu_lo = m.y;
+        cc.thr = &L.thr[t];
         band_bounds_f(L.thr_lo[t], L.thr_hi[t], fabsf(m.y), cc.lo_f, cc.hi_f);
         const unsigned bit = 1u << (t0 + t - t_item);
         const int rot = g % n;
@@ -645,20 +684,20 @@ __device__ void fdsc_item_f32(const Params& P, const Job& J, int item, unsigned 
     __syncthreads();
   }
 
-  // ---- flags
+  // ---- flags.  Two items share a mask word: each changes only its own bit
+  //      field (the last item of a row also clears the padding bits above it).
   const int nt = t_end - t_item;
-  const unsigned valid = nt >= 32 ? 0xFFFFFFFFu : ((1u << nt) - 1u);
+  const unsigned valid = (1u << nt) - 1u;  // nt <= 16
   if (P.mask_kind == MASK_BITS && J.mask) {
     const int W32 = (T + 31) >> 5;
-    unsigned* mb = static_cast<unsigned*>(J.mask) + item;
+    const int sh = t_item & 31;
+    unsigned* mb = static_cast<unsigned*>(J.mask) + (t_item >> 5);
+    const unsigned field = t_end == T ? (0xFFFFFFFFu << sh) : (0xFFFFu << sh);
     for (int c = threadIdx.x; c < C; c += NT) {
-      const unsigned f = L.fm[c] & valid;
+      const unsigned f = (L.fm[c] & valid) << sh;
       unsigned* wp = mb + (size_t)c * W32;
-      if (P.mask_or) {
-        if (f) *wp = __ldcg(wp) | f;
-      } else {
-        *wp = f;
-      }
+      if (!P.mask_or) atomicAnd(wp, ~field);
+      if (f) atomicOr(wp, f);
     }
   } else if (P.mask_kind == MASK_BYTES && J.mask) {
     uint8_t* mb = static_cast<uint8_t*>(J.mask);

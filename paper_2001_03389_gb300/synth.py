@@ -108,7 +108,7 @@ def beam_f32(cfg_seed: int, beam: int, C: int, T: int, model: RFIModel, layout: 
     g = np.exp(rng.uniform(np.log(0.5), np.log(2.0), size=C)).astype(np.float32)
     x = rng.standard_exponential((C, T), dtype=np.float32)
     x *= 2.0                       # chi^2 with 2 degrees of freedom
-    x += _rfi_offsets(rng, C, T, model, 1.0)  # in sigma units (sigma of chi^2_2 is 2)
+    x += _rfi_offsets(rng, C, T, model, 2.0)  # amplitudes in sigma units (sigma of chi^2_2 is 2)
     x *= g[:, None]
     return np.ascontiguousarray(x.T) if layout == "btc" else x
 
@@ -188,14 +188,13 @@ def stream_chunk(beam: int, chunk: int, C: int = 1536, T: int = 1250) -> np.ndar
 # oracle on copies of these bytes.)
 # ---------------------------------------------------------------------------
 
-def torch_beam_u8(gen, C: int, T: int, model: RFIModel, device):
-    """One uint8 beam (C, T) on `device`: round(N(128, 16^2) + RFI) clipped."""
+def _torch_rfi(gen, C: int, T: int, model: RFIModel, device):
+    """Additive RFI of one beam as a float32 (C, T) device tensor (the RFIModel recipe)."""
     import math
 
     import torch
 
-    x = torch.randn((C, T), generator=gen, device=device, dtype=torch.float32)
-    x.mul_(16.0).add_(128.0)
+    add = torch.zeros((C, T), device=device, dtype=torch.float32)
     n_nb = model.nb_count if model.nb_count is not None else int(round(model.nb_frac * C))
     if n_nb > 0:
         chans = torch.randperm(C, generator=gen, device=device)[:n_nb]
@@ -203,21 +202,56 @@ def torch_beam_u8(gen, C: int, T: int, model: RFIModel, device):
         if model.nb_sine:
             P = 500.0 + 4500.0 * torch.rand((n_nb, 1), generator=gen, device=device)
             phi = 2 * math.pi * torch.rand((n_nb, 1), generator=gen, device=device)
-            x[chans] += model.nb_amp * (1.0 + 0.5 * torch.sin(2 * math.pi * t[None, :] / P + phi))
+            add[chans] += model.nb_amp * (1.0 + 0.5 * torch.sin(2 * math.pi * t[None, :] / P + phi))
         else:
-            x[chans] += model.nb_amp
+            add[chans] += model.nb_amp
     n_bb = model.bb_count if model.bb_count is not None else int(round(model.bb_frac * T / max(model.bb_width, 1)))
     if n_bb > 0:
         starts = torch.randperm(max(T - model.bb_width + 1, 1), generator=gen, device=device)[:n_bb]
         for w in range(model.bb_width):
-            x[:, starts + w] += model.bb_amp
+            add[:, starts + w] += model.bb_amp
     if model.disp_amp:
         t0 = int(torch.randint(0, max(T // 2, 1), (1,), generator=gen, device=device).item())
-        delays = torch.from_numpy(_dispersion_delays(C, model.disp_span)).to(device)
-        ts = t0 + delays
+        ts = t0 + torch.from_numpy(_dispersion_delays(C, model.disp_span)).to(device)
         ok = ts < T
-        x[torch.arange(C, device=device)[ok], ts[ok]] += model.disp_amp
+        add[torch.arange(C, device=device)[ok], ts[ok]] += model.disp_amp
+    return add
+
+
+def torch_beam_u8(gen, C: int, T: int, model: RFIModel, device):
+    """One uint8 beam (C, T) on `device`: round(N(128, 16^2) + RFI) clipped."""
+    import torch
+
+    x = torch.randn((C, T), generator=gen, device=device, dtype=torch.float32)
+    x.mul_(16.0).add_(128.0).add_(_torch_rfi(gen, C, T, model, device))
     return x.round_().clamp_(0, 255).to(torch.uint8)
+
+
+def torch_beam_f32(gen, C: int, T: int, model: RFIModel, device):
+    """One float32 beam (C, T) on `device`: g_c (chi^2_2 noise + RFI in sigma units)."""
+    import math
+
+    import torch
+
+    g = torch.exp(math.log(0.5) + (math.log(2.0) - math.log(0.5)) * torch.rand((C, 1), generator=gen, device=device))
+    x = torch.empty((C, T), device=device, dtype=torch.float32).exponential_(1.0, generator=gen)
+    x.mul_(2.0).add_(_torch_rfi(gen, C, T, model, device), alpha=2.0)
+    return x.mul_(g)
+
+
+def torch_make_beams(cfg: int, beams: int, seed: int, device):
+    """A (beams, C, T) device block of a fixed-shape configuration, drawn on the device."""
+    import torch
+
+    spec = CONFIGS[cfg]
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    fn = torch_beam_u8 if spec["dtype"] == "u8" else torch_beam_f32
+    dt = torch.uint8 if spec["dtype"] == "u8" else torch.float32
+    out = torch.empty((beams, spec["C"], spec["T"]), dtype=dt, device=device)
+    for b in range(beams):
+        out[b] = fn(gen, spec["C"], spec["T"], spec["model"](), device)
+    return out
 
 
 def torch_ragged_batch(shapes, seed: int, device, layout: str = "bct"):
