@@ -230,40 +230,67 @@ rfim_status rfim_device_status(rfim_ctx* ctx, void* stream);
 
 /*
  * Open the streaming service: n_beams beams of `channels` x `chunk_samples`
- * chunks (BCT layout per chunk), cleaned with the given cuts (either may be
- * NULL).  Device slots are allocated up to the context's HBM budget; a
- * dispatcher thread closes micro-batches and launches them on several CUDA
- * streams so that batches overlap on the device.
+ * chunks (BCT layout per chunk) of dtype, cleaned with the given cuts (either
+ * may be NULL; rfim_clean semantics, bit mask output).
+ *   - Slots: each holds one chunk's cleaned output and bit mask in device
+ *     memory.  As many are allocated as the context's HBM budget allows
+ *     (rfim_create; 0 = a quarter of the free device memory), at most four per
+ *     beam.  A chunk is admitted only when a slot is free.
+ *   - A dispatcher thread launches everything waiting (up to 160 chunks) as
+ *     one micro-batch on whichever of four CUDA streams is idle, so batches
+ *     overlap on the device; completion is signalled from the stream.
+ *   - Per beam the service keeps the count of chunks and the latency of the
+ *     last one.  Statistics of earlier chunks never enter a decision.
+ * Returns RFIM_ERR_STATE if the service is already open, RFIM_ERR_OOM if not
+ * even one slot fits.
  */
 rfim_status rfim_stream_open(rfim_ctx* ctx, int n_beams, int channels, int chunk_samples, rfim_dtype dtype,
                              const rfim_cut* tdsc, const rfim_cut* fdsc);
 
 /*
- * Submit one chunk of beam `beam`.  chunk: device or host pointer (detected),
- * copied into a device slot before the call returns.  arrival_time_s: the
- * scheduled arrival time on the CLOCK_MONOTONIC scale (seconds), from which
- * latency is measured.  Returns RFIM_ERR_BUSY if no slot or memory is free
- * (the caller retries), RFIM_ERR_STATE if the service is not open.
+ * Submit one chunk of beam `beam` (0 <= beam < n_beams).
+ *   chunk: a DEVICE pointer is read in place by the kernels (zero copy): its
+ *     contents must be complete when the call is made and stay unchanged
+ *     until the ticket completes.  A HOST pointer is copied into the slot
+ *     before the call returns.
+ *   arrival_time_s: the chunk's scheduled arrival on the CLOCK_MONOTONIC
+ *     scale, seconds; latency is measured from it (so a late push counts).
+ * Returns RFIM_ERR_BUSY if no slot is free (retry after releasing tickets),
+ * RFIM_ERR_STATE if the service is not open.
  */
 rfim_status rfim_stream_push(rfim_ctx* ctx, int beam, const void* chunk, double arrival_time_s,
                              unsigned long long* ticket);
 
 /*
- * Poll a ticket.  When cleaned, *out_dev and *mask_dev (bit mask, BCT rows)
- * point to context-owned device memory valid until rfim_stream_release.
- * wait_us: how long to wait for completion (0 = do not wait).  Returns
- * RFIM_ERR_BUSY if not done in time, RFIM_ERR_ARG for an unknown ticket.
+ * Poll a ticket.  When cleaned, *out_dev and *mask_dev (bit mask, one row of
+ * ceil(chunk_samples / 32) words per channel) point to context-owned device
+ * memory valid until rfim_stream_release.  wait_us: how long to wait for
+ * completion (0 = do not wait).  Returns RFIM_ERR_BUSY if not done in time,
+ * RFIM_ERR_ARG for an unknown ticket.
  */
 rfim_status rfim_stream_poll(rfim_ctx* ctx, unsigned long long ticket, void** out_dev, void** mask_dev,
                              int wait_us);
 
-/* Return the ticket's slot to the pool. */
+/* Return a completed ticket's slot to the pool (RFIM_ERR_BUSY while it is in flight). */
 rfim_status rfim_stream_release(rfim_ctx* ctx, unsigned long long ticket);
 
 /*
+ * Replay an arrival schedule through the open service: chunk i (of beam
+ * beams[i], pointer chunks[i]) is pushed at its scheduled time arrival_s[i]
+ * (CLOCK_MONOTONIC seconds, non-decreasing; the call waits until then, or
+ * pushes at once when behind schedule), completed tickets are released as it
+ * goes, and the call returns when all n are done.  A load generator for
+ * recorded or simulated arrivals; latencies accumulate in rfim_stream_stats.
+ */
+rfim_status rfim_stream_replay(rfim_ctx* ctx, int n, const int* beams, const void* const* chunks,
+                               const double* arrival_s);
+
+/*
  * Latency percentiles (seconds, from scheduled arrival to completion seen by
- * the service) and input GB/s since rfim_stream_open or the last reset; any
- * pointer may be NULL.  reset != 0 clears the statistics after reading.
+ * the service) over the chunks completed since rfim_stream_open or the last
+ * reset, their count, and their input GB/s (input bytes / time from the
+ * earliest arrival to the last completion); any pointer may be NULL.
+ * reset != 0 clears the statistics after reading.
  */
 rfim_status rfim_stream_stats(rfim_ctx* ctx, double* p50, double* p99, double* p999, double* gbps,
                               unsigned long long* chunks, int reset);

@@ -711,19 +711,43 @@ void ctx_set_tunables(rfim_ctx* ctx, const Tunables& t) {
 // allocation, default tuning (fused schedule with one beam of lag).
 rfim_status noalloc_clean(const rfim_block* b, const rfim_cut* tdsc, const rfim_cut* fdsc, unsigned* counters,
                           unsigned* status, cudaStream_t st) {
-  if (!tdsc && !fdsc) return RFIM_ERR_ARG;
-  if (!b) return RFIM_ERR_ARG;
+  return launch_blocks_fixed(b, 1, tdsc, fdsc, counters, status, st);
+}
+
+rfim_status ctx_validate(rfim_ctx* ctx, const rfim_block* b, const rfim_cut* tdsc, const rfim_cut* fdsc) {
   CutNorm td, fd;
   rfim_status s;
-  if ((s = check_cut(nullptr, tdsc, b->channels, false, td)) != RFIM_OK) return s;
-  if ((s = check_cut(nullptr, fdsc, b->channels, true, fd)) != RFIM_OK) return s;
-  if ((s = check_block(nullptr, b, td, fd)) != RFIM_OK) return s;
-  if ((s = check_impl(nullptr, b, td, fd)) != RFIM_OK) return s;
-  if (b->beams > MAX_JOBS) return RFIM_ERR_RANGE;
+  if ((s = check_cut(ctx, tdsc, b->channels, false, td)) != RFIM_OK) return s;
+  if ((s = check_cut(ctx, fdsc, b->channels, true, fd)) != RFIM_OK) return s;
+  if ((s = check_block(ctx, b, td, fd)) != RFIM_OK) return s;
+  return check_impl(ctx, b, td, fd);
+}
+
+rfim_status launch_blocks_fixed(const rfim_block* blocks, int n, const rfim_cut* tdsc, const rfim_cut* fdsc,
+                                unsigned* counters, unsigned* status, cudaStream_t st) {
+  if (!tdsc && !fdsc) return RFIM_ERR_ARG;
+  if (!blocks || n < 1) return RFIM_ERR_ARG;
+  CutNorm td, fd;
+  rfim_status s;
+  int beams = 0;
+  for (int i = 0; i < n; i++) {
+    const rfim_block* b = &blocks[i];
+    if ((s = check_cut(nullptr, tdsc, b->channels, false, td)) != RFIM_OK) return s;
+    if ((s = check_cut(nullptr, fdsc, b->channels, true, fd)) != RFIM_OK) return s;
+    if ((s = check_block(nullptr, b, td, fd)) != RFIM_OK) return s;
+    if ((s = check_impl(nullptr, b, td, fd)) != RFIM_OK) return s;
+    if (b->dtype != blocks[0].dtype || b->layout != blocks[0].layout || b->mask_fmt != blocks[0].mask_fmt)
+      return RFIM_ERR_ARG;
+    if (fd.on && fdsc->fdsc_bin == 0 && b->channels != blocks[0].channels) return RFIM_ERR_ARG;
+    beams += b->beams;
+  }
+  if (beams > MAX_JOBS) return RFIM_ERR_RANGE;
   Params p;  // on the stack: no allocation
   memset(&p, 0, sizeof p);
-  p.n_jobs = b->beams;
-  for (int j = 0; j < b->beams; j++) p.jobs[j] = make_job(b, j, fd, 0, 113 * 1024);
+  p.n_jobs = beams;
+  for (int i = 0, j0 = 0; i < n; j0 += blocks[i].beams, i++)
+    for (int j = 0; j < blocks[i].beams; j++) p.jobs[j0 + j] = make_job(&blocks[i], j, fd, 0, 113 * 1024);
+  const rfim_block* b = &blocks[0];
   const int mode = (td.on && fd.on) ? 2 : (td.on ? 0 : 1);
   p.td = cut_dev(td);
   p.fd = cut_dev(fd);

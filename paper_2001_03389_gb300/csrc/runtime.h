@@ -29,6 +29,8 @@ size_t ctx_hbm_budget(rfim_ctx* ctx);
 void ctx_set_error(rfim_ctx* ctx, const char* msg);
 StreamService*& ctx_stream_service(rfim_ctx* ctx);
 void ctx_get_tunables(rfim_ctx* ctx, Tunables& t);
+// validation of one block and its cuts as a launch would do it (no launch)
+rfim_status ctx_validate(rfim_ctx* ctx, const rfim_block* b, const rfim_cut* tdsc, const rfim_cut* fdsc);
 void ctx_set_tunables(rfim_ctx* ctx, const Tunables& t);
 
 // host staging (runtime.cu)
@@ -43,9 +45,13 @@ void tuner_destroy(Tuner* t);
 rfim_status tuner_apply(Tuner* t, rfim_ctx* ctx, const rfim_block* blocks, int n, const rfim_cut* tdsc,
                         const rfim_cut* fdsc);
 
-// planning and launch with caller-provided counters, no allocation (api.cu)
+// planning and launch with caller-provided counters, no allocation (api.cu):
+// one launch over the blocks (at most 160 beams in all, same dtype, layout and
+// mask format), default tuning; `counters` holds 1 + 160 words, `status` one.
 rfim_status noalloc_clean(const rfim_block* b, const rfim_cut* tdsc, const rfim_cut* fdsc, unsigned* counters,
                           unsigned* status, cudaStream_t st);
+rfim_status launch_blocks_fixed(const rfim_block* blocks, int n, const rfim_cut* tdsc, const rfim_cut* fdsc,
+                                unsigned* counters, unsigned* status, cudaStream_t st);
 
 // streaming service (stream.cu)
 void stream_service_destroy(StreamService* s);

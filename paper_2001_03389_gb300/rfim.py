@@ -63,6 +63,8 @@ _SIGS = {
     "rfim_stream_push": ([_vp, ctypes.c_int, _vp, ctypes.c_double, ctypes.POINTER(ctypes.c_ulonglong)], ctypes.c_int),
     "rfim_stream_poll": ([_vp, ctypes.c_ulonglong, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int], ctypes.c_int),
     "rfim_stream_release": ([_vp, ctypes.c_ulonglong], ctypes.c_int),
+    "rfim_stream_replay": ([_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_vp),
+                            ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "rfim_stream_stats": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                            ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int], ctypes.c_int),
@@ -188,6 +190,49 @@ class Context:
 
     def device_status(self, stream=None):
         return rfim_device_status(self.h, _stream_ptr(stream))
+
+    # ---- streaming service
+    def stream_open(self, n_beams, channels, chunk_samples, dtype=U8, tdsc=None, fdsc=None):
+        self._check(rfim_stream_open(self.h, int(n_beams), int(channels), int(chunk_samples), int(dtype),
+                                     _cut_arg(tdsc), _cut_arg(fdsc)), "rfim_stream_open")
+
+    def stream_push(self, beam, chunk, arrival_s):
+        """Returns the ticket, or None when no slot is free (RFIM_ERR_BUSY)."""
+        t = ctypes.c_ulonglong()
+        st = rfim_stream_push(self.h, int(beam), _ptr(chunk), float(arrival_s), ctypes.byref(t))
+        if st == ERR_BUSY:
+            return None
+        self._check(st, "rfim_stream_push")
+        return t.value
+
+    def stream_poll(self, ticket, wait_us=0):
+        """(out_ptr, mask_ptr) when done, None while in flight."""
+        o, m = _vp(), _vp()
+        st = rfim_stream_poll(self.h, ticket, ctypes.byref(o), ctypes.byref(m), int(wait_us))
+        if st == ERR_BUSY:
+            return None
+        self._check(st, "rfim_stream_poll")
+        return o.value, m.value
+
+    def stream_release(self, ticket):
+        self._check(rfim_stream_release(self.h, ticket), "rfim_stream_release")
+
+    def stream_replay(self, beams, chunk_ptrs, arrivals):
+        n = len(beams)
+        b = (ctypes.c_int * n)(*[int(v) for v in beams])
+        c = (_vp * n)(*[int(v) for v in chunk_ptrs])
+        a = (ctypes.c_double * n)(*[float(v) for v in arrivals])
+        self._check(rfim_stream_replay(self.h, n, b, c, a), "rfim_stream_replay")
+
+    def stream_stats(self, reset=False):
+        p50, p99, p999, g = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        n = ctypes.c_ulonglong()
+        self._check(rfim_stream_stats(self.h, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(p999),
+                                      ctypes.byref(g), ctypes.byref(n), int(bool(reset))), "rfim_stream_stats")
+        return {"p50_s": p50.value, "p99_s": p99.value, "p999_s": p999.value, "gbps": g.value, "chunks": n.value}
+
+    def stream_close(self):
+        self._check(rfim_stream_close(self.h), "rfim_stream_close")
 
     def last_error(self) -> str:
         return rfim_last_error(self.h).decode()

@@ -91,3 +91,16 @@ def noise_u8(rng, shape, rfi=True):
         flat[idx] = rng.integers(200, 256, idx.size).astype(np.uint8)
         flat[rng.integers(0, flat.size, max(1, flat.size // 500))] = 0
     return x
+
+
+class _RawDevice:
+    def __init__(self, ptr, nbytes):
+        self.__cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (int(ptr), False),
+                                         "version": 3}
+
+
+def device_bytes(ptr, nbytes):
+    """A uint8 torch view of nbytes of device memory at a raw pointer (no copy)."""
+    import torch
+
+    return torch.as_tensor(_RawDevice(ptr, nbytes), device="cuda")
