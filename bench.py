@@ -343,6 +343,8 @@ def run_gpu(args):
         }
         if clk:
             res["clocks"] = clk
+        if CFG == 2 and not args.no_stream and ws == 1:
+            res["streaming"] = run_stream_bench(rfim, synth, dev)
         if not args.no_cpu_baseline and ws == 1:
             res["cpu_baseline"] = cpu_baseline(spec)
         print(json.dumps(res), flush=True)
@@ -359,6 +361,60 @@ PROFILES = {
     3: ("engine_f32_fp32x32.md", ("common.cuh", "engine.h", "engine_f32.cu"),
         "k_engine_f32 (fused TDSC->FDSC persistent work queue)"),
 }
+
+
+# ---------------------------------------------------------------------------
+# streaming service: Poisson arrivals of 1536 x 1250 uint8 chunks from 480 beams
+# ---------------------------------------------------------------------------
+def run_stream_bench(rfim, synth, dev, rates=(10, 25, 50, 100), duration_s=0.5, seed=2001033895):
+    """Latency percentiles and sustained GB/s of the streaming service at m x the
+    ARTS input rate of 73 Gb/s (480 beams of 1536 channels sampled every
+    81.92 us; a 1250-sample chunk lasts 102.4 ms).  Chunks come from a pool of 4
+    per beam resident in HBM (device ingest, read in place by the kernels)."""
+    import numpy as np
+    import torch
+
+    n_beams, C, T = 480, 1536, 1250
+    per_beam = 4
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    pool = torch.empty((n_beams * per_beam, C, T), dtype=torch.uint8, device=dev)
+    model = synth.cfg2_model()
+    for i in range(pool.shape[0]):
+        pool[i] = synth.torch_beam_u8(gen, C, T, model, dev)
+    torch.cuda.synchronize()
+    base = pool.data_ptr()
+    cb = C * T
+    ctx = rfim.Context(dev.index or 0)
+    td = rfim.make_cut(3.0, 2, "median")
+    fd = rfim.make_cut(3.0, 2, "median", 32)
+    ctx.stream_open(n_beams, C, T, rfim.U8, td, fd)
+    rng = np.random.default_rng(seed)
+    chunk_rate = 73e9 / (8 * C * T)  # ARTS input rate, 73 Gb/s (Sec. I), in 1536 x 1250 chunks: 4753 /s
+
+    def replay(m, dur):
+        n = max(1, int(m * chunk_rate * dur))
+        arr = time.monotonic() + 0.02 + np.cumsum(rng.exponential(1.0 / (m * chunk_rate), n))
+        beams = np.arange(n) % n_beams
+        ptrs = base + (beams * per_beam + (np.arange(n) // n_beams) % per_beam) * cb
+        ctx.stream_replay(beams, ptrs, arr)
+        return ctx.stream_stats(reset=True)
+
+    replay(10, 0.1)  # warm-up
+    out = []
+    for m in rates:
+        st = replay(m, duration_s)
+        out.append({"rate_x_arts": m, "offered_chunks_per_s": m * chunk_rate,
+                    "offered_gbps": m * chunk_rate * cb / 1e9, "gbps": st["gbps"], "chunks": st["chunks"],
+                    "p50_ms": st["p50_s"] * 1e3, "p99_ms": st["p99_s"] * 1e3, "p999_ms": st["p999_s"] * 1e3})
+    ctx.stream_close()
+    ctx.close()
+    del pool
+    torch.cuda.empty_cache()
+    return {"workload": "480 beams x 1536 ch x 1250-sample uint8 chunks, Poisson arrivals, TDSC+FDSC k=3 median",
+            "ingest": "device (chunks read in place from an HBM pool of 4 per beam)",
+            "latency": "scheduled arrival -> completion seen by the host", "budget_ms": 102.4,
+            "duration_s_per_rate": duration_s, "rates": out}
 
 
 def profiled_traffic():
@@ -405,6 +461,7 @@ def main():
     ap.add_argument("--beams", type=int, default=None, help="clean only the first N beams (profiling captures)")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-stream", action="store_true", help="skip the streaming-service measurement")
     ap.add_argument("--profile", action="store_true", help="warm-up and plain steps only (for ncu captures)")
     args = ap.parse_args()
     global CFG

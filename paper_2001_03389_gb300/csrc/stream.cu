@@ -88,6 +88,7 @@ struct StreamService {
   std::condition_variable cv_work, cv_done;
   std::thread dispatcher;
   bool stop = false;
+  bool disp_waiting = false;  // the dispatcher sleeps on cv_work (pushes wake it only then)
   rfim_status fault = RFIM_OK;
 };
 
@@ -128,6 +129,7 @@ void dispatch_loop(StreamService* s) {
   std::unique_lock<std::mutex> lk(s->mu);
   for (;;) {
     int lane = -1;
+    s->disp_waiting = true;
     s->cv_work.wait(lk, [&] {
       if (s->stop) return true;
       if (s->waiting.empty()) return false;
@@ -138,6 +140,7 @@ void dispatch_loop(StreamService* s) {
         }
       return false;
     });
+    s->disp_waiting = false;
     if (s->stop) break;
     // close a micro-batch: everything waiting, up to MAX_BATCH chunks
     StreamService::Batch& b = s->batches[lane];
@@ -217,6 +220,9 @@ bool is_device_ptr(const void* p) {
 }
 
 StreamService* svc_of(rfim_ctx* ctx) { return ctx ? ctx_stream_service(ctx) : nullptr; }
+
+rfim_status svc_push(StreamService* s, int beam, const void* chunk, bool on_device, double arrival_time_s,
+                     unsigned long long* ticket);
 
 }  // namespace
 
@@ -329,6 +335,15 @@ rfim_status rfim_stream_push(rfim_ctx* ctx, int beam, const void* chunk, double 
   if (!ctx) return RFIM_ERR_ARG;
   if (!s) return RFIM_ERR_STATE;
   if (beam < 0 || beam >= s->n_beams || !chunk || !ticket) return RFIM_ERR_ARG;
+  return svc_push(s, beam, chunk, is_device_ptr(chunk), arrival_time_s, ticket);
+}
+
+}  // extern "C"
+
+namespace rfim {
+namespace {
+rfim_status svc_push(StreamService* s, int beam, const void* chunk, bool on_device, double arrival_time_s,
+                     unsigned long long* ticket) {
   int slot;
   {
     std::lock_guard<std::mutex> g(s->mu);
@@ -337,7 +352,7 @@ rfim_status rfim_stream_push(rfim_ctx* ctx, int beam, const void* chunk, double 
     s->free_slots.pop_back();
   }
   const void* src = chunk;
-  if (!is_device_ptr(chunk)) {
+  if (!on_device) {
     // host chunk: copy it into the slot, cleaned in place there
     unsigned char* dst = s->d_slots + (size_t)slot * s->chunk_bytes;
     const size_t n = s->in_bytes;
@@ -355,6 +370,7 @@ rfim_status rfim_stream_push(rfim_ctx* ctx, int beam, const void* chunk, double 
     src = dst;
   }
   unsigned long long id;
+  bool wake;
   {
     std::lock_guard<std::mutex> g(s->mu);
     id = s->next_ticket++;
@@ -368,11 +384,16 @@ rfim_status rfim_stream_push(rfim_ctx* ctx, int beam, const void* chunk, double 
     s->tickets.emplace(id, k);
     s->waiting.push_back(id);
     s->beam_chunks[beam]++;
+    wake = s->disp_waiting;
   }
-  s->cv_work.notify_one();
+  if (wake) s->cv_work.notify_one();
   *ticket = id;
   return RFIM_OK;
 }
+}  // namespace
+}  // namespace rfim
+
+extern "C" {
 
 rfim_status rfim_stream_poll(rfim_ctx* ctx, unsigned long long ticket, void** out_dev, void** mask_dev,
                              int wait_us) {
@@ -417,6 +438,9 @@ rfim_status rfim_stream_replay(rfim_ctx* ctx, int n, const int* beams, const voi
   if (!s) return RFIM_ERR_STATE;
   if (n < 0 || (n > 0 && (!beams || !chunks || !arrival_s))) return RFIM_ERR_ARG;
   std::deque<unsigned long long> out;
+  std::unordered_map<const void*, bool> kind;  // pointer -> device memory (classified once)
+  for (int i = 0; i < n; i++)
+    if (beams[i] < 0 || beams[i] >= s->n_beams || !chunks[i]) return RFIM_ERR_ARG;
   auto reap = [&](bool block) -> rfim_status {
     while (!out.empty()) {
       rfim_status st = rfim_stream_poll(ctx, out.front(), nullptr, nullptr, block ? 1000000 : 0);
@@ -440,8 +464,10 @@ rfim_status rfim_stream_replay(rfim_ctx* ctx, int n, const int* beams, const voi
       if (dt > 200e-6) std::this_thread::sleep_for(std::chrono::microseconds((long)(dt * 0.5e6)));
     }
     unsigned long long id;
+    auto kt = kind.find(chunks[i]);
+    if (kt == kind.end()) kt = kind.emplace(chunks[i], is_device_ptr(chunks[i])).first;
     for (;;) {
-      rfim_status st = rfim_stream_push(ctx, beams[i], chunks[i], arrival_s[i], &id);
+      rfim_status st = svc_push(s, beams[i], chunks[i], kt->second, arrival_s[i], &id);
       if (st == RFIM_OK) break;
       if (st != RFIM_ERR_BUSY) return st;
       // no slot free: wait for the oldest outstanding chunk
@@ -455,8 +481,10 @@ rfim_status rfim_stream_replay(rfim_ctx* ctx, int n, const int* beams, const voi
       }
     }
     out.push_back(id);
-    rfim_status st = reap(false);
-    if (st != RFIM_OK) return st;
+    if ((i & 31) == 31) {
+      rfim_status st = reap(false);
+      if (st != RFIM_OK) return st;
+    }
   }
   return reap(true);
 }

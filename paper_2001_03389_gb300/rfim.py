@@ -218,11 +218,17 @@ class Context:
         self._check(rfim_stream_release(self.h, ticket), "rfim_stream_release")
 
     def stream_replay(self, beams, chunk_ptrs, arrivals):
-        n = len(beams)
-        b = (ctypes.c_int * n)(*[int(v) for v in beams])
-        c = (_vp * n)(*[int(v) for v in chunk_ptrs])
-        a = (ctypes.c_double * n)(*[float(v) for v in arrivals])
-        self._check(rfim_stream_replay(self.h, n, b, c, a), "rfim_stream_replay")
+        import numpy as np
+
+        b = np.ascontiguousarray(beams, dtype=np.int32)
+        c = np.ascontiguousarray(chunk_ptrs, dtype=np.uint64)
+        a = np.ascontiguousarray(arrivals, dtype=np.float64)
+        n = int(b.shape[0])
+        if c.shape[0] != n or a.shape[0] != n:
+            raise ValueError("beams, chunk_ptrs and arrivals differ in length")
+        self._check(rfim_stream_replay(self.h, n, b.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                       ctypes.cast(c.ctypes.data, ctypes.POINTER(_vp)),
+                                       a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "rfim_stream_replay")
 
     def stream_stats(self, reset=False):
         p50, p99, p999, g = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
