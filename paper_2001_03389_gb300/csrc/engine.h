@@ -111,7 +111,11 @@ struct LaunchCfg {
   int smem;
 };
 int engine_smem_u8(const Params& p);
-void* engine_kernel_u8();
+void* engine_kernel_u8(const Params& p);
+// dynamic shared memory per CTA with three CTAs per SM: 228 KB / 3 = 77824 B
+// less the 1 KB the runtime reserves per CTA and the kernel's ~0.5 KB of
+// static shared variables
+constexpr int FD_SMEM_3PER_SM = 233472 / 3 - 1024 - 768;
 int launch_engine_u8(const Params& p, const LaunchCfg& cfg, void* stream);
 
 // float32 engine: TDSC rows of up to TD32_MAX_T samples staged per CTA; FDSC tile
@@ -132,7 +136,7 @@ void* engine_kernel_f32();
 int launch_engine_f32(const Params& p, const LaunchCfg& cfg, void* stream);
 
 inline int engine_smem(const Params& p) { return p.dtype ? engine_smem_f32(p) : engine_smem_u8(p); }
-inline void* engine_kernel(const Params& p) { return p.dtype ? engine_kernel_f32() : engine_kernel_u8(); }
+inline void* engine_kernel(const Params& p) { return p.dtype ? engine_kernel_f32() : engine_kernel_u8(p); }
 inline int launch_engine(const Params& p, const LaunchCfg& cfg, void* stream) {
   return p.dtype ? launch_engine_f32(p, cfg, stream) : launch_engine_u8(p, cfg, stream);
 }

@@ -689,6 +689,51 @@ __device__ __forceinline__ int toff(int r, int c, int pitch) {
   return r * pitch + ((((c >> 4) ^ ((r >> 2) & 7)) << 4) | (c & 15));
 }
 
+// Whole 32-sample items of rows on 4-byte boundaries with C % 16 == 0: units of
+// 16 channels x 4 samples.  16 row words (lanes along time, so 8 lanes read 32
+// contiguous bytes of a row), four 4x4 byte transposes, and one 16-byte shared
+// store per sample row (the 16 channels are one swizzle unit).
+__device__ __forceinline__ void fd_load_full(uint8_t* tile, const uint8_t* src, int C, int T, int t0, int pitch) {
+  const int nunits = (C >> 4) * 8;
+  for (int u = threadIdx.x; u < nunits; u += NT) {
+    const int tq = u & 7, cg = u >> 3;
+    const uint8_t* a = src + (size_t)(cg * 16) * T + t0 + 4 * tq;
+    uint32_t w[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) w[i] = *reinterpret_cast<const uint32_t*>(a + (size_t)i * T);
+#pragma unroll
+    for (int g = 0; g < 4; g++) transpose4x4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3]);
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+      const int t = 4 * tq + r;
+      *reinterpret_cast<uint4*>(tile + t * pitch + ((cg ^ ((t >> 2) & 7)) << 4)) =
+          make_uint4(w[r], w[4 + r], w[8 + r], w[12 + r]);
+    }
+  }
+}
+
+__device__ __forceinline__ void fd_store_full(const uint8_t* tile, uint8_t* dst, int C, int T, int t0, int pitch) {
+  const int nunits = (C >> 4) * 8;
+  for (int u = threadIdx.x; u < nunits; u += NT) {
+    const int tq = u & 7, cg = u >> 3;
+    uint32_t w[16];
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+      const int t = 4 * tq + r;
+      const uint4 v = *reinterpret_cast<const uint4*>(tile + t * pitch + ((cg ^ ((t >> 2) & 7)) << 4));
+      w[r] = v.x;
+      w[4 + r] = v.y;
+      w[8 + r] = v.z;
+      w[12 + r] = v.w;
+    }
+#pragma unroll
+    for (int g = 0; g < 4; g++) transpose4x4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3]);
+    uint8_t* a = dst + (size_t)(cg * 16) * T + t0 + 4 * tq;
+#pragma unroll
+    for (int i = 0; i < 16; i++) *reinterpret_cast<uint32_t*>(a + (size_t)i * T) = w[i];
+  }
+}
+
 __device__ __forceinline__ unsigned long long fd_contrib(unsigned long long m, unsigned gsz, unsigned S, unsigned Q) {
   // sum over the bin of D^2 = m^2 * G * (G Q - S^2)
   return m * m * (unsigned long long)gsz * ((unsigned long long)gsz * Q - (unsigned long long)S * S);
@@ -852,9 +897,12 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
   for (int t0 = t_item; t0 < t_end; t0 += Ws) {
     const int ws = min(Ws, t_end - t0);
     const int nt4 = (ws + 3) >> 2, nq = (C + 3) >> 2;
+    const bool full = ws == 32 && (C & 15) == 0;
     // ---- load: units of 4 channels x 4 samples, lanes along time, transposed into [t][c];
     //      four units per thread are in flight at a time
-    {
+    if (full && rows4) {
+      fd_load_full(L.tile, src, C, T, t0, pitch);
+    } else {
       const int nunits = nq * nt4;
       for (int ub = threadIdx.x; ub < nunits; ub += 4 * NT) {
         uint32_t a[4][4];
@@ -1149,7 +1197,8 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
     __syncthreads();
 
     // ---- store: transpose back to [c][t], lanes along time
-    for (int u = threadIdx.x; u < nq * nt4; u += NT) {
+    if (full && out4) fd_store_full(L.tile, dst, C, T, t0, pitch);
+    else for (int u = threadIdx.x; u < nq * nt4; u += NT) {
       const int tq = u % nt4, cq = u / nt4;
       const int c = 4 * cq, tt = 4 * tq;
       const int nv = min(4, ws - tt);
@@ -1231,7 +1280,10 @@ __device__ bool wait_rows(const Params& P, int job, unsigned need, int* flag) {
   return ok;
 }
 
-__global__ void __launch_bounds__(NT, 2) k_engine_u8(const __grid_constant__ Params P) {
+// MINB = CTAs per SM the register allocation targets: 2 for launches with
+// TDSC items (their row stage is 102 KB), 3 for FDSC-only launches (a 72 KB tile).
+template <int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_engine_u8(const __grid_constant__ Params P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long scr[GRP_SUM_MAX * (NT / 32)];
   __shared__ int s_item, s_flag;
@@ -1294,11 +1346,18 @@ int engine_smem_u8(const Params& p) {
   return align16i(s);
 }
 
-void* engine_kernel_u8() { return (void*)k_engine_u8; }
+// FDSC-only launches whose tile fits three CTAs per SM use the 3-CTA build.
+static bool use_minb3(const Params& p) {
+  return p.td.iterations == 0 && engine_smem_u8(p) <= FD_SMEM_3PER_SM;
+}
+
+void* engine_kernel_u8(const Params& p) {
+  return use_minb3(p) ? (void*)k_engine_u8<3> : (void*)k_engine_u8<2>;
+}
 
 int launch_engine_u8(const Params& p, const LaunchCfg& cfg, void* stream) {
   void* args[] = {const_cast<Params*>(&p)};
-  return (int)cudaLaunchKernel((void*)k_engine_u8, dim3(cfg.grid), dim3(NT), args, (size_t)cfg.smem,
+  return (int)cudaLaunchKernel(engine_kernel_u8(p), dim3(cfg.grid), dim3(NT), args, (size_t)cfg.smem,
                                (cudaStream_t)stream);
 }
 
