@@ -80,6 +80,15 @@ typedef enum {
 typedef enum { RFIM_U8 = 0, RFIM_F32 = 1 } rfim_dtype;
 
 /* BCT: x[b][c][t], time fastest ("channel-major").  BTC: x[b][t][c], channel fastest. */
+/*
+ * Layouts: BCT = [beam][channel][time] (time fastest: TDSC rows contiguous);
+ * BTC = [beam][time][channel] (channels fastest).  The kernels work on BCT; a
+ * BTC block is transposed on the device into a context-owned BCT scratch copy,
+ * cleaned there and transposed back (three reads and writes of the block in
+ * all), with identical results.  rfim_clean_batch runs BTC blocks one after
+ * the other without graph capture; rfim_clean_noalloc and the streaming
+ * service take BCT only.
+ */
 typedef enum { RFIM_LAYOUT_BCT = 0, RFIM_LAYOUT_BTC = 1 } rfim_layout;
 
 typedef enum { RFIM_REPLACE_MEAN = 0, RFIM_REPLACE_MEDIAN = 1 } rfim_replace;

@@ -56,6 +56,11 @@ struct rfim_ctx {
   unsigned* capture_counters = nullptr;  // while capturing: counter blocks of the graph
   int capture_used = 0;
   cudaStream_t capture_stream = nullptr;
+  // BTC blocks: BCT scratch copies of the data and the mask
+  void* btc_buf = nullptr;
+  size_t btc_cap = 0;
+  void* btc_mask = nullptr;
+  size_t btc_mask_cap = 0;
   // host staging (rfim_clean_host)
   HostStager* stager = nullptr;
   // streaming service
@@ -186,7 +191,8 @@ rfim_status check_block(rfim_ctx* ctx, const rfim_block* b, const CutNorm& td, c
 
 // Engine limits of this build.
 rfim_status check_impl(rfim_ctx* ctx, const rfim_block* b, const CutNorm& td, const CutNorm& fd) {
-  if (b->layout != RFIM_LAYOUT_BCT) return fail(ctx, RFIM_ERR_ARG, "BTC layout is not available in this build");
+  if (b->layout != RFIM_LAYOUT_BCT)
+    return fail(ctx, RFIM_ERR_ARG, "BTC blocks are cleaned through a context's BCT scratch (not here)");
   if (b->dtype == RFIM_F32) {
     if (td.on && b->samples > TD32_MAX_T)
       return fail(ctx, RFIM_ERR_ARG, "float32 TDSC rows longer than %d samples are not available in this build",
@@ -491,6 +497,8 @@ rfim_status rfim_destroy(rfim_ctx* ctx) {
     cudaFree(kv.second.second);
   }
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+  cudaFree(ctx->btc_buf);
+  cudaFree(ctx->btc_mask);
   if (ctx->stager) stager_destroy(ctx->stager);
   if (ctx->tuner) tuner_destroy(ctx->tuner);
   cudaFree(ctx->d_counters);
@@ -529,11 +537,72 @@ rfim_status rfim_set_option(rfim_ctx* ctx, const char* key, long long value) {
   return RFIM_OK;
 }
 
+// BTC blocks (channel fastest): each block is transposed into a BCT scratch
+// copy, cleaned there in place with the BCT engine, and transposed back; the
+// mask is produced in BCT form and transposed into the caller's BTC mask.
+static rfim_status run_btc(rfim_ctx* ctx, const rfim_block* blocks, int n, const rfim_cut* tdsc,
+                           const rfim_cut* fdsc, cudaStream_t st) {
+  for (int i = 0; i < n; i++) {
+    const rfim_block* b = &blocks[i];
+    if (!b) return fail(ctx, RFIM_ERR_ARG, "null block");
+    CutNorm td, fd;
+    rfim_status s;
+    if ((s = check_cut(ctx, tdsc, b->channels, false, td)) != RFIM_OK) return s;
+    if ((s = check_cut(ctx, fdsc, b->channels, true, fd)) != RFIM_OK) return s;
+    if ((s = check_block(ctx, b, td, fd)) != RFIM_OK) return s;
+    if (b->layout != RFIM_LAYOUT_BTC || b->dtype != blocks[0].dtype || b->mask_fmt != blocks[0].mask_fmt)
+      return fail(ctx, RFIM_ERR_ARG, "all blocks of a batch must share dtype, layout and mask format");
+    const size_t es = dtype_size(b->dtype);
+    const size_t N = (size_t)b->beams * b->channels * b->samples;
+    const size_t mbytes = b->mask_fmt == RFIM_MASK_BITS
+                              ? (size_t)b->beams * b->channels * ((b->samples + 31) / 32) * 4
+                              : (b->mask_fmt == RFIM_MASK_BYTES ? N : 0);
+    if (ctx->btc_cap < N * es) {
+      cudaFree(ctx->btc_buf);
+      ctx->btc_buf = nullptr;
+      ctx->btc_cap = 0;
+      if (cudaMalloc(&ctx->btc_buf, N * es) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, RFIM_ERR_OOM, "BTC scratch of %zu bytes", N * es);
+      }
+      ctx->btc_cap = N * es;
+    }
+    if (mbytes && ctx->btc_mask_cap < mbytes) {
+      cudaFree(ctx->btc_mask);
+      ctx->btc_mask = nullptr;
+      ctx->btc_mask_cap = 0;
+      if (cudaMalloc(&ctx->btc_mask, mbytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, RFIM_ERR_OOM, "BTC mask scratch of %zu bytes", mbytes);
+      }
+      ctx->btc_mask_cap = mbytes;
+    }
+    int e = launch_transpose(b->in, ctx->btc_buf, b->beams, b->samples, b->channels, (int)es, st);
+    if (e != 0) return cuda_fail(ctx, (cudaError_t)e, "BTC transpose");
+    rfim_block d = *b;
+    d.in = ctx->btc_buf;
+    d.out = ctx->btc_buf;
+    d.mask = mbytes ? ctx->btc_mask : nullptr;
+    d.layout = RFIM_LAYOUT_BCT;
+    Plan pl;
+    if ((s = make_plan(ctx, &d, 1, tdsc, fdsc, pl)) != RFIM_OK) return s;
+    if ((s = run_plan(ctx, pl, st)) != RFIM_OK) return s;
+    e = launch_transpose(ctx->btc_buf, b->out, b->beams, b->channels, b->samples, (int)es, st);
+    if (e == 0 && b->mask_fmt == RFIM_MASK_BITS)
+      e = launch_transpose_bits(ctx->btc_mask, b->mask, b->beams, b->channels, b->samples, st);
+    else if (e == 0 && b->mask_fmt == RFIM_MASK_BYTES)
+      e = launch_transpose(ctx->btc_mask, b->mask, b->beams, b->channels, b->samples, 1, st);
+    if (e != 0) return cuda_fail(ctx, (cudaError_t)e, "BTC transpose back");
+  }
+  return RFIM_OK;
+}
+
 static rfim_status clean_common(rfim_ctx* ctx, const rfim_block* blk, const rfim_cut* tdsc, const rfim_cut* fdsc,
                                 void* stream) {
   if (!ctx) return RFIM_ERR_ARG;
   if (!tdsc && !fdsc) return fail(ctx, RFIM_ERR_ARG, "no cut given");
   cudaSetDevice(ctx->device);
+  if (blk && blk->layout == RFIM_LAYOUT_BTC) return run_btc(ctx, blk, 1, tdsc, fdsc, (cudaStream_t)stream);
   Plan pl;
   rfim_status s = make_plan(ctx, blk, 1, tdsc, fdsc, pl);
   if (s != RFIM_OK) return s;
@@ -561,6 +630,8 @@ rfim_status rfim_clean_batch(rfim_ctx* ctx, const rfim_block* blocks, int n, con
   if (!tdsc && !fdsc) return fail(ctx, RFIM_ERR_ARG, "no cut given");
   if (flags & ~(RFIM_BATCH_GRAPH | RFIM_BATCH_AUTOTUNE)) return fail(ctx, RFIM_ERR_ARG, "unknown batch flags");
   cudaSetDevice(ctx->device);
+  if (n >= 1 && blocks && blocks[0].layout == RFIM_LAYOUT_BTC)
+    return run_btc(ctx, blocks, n, tdsc, fdsc, (cudaStream_t)stream);  // block by block, no capture
   Plan pl;
   rfim_status s = make_plan(ctx, blocks, n, tdsc, fdsc, pl);
   if (s != RFIM_OK) return s;
@@ -684,6 +755,7 @@ namespace rfim {
 
 rfim_status ctx_clean_async(rfim_ctx* ctx, const rfim_block* blocks, int n, const rfim_cut* tdsc,
                             const rfim_cut* fdsc, cudaStream_t st) {
+  if (n >= 1 && blocks && blocks[0].layout == RFIM_LAYOUT_BTC) return run_btc(ctx, blocks, n, tdsc, fdsc, st);
   Plan pl;
   rfim_status s = make_plan(ctx, blocks, n, tdsc, fdsc, pl);
   if (s != RFIM_OK) return s;

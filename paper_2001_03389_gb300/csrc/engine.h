@@ -135,6 +135,11 @@ int engine_smem_f32(const Params& p);
 void* engine_kernel_f32();
 int launch_engine_f32(const Params& p, const LaunchCfg& cfg, void* stream);
 
+// layout conversion (transpose.cu): out[b][c][r] = in[b][r][c] for rows x cols
+// planes of esize-byte elements; bit masks from BCT rows (c) to BTC rows (t).
+int launch_transpose(const void* in, void* out, int batch, int rows, int cols, int esize, void* stream);
+int launch_transpose_bits(const void* in_bct, void* out_btc, int batch, int C, int T, void* stream);
+
 inline int engine_smem(const Params& p) { return p.dtype ? engine_smem_f32(p) : engine_smem_u8(p); }
 inline void* engine_kernel(const Params& p) { return p.dtype ? engine_kernel_f32() : engine_kernel_u8(p); }
 inline int launch_engine(const Params& p, const LaunchCfg& cfg, void* stream) {

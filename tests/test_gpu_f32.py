@@ -198,3 +198,24 @@ def test_f32_validation(ctx):
     with pytest.raises(rfim.RfimError) as e:
         ctx.fdsc(ctx.block(big, torch.empty_like(big)), rfim.make_cut(3.0, bin=32))
     assert e.value.status == rfim.ERR_RANGE
+
+
+@pytest.mark.parametrize("C,T", [(3, 7), (40, 301), (96, 64), (257, 129)])
+def test_f32_btc_layout(oracle, ctx, C, T):
+    rng = np.random.default_rng(C + 5 * T)
+    xb = chi2_block(rng, 2, C, T)
+    x = np.ascontiguousarray(xb.transpose(0, 2, 1))
+    td = dict(k=2.5, iterations=3, replace="mean")
+    fd = dict(k=2.5, iterations=3, replace="median", bin=min(32, C))
+    want, wf, margin = oracle.clean_f32_margin(x, "btc", tdsc=td, fdsc=fd)
+    for kw in (dict(), dict(in_place=True), dict(mask_fmt="bytes")):
+        mf = kw.pop("mask_fmt", "bits")
+        got, gf = run_gpu(ctx, x, layout="btc", tdsc=td, fdsc=fd, mask_fmt=mf, **kw)
+        gflag = gf if mf == "bits" else gf > 0
+        dis = gflag != (wf > 0)
+        assert not (dis & ~(margin <= MARGIN)).any()
+        if not dis.any():
+            keep = ~(wf > 0)
+            assert np.array_equal(got[keep].view(np.uint32), x[keep].view(np.uint32))
+            both = wf > 0
+            assert np.all(np.abs(got[both].astype(np.float64) - want[both]) <= REL * np.abs(want[both]) + 1e-30)

@@ -233,3 +233,43 @@ def test_device_wait_timeout_is_reported(ctx):
         ctx.set_option("schedule", 0)
     ctx.clean(blk, rfim.make_cut(3.0), rfim.make_cut(3.0, bin=32))
     assert ctx.device_status() == rfim.OK
+
+
+@pytest.mark.parametrize("C,T", [(1, 1), (7, 33), (40, 301), (100, 64), (1536, 97), (33, 1250)])
+def test_btc_layout(oracle, ctx, C, T):
+    # time-major blocks (B, T, C): every method and mask format, against the oracle's BTC path
+    rng = np.random.default_rng(C * 3 + T)
+    x = np.ascontiguousarray(noise_u8(rng, (2, C, T)).transpose(0, 2, 1))
+    td = dict(k=3.0, iterations=2, replace="median")
+    fd = dict(k=2.5, iterations=2, replace="mean", bin=min(32, C))
+    check(oracle, ctx, x, td=td, fd=fd, layout="btc")
+    check(oracle, ctx, x, td=td, fd=fd, layout="btc", mask_fmt="bytes")
+    check(oracle, ctx, x, td=td, api="tdsc", layout="btc")
+    check(oracle, ctx, x, fd=fd, api="fdsc", layout="btc", mask_fmt=None)
+    check(oracle, ctx, x, td=td, fd=fd, layout="btc", in_place=True)
+    check(oracle, ctx, x, td=td, fd=fd, layout="btc", in_off=3, out_off=5)
+
+
+def test_btc_batch(oracle, ctx):
+    import torch
+
+    from gpu_util import unpack_bits
+    from paper_2001_03389_gb300 import rfim
+
+    rng = np.random.default_rng(44)
+    shapes = [(96, 300), (40, 129), (1536, 64)]
+    xs = [np.ascontiguousarray(noise_u8(rng, (1, C, T)).transpose(0, 2, 1)) for C, T in shapes]
+    td = dict(k=3.0, iterations=2, replace="median")
+    fd = dict(k=3.0, iterations=2, replace="median", bin=32)
+    dev = [torch.from_numpy(x).cuda() for x in xs]
+    outs = [torch.empty_like(d) for d in dev]
+    # BTC bit masks: one row of ceil(C / 32) words per time sample
+    masks = [torch.zeros(T * ((C + 31) // 32), dtype=torch.int32, device="cuda:0") for C, T in shapes]
+    blks = [ctx.block(d, o, m, "btc", "bits") for d, o, m in zip(dev, outs, masks)]
+    ctx.clean_batch(blks, rfim.make_cut(**td), rfim.make_cut(**fd), flags=rfim.BATCH_GRAPH)
+    torch.cuda.synchronize()
+    for x, o, m, (C, T) in zip(xs, outs, masks, shapes):
+        want, wf = oracle.clean(x, "btc", tdsc=td, fdsc=fd)
+        assert np.array_equal(o.cpu().numpy(), want)
+        # BTC bit mask: rows are time samples, bits along channels
+        assert np.array_equal(unpack_bits(m.cpu().numpy(), T, C)[None], wf > 0)
