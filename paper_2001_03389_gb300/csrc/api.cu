@@ -266,13 +266,13 @@ Job make_job(const rfim_block* b, int j, const CutNorm& fd, int tile_samples, in
     // float32: one CTA per TDSC row; FDSC sub-slab of 8, 4, 2 or 1 samples
     J.td_mode = 1;
     J.td_items = C;
-    J.fd_items = (T + FD32_ITEM_T - 1) / FD32_ITEM_T;
     J.ws = 1;
     for (int ws : {8, 4, 2})
       if ((tile_samples == 0 || ws <= tile_samples) && fd32_smem_bytes(ws, C, J.nb) <= smem_target) {
         J.ws = ws;
         break;
       }
+    J.fd_items = (T + J.ws - 1) / J.ws;
   }
   return J;
 }
@@ -369,6 +369,20 @@ void fill_params(rfim_ctx* ctx, const Plan& pl, int j0, int j1, int mode, Params
   fill_segments(p, mode, ctx->fused_lag);
 }
 
+// float32 FDSC items OR their bits into the mask words they share: a launch
+// whose TDSC part did not write the mask first starts from zeroed bit masks.
+cudaError_t clear_f32_fdsc_masks(const Params& p, cudaStream_t st) {
+  if (p.dtype != 1 || p.fd.iterations == 0 || p.mask_or || p.mask_kind != MASK_BITS) return cudaSuccess;
+  for (int j = 0; j < p.n_jobs; j++) {
+    const Job& J = p.jobs[j];
+    if (!J.mask) continue;
+    const size_t bytes = (size_t)J.C * ((J.T + 31) / 32) * 4;
+    cudaError_t e = cudaMemsetAsync(J.mask, 0, bytes, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 rfim_status launch_one(rfim_ctx* ctx, Params& p, int max_T, cudaStream_t st) {
   (void)max_T;
   LaunchCfg cfg;
@@ -380,6 +394,7 @@ rfim_status launch_one(rfim_ctx* ctx, Params& p, int max_T, cudaStream_t st) {
   cfg.grid = std::max(1, std::min(p.n_items, ctx->sms * per_sm));
   cudaError_t e = cudaMemsetAsync(p.counters, 0, sizeof(unsigned) * (1 + p.n_jobs), st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync");
+  if ((e = clear_f32_fdsc_masks(p, st)) != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync");
   e = (cudaError_t)launch_engine(p, cfg, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "engine launch");
   return RFIM_OK;
@@ -846,7 +861,7 @@ rfim_status launch_blocks_fixed(const rfim_block* blocks, int n, const rfim_cut*
   cfg.grid = std::max(1, std::min(p.n_items, sms * std::max(1, per_sm)));
   // the shared counters and status word keep the previous call's values: clear them
   if (cudaMemsetAsync(counters, 0, sizeof(unsigned) * (1 + p.n_jobs), st) != cudaSuccess ||
-      cudaMemsetAsync(status, 0, sizeof(unsigned), st) != cudaSuccess)
+      cudaMemsetAsync(status, 0, sizeof(unsigned), st) != cudaSuccess || clear_f32_fdsc_masks(p, st) != cudaSuccess)
     return RFIM_ERR_CUDA;
   if (launch_engine(p, cfg, st) != (int)cudaSuccess) return RFIM_ERR_CUDA;
   return RFIM_OK;

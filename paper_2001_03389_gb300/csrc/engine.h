@@ -9,7 +9,8 @@ namespace rfim {
 constexpr int MAX_JOBS = 160;      // beams per launch (kernel parameters stay below 32 KB)
 constexpr int MAX_SEGS = 2 * MAX_JOBS;
 constexpr int FD_ITEM_T = 32;      // time samples per uint8 FDSC work item (one mask word column)
-constexpr int FD32_ITEM_T = 16;    // time samples per float32 FDSC work item (64 bytes of each channel row)
+// float32 FDSC work items are one sub-slab (Job::ws = 1, 2, 4 or 8 samples): the
+// items that share a 128-byte line of each channel row run side by side.
 
 enum ReplaceKind { REP_MEAN = 0, REP_MEDIAN = 1 };
 enum MaskKind { MASK_NONE = 0, MASK_BITS = 1, MASK_BYTES = 2 };

@@ -106,6 +106,18 @@ __device__ __forceinline__ FF warp_ff(FF a) {
   return a;
 }
 
+// sqrt(v) for v >= 0 to ~1e-14 relative: a float32 reciprocal square root
+// refined by one Newton step in double (a double sqrt is ~30 slow FP64
+// instructions on this part; one FMA-based step is four).
+__device__ __forceinline__ double sqrt_fast(double v) {
+  if (!(v > 0.0)) return 0.0;
+  const float vf = (float)v;
+  if (!(vf > 0.0f) || isinf(vf)) return sqrt(v);  // outside float range
+  const double r = (double)rsqrtf(vf);  // ~2^-23 relative
+  const double y = v * r;                // ~sqrt(v)
+  return fma(0.5 * r, fma(-y, y, v), y);  // y + (v - y^2) / (2 sqrt v)
+}
+
 // ---------------------------------------------------------------------------
 // Decisions
 // ---------------------------------------------------------------------------
@@ -321,15 +333,15 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
   };
   __shared__ RowStat rs_s;
   RowStat* rs_ = &rs_s;
-  const double Tn = (double)T;
+  const double Tn = (double)T, rT = 1.0 / (double)T;
   const int I = cut.iterations;
 
   for (int it = 0; it < I; it++) {
     // statistics of the current values, finished in double by one thread
     if (threadIdx.x == 0) {
-      const double mu = Sd / Tn;
-      const double var = Qd / Tn - mu * mu;
-      rs_->prec = !(var >= 1e-3 * (Qd / Tn));
+      const double mu = Sd * rT;
+      const double var = Qd * rT - mu * mu;
+      rs_->prec = !(var >= 1e-3 * (Qd * rT));
       rs_->var = var;
     }
     __syncthreads();
@@ -341,7 +353,7 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
         s += ((double)v.x + (double)v.y) + ((double)v.z + (double)v.w);  // padding is 0
       }
       s = block_dsum(s, red);
-      const double m2 = s / Tn;
+      const double m2 = s * rT;
       double ss = 0.0;
       for (int k = threadIdx.x; k < nch; k += NT) {
         const float4 v = st[k];
@@ -355,14 +367,14 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
       }
       ss = block_dsum(ss, red);
       if (threadIdx.x == 0) {
-        rs_->var = ss / Tn;
+        rs_->var = ss * rT;
         Sd = s;  // the two-pass mean
       }
     }
     if (threadIdx.x == 0) {
-      const double mu = Sd / Tn;
+      const double mu = Sd * rT;
       const double var = rs_->var;
-      const double thr = cut.k * sqrt(var > 0.0 ? var : 0.0);
+      const double thr = cut.k * sqrt_fast(var);
       rs_->mu_thr[0] = mu;
       rs_->mu_thr[1] = thr;
       const float mu_f = __double2float_rn(mu);
@@ -482,9 +494,10 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
 }
 
 // ---------------------------------------------------------------------------
-// FDSC on one item: FD32_ITEM_T time samples x C channels of a float32 beam.
-// 16 samples are 64 bytes of each channel row: the lines an item touches stay
-// in L2 across its sub-slabs even with every SM's items in flight.
+// FDSC on one item: one sub-slab of ws time samples x C channels of a float32
+// beam (16 bytes of each channel row for ws = 4).  Consecutive items, which
+// share the 128-byte lines of the rows, run at the same time, so the lines in
+// flight stay few and are read from DRAM once.
 // ---------------------------------------------------------------------------
 // Tile [c][t] (pitch ws floats).  Work units are (t, bin) pairs, one thread
 // each, t fastest; a unit walks its bin starting at a rotation of (bin mod 32)
@@ -541,35 +554,81 @@ __device__ float bin_median_f32(const float* tile, int c0, int n, int ws, int t)
 __device__ void fdsc_item_f32(const Params& P, const Job& J, int item, unsigned char* smem, Red32* red) {
   const CutDev& cut = P.fd;
   const int C = J.C, T = J.T, G = cut.bin, NB = J.nb, Gl = J.last_g;
-  const int t_item = item * FD32_ITEM_T;
-  const int t_end = min(t_item + FD32_ITEM_T, T);
   const int Ws = J.ws;
+  const int t_item = item * Ws;
+  const int t_end = min(t_item + Ws, T);
   const float* src = static_cast<const float*>(P.fd_reads_out ? J.out : J.in);
   float* dst = static_cast<float*>(J.out);
   const Fd32Layout L = fd32_layout(smem, Ws, C, NB);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool vec = ((((uintptr_t)src) | ((uintptr_t)dst)) & 15) == 0 && (T & 3) == 0;
-  const double Cn = (double)C;
+  const double Cn = (double)C, rC = 1.0 / (double)C;
 
   for (int c = threadIdx.x; c < C; c += NT) L.fm[c] = 0;
 
   for (int t0 = t_item; t0 < t_end; t0 += Ws) {
     const int w = min(Ws, t_end - t0);
-    // ---- load the sub-slab: thread per channel
-    for (int c = threadIdx.x; c < C; c += NT) {
-      const float* a = src + (size_t)c * T + t0;
-      float* d = L.tile + c * Ws;
-      if (vec && w == Ws && Ws >= 4) {
-#pragma unroll 2
-        for (int j = 0; j < Ws; j += 4) *reinterpret_cast<float4*>(d + j) = ld_f4_na(a + j);
-      } else {
+    // ---- load the sub-slab: thread per channel; 16-byte asynchronous copies
+    //      (all in flight at once, L1 bypassed) where rows allow them
+    if (vec && w == Ws && Ws >= 4) {
+      for (int c = threadIdx.x; c < C; c += NT) {
+        const float* a = src + (size_t)c * T + t0;
+        float* d = L.tile + c * Ws;
+        for (int j = 0; j < Ws; j += 4) {
+          const unsigned sdst = (unsigned)__cvta_generic_to_shared(d + j);
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sdst), "l"(a + j) : "memory");
+        }
+      }
+      asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+    } else {
+      for (int c = threadIdx.x; c < C; c += NT) {
+        const float* a = src + (size_t)c * T + t0;
+        float* d = L.tile + c * Ws;
         for (int j = 0; j < w; j++) d[j] = a[j];
       }
     }
     __syncthreads();
 
     const int U = w * NB;
+    // 4-sample sub-slabs of 32-channel bins, mean replacement: a thread owns half
+    // a bin (16 channels) over the 4 samples, read as one float4 per channel
+    const bool quad = w == 4 && Ws == 4 && G == 32 && (C & 31) == 0 && cut.replace == REP_MEAN;
+    float4* tile4 = reinterpret_cast<float4*>(L.tile);
     for (int it = 0; it < cut.iterations; it++) {
+      if (quad) {
+        // whole warps take part in every round (the pair shuffle below needs all lanes)
+        for (int ub = 0; ub < 2 * NB; ub += NT) {
+          const int u = ub + threadIdx.x;
+          const bool act = u < 2 * NB;
+          const int g = u >> 1, c0 = 32 * g + 16 * (u & 1), rot = u & 7;
+          FF s[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+          FF q[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 4
+          for (int j = 0; j < (act ? 16 : 0); j++) {
+            const float4 v = tile4[c0 + ((j + rot) & 15)];
+            ff_acc(s[0], v.x);
+            ff_acc_sq(q[0], v.x);
+            ff_acc(s[1], v.y);
+            ff_acc_sq(q[1], v.y);
+            ff_acc(s[2], v.z);
+            ff_acc_sq(q[2], v.z);
+            ff_acc(s[3], v.w);
+            ff_acc_sq(q[3], v.w);
+          }
+#pragma unroll
+          for (int t = 0; t < 4; t++) {
+            s[t] = ff_add(s[t], shfl_ff(s[t], 1));  // the other half of the bin
+            q[t] = ff_add(q[t], shfl_ff(q[t], 1));
+            if (act && (u & 1) == 0) {
+              const FF m = ff_add(ff_div_int(s[t], 32), FF{0.f, 0.f});
+              const FF m2 = ff_add(q[t], ff_neg(ff_mul(s[t], m)));
+              L.um[g * 4 + t] = make_float2(m.hi, m.lo);
+              L.uv[g * 4 + t] = make_float2(m2.hi, m2.lo);
+              L.uq[g * 4 + t] = q[t].hi;
+            }
+          }
+        }
+      } else
       // ---- per (t, bin): float-float sum and sum of squares, bin mean, M2
       for (int u = threadIdx.x; u < U; u += NT) {
         const int t = u % w, g = u / w;
@@ -605,7 +664,7 @@ __device__ void fdsc_item_f32(const Params& P, const Job& J, int item, unsigned 
           const double V = ff_d(v);
           const int prec = !(V >= 1e-3 * (double)qs);
           L.prec[t] = prec;
-          const double thr = cut.k * sqrt((V > 0.0 ? V : 0.0) / Cn);
+          const double thr = cut.k * sqrt_fast(V * rC);
           L.thr[t] = thr;
           L.thr_lo[t] = __double2float_rd(thr);
           L.thr_hi[t] = __double2float_ru(thr);
@@ -621,7 +680,7 @@ __device__ void fdsc_item_f32(const Params& P, const Job& J, int item, unsigned 
           sd += (double)L.tile[c * Ws + t] - ((double)m.x + (double)m.y);
         }
         sd = warp_sum(sd);
-        const double mup = sd / Cn;
+        const double mup = sd * rC;
         double ss = 0.0;
         for (int c = lane; c < C; c += 32) {
           const float2 m = L.um[(c / G) * w + t];
@@ -630,14 +689,45 @@ __device__ void fdsc_item_f32(const Params& P, const Job& J, int item, unsigned 
         }
         ss = warp_sum(ss);
         if (lane == 0) {
-          const double thr = cut.k * sqrt(ss / Cn);
+          const double thr = cut.k * sqrt_fast(ss * rC);
           L.thr[t] = thr;
           L.thr_lo[t] = __double2float_rd(thr);
           L.thr_hi[t] = __double2float_ru(thr);
         }
       }
       __syncthreads();
-      // ---- decide and replace, per (t, bin)
+      // ---- decide and replace
+      if (quad) {
+        // per half bin: its 16 channels over the 4 samples; a thread owns its
+        // channels' flag words (fm) in every 4-sample sub-slab
+        const int sh = t0 - t_item;
+        for (int u = threadIdx.x; u < 2 * NB; u += NT) {
+          const int g = u >> 1, c0 = 32 * g + 16 * (u & 1), rot = u & 7;
+          Cut32 cc[4];
+#pragma unroll
+          for (int t = 0; t < 4; t++) {
+            const float2 m = L.um[g * 4 + t];
+            cc[t].mu_f = m.x;
+            cc[t].mu_lo = m.y;
+            cc[t].thr = &L.thr[t];
+            band_bounds_f(L.thr_lo[t], L.thr_hi[t], fabsf(m.y), cc[t].lo_f, cc[t].hi_f);
+          }
+#pragma unroll 2
+          for (int j = 0; j < 16; j++) {
+            const int c = c0 + ((j + rot) & 15);
+            float4 v = tile4[c];
+            unsigned nib = 0;
+            if (flag32(v.x, cc[0])) { v.x = cc[0].mu_f; nib |= 1u; }
+            if (flag32(v.y, cc[1])) { v.y = cc[1].mu_f; nib |= 2u; }
+            if (flag32(v.z, cc[2])) { v.z = cc[2].mu_f; nib |= 4u; }
+            if (flag32(v.w, cc[3])) { v.w = cc[3].mu_f; nib |= 8u; }
+            if (nib) {
+              tile4[c] = v;
+              L.fm[c] |= nib << sh;
+            }
+          }
+        }
+      } else
       for (int u = threadIdx.x; u < U; u += NT) {
         const int t = u % w, g = u / w;
         const int c0 = g * G, n = g == NB - 1 ? Gl : G;
@@ -684,20 +774,17 @@ __device__ void fdsc_item_f32(const Params& P, const Job& J, int item, unsigned 
     __syncthreads();
   }
 
-  // ---- flags.  Two items share a mask word: each changes only its own bit
-  //      field (the last item of a row also clears the padding bits above it).
+  // ---- flags.  Items of ws samples share a mask word (ws divides 32): each
+  //      ORs its flagged bits in; the word was written by the TDSC rows or zeroed.
   const int nt = t_end - t_item;
-  const unsigned valid = (1u << nt) - 1u;  // nt <= 16
+  const unsigned valid = (1u << nt) - 1u;  // nt <= 8
   if (P.mask_kind == MASK_BITS && J.mask) {
     const int W32 = (T + 31) >> 5;
     const int sh = t_item & 31;
     unsigned* mb = static_cast<unsigned*>(J.mask) + (t_item >> 5);
-    const unsigned field = t_end == T ? (0xFFFFFFFFu << sh) : (0xFFFFu << sh);
     for (int c = threadIdx.x; c < C; c += NT) {
       const unsigned f = (L.fm[c] & valid) << sh;
-      unsigned* wp = mb + (size_t)c * W32;
-      if (!P.mask_or) atomicAnd(wp, ~field);
-      if (f) atomicOr(wp, f);
+      if (f) atomicOr(mb + (size_t)c * W32, f);
     }
   } else if (P.mask_kind == MASK_BYTES && J.mask) {
     uint8_t* mb = static_cast<uint8_t*>(J.mask);
