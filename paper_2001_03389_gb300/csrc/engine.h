@@ -78,7 +78,7 @@ __host__ __device__ inline int fd_nbp(int nb) { return nb + ((8 - nb) % 32 + 32)
 
 __host__ __device__ inline int fd_smem_bytes(int ws, int pitch, int nb, int C) {
   const int nbp = fd_nbp(nb);
-  return ws * pitch + align16i(ws * nbp * 4) + align16i(ws * nbp * 2) + align16i(ws * 8) + align16i(ws * 8) +
+  return ws * pitch + 2 * align16i(ws * nbp * 4) + align16i(ws * nbp * 2) + align16i(ws * 8) + align16i(ws * 8) +
          align16i(C * 4) + align16i(ws * nb * 4) + 4 * (NT / 32);
 }
 
@@ -113,10 +113,6 @@ struct LaunchCfg {
 };
 int engine_smem_u8(const Params& p);
 void* engine_kernel_u8(const Params& p);
-// dynamic shared memory per CTA with three CTAs per SM: 228 KB / 3 = 77824 B
-// less the 1 KB the runtime reserves per CTA and the kernel's ~0.5 KB of
-// static shared variables
-constexpr int FD_SMEM_3PER_SM = 233472 / 3 - 1024 - 768;
 int launch_engine_u8(const Params& p, const LaunchCfg& cfg, void* stream);
 
 // float32 engine: TDSC rows of up to TD32_MAX_T samples staged per CTA; FDSC tile

@@ -654,6 +654,7 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
 struct FdLayout {
   uint8_t* tile;          // ws rows x pitch bytes
   unsigned* Sg;           // ws x nbp bin sums
+  unsigned* Qg;           // ws x nbp bin sums of squares
   uint16_t* med;          // ws x nbp cached bin medians (0xFFFF unknown)
   unsigned long long* V;  // ws: sum of D^2 per column
   unsigned* A;            // ws x 2: keep half-widths per bin-size class
@@ -669,6 +670,8 @@ __device__ __forceinline__ FdLayout fd_layout(unsigned char* smem, int ws, int p
   L.tile = p;
   p += ws * pitch;
   L.Sg = reinterpret_cast<unsigned*>(p);
+  p += align16i(ws * nbp * 4);
+  L.Qg = reinterpret_cast<unsigned*>(p);
   p += align16i(ws * nbp * 4);
   L.med = reinterpret_cast<uint16_t*>(p);
   p += align16i(ws * nbp * 2);
@@ -693,21 +696,34 @@ __device__ __forceinline__ int toff(int r, int c, int pitch) {
 // 16 channels x 4 samples.  16 row words (lanes along time, so 8 lanes read 32
 // contiguous bytes of a row), four 4x4 byte transposes, and one 16-byte shared
 // store per sample row (the 16 channels are one swizzle unit).
+template <int UPR>  // units per round: their 16 x UPR row words are in flight together
 __device__ __forceinline__ void fd_load_full(uint8_t* tile, const uint8_t* src, int C, int T, int t0, int pitch) {
   const int nunits = (C >> 4) * 8;
-  for (int u = threadIdx.x; u < nunits; u += NT) {
-    const int tq = u & 7, cg = u >> 3;
-    const uint8_t* a = src + (size_t)(cg * 16) * T + t0 + 4 * tq;
-    uint32_t w[16];
+  for (int u0 = threadIdx.x; u0 < nunits; u0 += UPR * NT) {
+    uint32_t w[UPR][16];
 #pragma unroll
-    for (int i = 0; i < 16; i++) w[i] = *reinterpret_cast<const uint32_t*>(a + (size_t)i * T);
+    for (int k = 0; k < UPR; k++) {
+      const int u = u0 + k * NT;
+      if (u < nunits) {
+        const uint8_t* a = src + (size_t)((u >> 3) * 16) * T + t0 + 4 * (u & 7);
 #pragma unroll
-    for (int g = 0; g < 4; g++) transpose4x4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3]);
+        for (int i = 0; i < 16; i++) w[k][i] = *reinterpret_cast<const uint32_t*>(a + (size_t)i * T);
+      }
+    }
 #pragma unroll
-    for (int r = 0; r < 4; r++) {
-      const int t = 4 * tq + r;
-      *reinterpret_cast<uint4*>(tile + t * pitch + ((cg ^ ((t >> 2) & 7)) << 4)) =
-          make_uint4(w[r], w[4 + r], w[8 + r], w[12 + r]);
+    for (int k = 0; k < UPR; k++) {
+      const int u = u0 + k * NT;
+      if (u < nunits) {
+        const int tq = u & 7, cg = u >> 3;
+#pragma unroll
+        for (int g = 0; g < 4; g++) transpose4x4(w[k][4 * g], w[k][4 * g + 1], w[k][4 * g + 2], w[k][4 * g + 3]);
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+          const int t = 4 * tq + r;
+          *reinterpret_cast<uint4*>(tile + t * pitch + ((cg ^ ((t >> 2) & 7)) << 4)) =
+              make_uint4(w[k][r], w[k][4 + r], w[k][8 + r], w[k][12 + r]);
+        }
+      }
     }
   }
 }
@@ -883,7 +899,6 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
   const int sl = lane % LPC;
   const int tcol = warp * cpw + lane / LPC;
   unsigned* wlist = L.list + warp * (cpw * NB);
-  unsigned* wcnt = L.cnt + warp;
   const float rcpG = 1.0f / (float)G, rcpL = 1.0f / (float)Gl;
   const int NBP = fd_nbp(NB);
   const bool fast32 = G == 32;  // whole bins are two 16-byte tile units
@@ -901,7 +916,7 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
     // ---- load: units of 4 channels x 4 samples, lanes along time, transposed into [t][c];
     //      four units per thread are in flight at a time
     if (full && rows4) {
-      fd_load_full(L.tile, src, C, T, t0, pitch);
+      fd_load_full<1>(L.tile, src, C, T, t0, pitch);
     } else {
       const int nunits = nq * nt4;
       for (int ub = threadIdx.x; ub < nunits; ub += 4 * NT) {
@@ -986,6 +1001,7 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
             }
           }
           L.Sg[t * NBP + gi] = s;
+          L.Qg[t * NBP + gi] = q;
           v += fd_contrib(gi == NB - 1 ? ml : mf, gsz, s, q);
         }
       }
@@ -1003,9 +1019,9 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
         L.A[2 * tcol] = Af;
         L.A[2 * tcol + 1] = Al;
       }
-      if (lane == 0) *wcnt = 0;
-      __syncwarp();
-      // pass B: bins with a byte outside their keep interval
+      // pass B: bins with a byte outside their keep interval, compacted into this
+      //        warp's list (the running length is the same in every lane)
+      unsigned nlist = 0;
       const int nsteps = (NB + LPC - 1) / LPC;
       for (int stp = 0; stp < nsteps; stp++) {
         const int gi = sl + stp * LPC;
@@ -1046,13 +1062,11 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
           }
         }
         const unsigned b = __ballot_sync(0xffffffffu, any);
-        const unsigned n0 = *wcnt;
-        if (any) wlist[n0 + __popc(b & ((1u << lane) - 1u))] = (unsigned)(tcol * NB + gi);
-        __syncwarp();
-        if (lane == 0) *wcnt = n0 + __popc(b);
-        __syncwarp();
+        if (any) wlist[nlist + __popc(b & ((1u << lane) - 1u))] = (unsigned)(tcol * NB + gi);
+        nlist += __popc(b);
       }
-      const unsigned n = *wcnt;
+      __syncwarp();  // the list entries are visible to the whole warp
+      const unsigned n = nlist;
       // resolve the flagged bins of this warp's columns, one per lane
       for (unsigned e = lane; e < n; e += 32) {
         const int pair = (int)wlist[e];
@@ -1065,16 +1079,7 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
           // the bin in registers: two 16-byte loads, half order staggered by lane
           uint32_t w[8];
           load_bin32(L.tile, t, gi, pitch, lane & 1, w);
-          unsigned s_old = 0, q_old = 0, s1 = 0, q1 = 0;
-#pragma unroll
-          for (int i = 0; i < 8; i += 2) {
-            s_old = dp4a_u(w[i], 0x01010101u, s_old);
-            q_old = dp4a_u(w[i], w[i], q_old);
-            s1 = dp4a_u(w[i + 1], 0x01010101u, s1);
-            q1 = dp4a_u(w[i + 1], w[i + 1], q1);
-          }
-          s_old += s1;
-          q_old += q1;
+          const unsigned s_old = L.Sg[t * NBP + gi], q_old = L.Qg[t * NBP + gi];
           const unsigned A = L.A[2 * t + (lastbin ? 1 : 0)];
           const int lo = s_old <= A ? 0 : (int)((s_old - A + 31) >> 5);
           const unsigned hv = (s_old + A) >> 5;
@@ -1096,14 +1101,18 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
           }
           const ByteKeep kp = make_keep(lo, hi);
           const uint32_t r4 = splat4(r);
-          unsigned s_new = 0, q_new = 0;
-          bool changed = false;
+          // sums of the replaced originals; the new sums follow from them
+          unsigned s_rep = 0, q_rep = 0, n_rep = 0;
 #pragma unroll
           for (int i = 0; i < 8; i++) {
             const uint32_t f = outside_exact(w[i], kp);
-            const uint32_t y = w[i] ^ ((w[i] ^ r4) & ((f >> 7) * 0xFFu));
             if (f) {
-              changed |= (y != w[i]);
+              const uint32_t wm = (f >> 7) * 0xFFu;
+              const uint32_t xo = w[i] & wm;
+              s_rep = dp4a_u(xo, 0x01010101u, s_rep);
+              q_rep = dp4a_u(xo, xo, q_rep);
+              n_rep += __popc(f);
+              w[i] ^= (w[i] ^ r4) & wm;
               uint32_t ff = f;
               while (ff) {
                 const int byte = (__ffs(ff) - 1) >> 3;
@@ -1111,13 +1120,12 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
                 atomicOr(&L.fmask[gi * 32 + 4 * i + byte], bit);
               }
             }
-            w[i] = y;
-            s_new = dp4a_u(y, 0x01010101u, s_new);
-            q_new = dp4a_u(y, y, q_new);
           }
-          if (changed) {
+          const unsigned s_new = s_old - s_rep + n_rep * r, q_new = q_old - q_rep + n_rep * r * r;
+          if (s_new != s_old || q_new != q_old) {  // some value changed (equal sums imply x == r)
             store_bin32(L.tile, t, gi, pitch, w);
             L.Sg[t * NBP + gi] = s_new;
+            L.Qg[t * NBP + gi] = q_new;
             atomicAdd(&L.V[t], fd_contrib(mm, 32u, s_new, q_new) - fd_contrib(mm, 32u, s_old, q_old));
           }
           continue;
@@ -1189,6 +1197,7 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
         }
         if (s_new != s_old || q_new != q_old) {
           L.Sg[t * NBP + gi] = s_new;
+          L.Qg[t * NBP + gi] = q_new;
           atomicAdd(&L.V[t], fd_contrib(mm, gsz, s_new, q_new) - fd_contrib(mm, gsz, s_old, q_old));
         }
       }
@@ -1280,8 +1289,8 @@ __device__ bool wait_rows(const Params& P, int job, unsigned need, int* flag) {
   return ok;
 }
 
-// MINB = CTAs per SM the register allocation targets: 2 for launches with
-// TDSC items (their row stage is 102 KB), 3 for FDSC-only launches (a 72 KB tile).
+// MINB = CTAs per SM the register allocation targets (the TDSC row stage is
+// 102 KB, so two CTAs share an SM).
 template <int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_engine_u8(const __grid_constant__ Params P) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1346,13 +1355,9 @@ int engine_smem_u8(const Params& p) {
   return align16i(s);
 }
 
-// FDSC-only launches whose tile fits three CTAs per SM use the 3-CTA build.
-static bool use_minb3(const Params& p) {
-  return p.td.iterations == 0 && engine_smem_u8(p) <= FD_SMEM_3PER_SM;
-}
-
 void* engine_kernel_u8(const Params& p) {
-  return use_minb3(p) ? (void*)k_engine_u8<3> : (void*)k_engine_u8<2>;
+  (void)p;
+  return (void*)k_engine_u8<2>;
 }
 
 int launch_engine_u8(const Params& p, const LaunchCfg& cfg, void* stream) {
