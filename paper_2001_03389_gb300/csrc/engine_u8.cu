@@ -1062,7 +1062,7 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
           }
         }
         const unsigned b = __ballot_sync(0xffffffffu, any);
-        if (any) wlist[nlist + __popc(b & ((1u << lane) - 1u))] = (unsigned)(tcol * NB + gi);
+        if (any) wlist[nlist + __popc(b & ((1u << lane) - 1u))] = ((unsigned)tcol << 16) | (unsigned)gi;
         nlist += __popc(b);
       }
       __syncwarp();  // the list entries are visible to the whole warp
@@ -1070,7 +1070,7 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
       // resolve the flagged bins of this warp's columns, one per lane
       for (unsigned e = lane; e < n; e += 32) {
         const int pair = (int)wlist[e];
-        const int t = pair / NB, gi = pair % NB;
+        const int t = pair >> 16, gi = pair & 0xFFFF;  // (column, bin) packed by the flag pass
         const bool lastbin = gi == NB - 1;
         const unsigned gsz = lastbin ? (unsigned)Gl : (unsigned)G;
         const unsigned bit = 1u << (t0 + t - t_item);

@@ -265,3 +265,49 @@ def torch_ragged_batch(shapes, seed: int, device, layout: str = "bct"):
         b = torch_beam_u8(gen, C, T, cfg2_model(), device)
         out.append(b.t().contiguous() if layout == "btc" else b)
     return out
+
+
+# ---------------------------------------------------------------------------
+# The simulated accuracy canvas of Sec. V-A (Figs. 4-6): Gaussian noise
+# (mu = 0, sigma = 1) on the ARTS band, a faint dispersed FRB and bright RFI.
+# ---------------------------------------------------------------------------
+K_DM = 4.15e3          # MHz^2 pc^-1 cm^3 s (Eq. 2)
+T_SAMP = 81.92e-6      # s (Sec. V-A)
+
+
+def dm_delays(C: int, dm: float, f_hi: float = F_HI_MHZ, bw: float = BW_MHZ, dt: float = T_SAMP) -> np.ndarray:
+    """Per-channel delay in samples of a pulse of dispersion measure dm (Eq. 2),
+    channel 0 the highest frequency."""
+    f = f_hi - bw * (np.arange(C) + 0.5) / C
+    return np.rint(K_DM * (f ** -2.0 - f_hi ** -2.0) * dm / dt).astype(np.int64)
+
+
+FRB_CANVAS = dict(frb_dm=500.0, frb_t0=488, frb_snr=15.0,            # Fig. 4 caption; t0 = 0.04 s
+                  bb=((1.0, 2000, 100.0), (10.0, 6500, 150.0)),       # (DM, start, amplitude in sigma)
+                  nb=((300, 10), (900, 15)), nb_amp=125.0, nb_period=400, nb_width=16)
+
+
+def frb_canvas(C: int = 1536, T: int = 8192, seed: int = SEED_BASE + 6, frb: bool = True, rfi: bool = True):
+    """float32 (C, T) block: N(0, 1) noise, a one-sample FRB at DM 500 whose
+    dedispersed S/N is 15 (amplitude 15 / sqrt(C) per channel), two bright
+    low-DM broadband pulses (DM 1 and 10, 100 and 150 sigma per channel) and two
+    periodic narrowband pulses (125 sigma in 10 and 15 channels)."""
+    p = FRB_CANVAS
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal((C, T)).astype(np.float32)
+    ch = np.arange(C)
+
+    def sweep(dm, t0, amp):
+        ts = t0 + dm_delays(C, dm)
+        ok = ts < T
+        x[ch[ok], ts[ok]] += np.float32(amp)
+
+    if frb:
+        sweep(p["frb_dm"], p["frb_t0"], p["frb_snr"] / np.sqrt(C))
+    if rfi:
+        for dm, t0, amp in p["bb"]:
+            sweep(dm, t0, amp)
+        for c0, n in p["nb"]:
+            for t in range(100, T, p["nb_period"]):
+                x[c0:c0 + n, t:t + p["nb_width"]] += np.float32(p["nb_amp"])
+    return x
