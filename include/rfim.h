@@ -151,6 +151,11 @@ rfim_status rfim_destroy(rfim_ctx* ctx);
  *                     (uint8 tiles use at least 8, float32 tiles at most 8);
  *   "smem_target"     shared memory an FDSC tile may use, bytes (sets the automatic width);
  *   "fused_lag"       beams of TDSC rows queued ahead of a beam's FDSC items (0..8);
+ *   "order"           order of the methods in rfim_clean and rfim_clean_batch:
+ *                     0 = blocked (all TDSC iterations on every row, then all
+ *                     FDSC iterations on every column; default), 1 = interleaved
+ *                     (round i: TDSC iteration i on every row, then FDSC
+ *                     iteration i on every column; single-iteration launches);
  *   "ctas_per_sm"     persistent-kernel CTAs per SM (0 = occupancy maximum);
  *   "withhold_tdsc_done"  test hook: 1 makes the fused kernel never publish the
  *                     TDSC completion of beam 0, so its FDSC items time out

@@ -61,6 +61,10 @@ def lib():
         L.orc_clean_u8.restype = ctypes.c_int
         L.orc_clean_f32.argtypes = [f32p, f32p, u8p, i64, i64, i64, ctypes.c_int, cutp, cutp]
         L.orc_clean_f32.restype = ctypes.c_int
+        L.orc_clean_u8_interleaved.argtypes = [u8p, u8p, u8p, i64, i64, i64, ctypes.c_int, cutp, cutp]
+        L.orc_clean_u8_interleaved.restype = ctypes.c_int
+        L.orc_clean_f32_interleaved.argtypes = [f32p, f32p, u8p, i64, i64, i64, ctypes.c_int, cutp, cutp]
+        L.orc_clean_f32_interleaved.restype = ctypes.c_int
         f64p = ctypes.POINTER(ctypes.c_double)
         L.orc_clean_f32m.argtypes = [f32p, f32p, u8p, f64p, i64, i64, i64, ctypes.c_int, cutp, cutp]
         L.orc_clean_f32m.restype = ctypes.c_int
@@ -98,14 +102,19 @@ class OracleError(RuntimeError):
         self.rc = rc
 
 
-def clean(x: np.ndarray, layout: str = "bct", tdsc: dict | None = None, fdsc: dict | None = None):
+def clean(x: np.ndarray, layout: str = "bct", tdsc: dict | None = None, fdsc: dict | None = None,
+          order: str = "blocked"):
     """Clean a 3-D filterbank block.
 
     x: uint8 or float32 array shaped (B, C, T) for layout 'bct' or (B, T, C)
     for 'btc'.  tdsc / fdsc: dicts with k, iterations, replace ('mean' or
     'median') and, for fdsc, bin (defaults to 32 capped at C).
+    order: 'blocked' (all TDSC iterations, then all FDSC iterations) or
+    'interleaved' (TDSC iteration i, then FDSC iteration i, per round).
     Returns (out, flags) where flags holds bit 0 = TDSC, bit 1 = FDSC.
     """
+    if order not in ("blocked", "interleaved"):
+        raise ValueError(order)
     x = np.ascontiguousarray(x)
     if layout == "bct":
         B, C, T = x.shape
@@ -116,12 +125,15 @@ def clean(x: np.ndarray, layout: str = "bct", tdsc: dict | None = None, fdsc: di
     out = np.empty_like(x)
     flags = np.zeros(x.shape, dtype=np.uint8)
     L = lib()
+    il = order == "interleaved"
     if x.dtype == np.uint8:
-        rc = L.orc_clean_u8(_ptr(x, ctypes.c_uint8), _ptr(out, ctypes.c_uint8), _ptr(flags, ctypes.c_uint8),
-                            B, C, T, LAYOUT[layout], ctypes.byref(tc), ctypes.byref(fc))
+        fn = L.orc_clean_u8_interleaved if il else L.orc_clean_u8
+        rc = fn(_ptr(x, ctypes.c_uint8), _ptr(out, ctypes.c_uint8), _ptr(flags, ctypes.c_uint8),
+                B, C, T, LAYOUT[layout], ctypes.byref(tc), ctypes.byref(fc))
     elif x.dtype == np.float32:
-        rc = L.orc_clean_f32(_ptr(x, ctypes.c_float), _ptr(out, ctypes.c_float), _ptr(flags, ctypes.c_uint8),
-                             B, C, T, LAYOUT[layout], ctypes.byref(tc), ctypes.byref(fc))
+        fn = L.orc_clean_f32_interleaved if il else L.orc_clean_f32
+        rc = fn(_ptr(x, ctypes.c_float), _ptr(out, ctypes.c_float), _ptr(flags, ctypes.c_uint8),
+                B, C, T, LAYOUT[layout], ctypes.byref(tc), ctypes.byref(fc))
     else:
         raise TypeError(f"unsupported dtype {x.dtype}")
     if rc != 0:

@@ -365,3 +365,51 @@ int orc_clean_f32m(const float* in, float* out, uint8_t* flags, double* margin, 
   free(mg);
   return ORC_OK;
 }
+
+
+/* ------------------------------------------------------------------ */
+/* Interleaved order: round i runs TDSC iteration i on every row, then  */
+/* FDSC iteration i on every column (each a single-iteration cut on the  */
+/* current values); flags are OR-ed over rounds.  With one iteration of  */
+/* each method this is the blocked order.                                */
+/* ------------------------------------------------------------------ */
+static int clean_interleaved(const void* in, void* out, uint8_t* flags, int64_t B, int64_t C, int64_t T,
+                             int layout, const orc_cut* tdsc, const orc_cut* fdsc, int is_f32) {
+  int rc = check_block(B, C, T, layout, tdsc, fdsc);
+  if (rc) return rc;
+  const int64_t N = B * C * T;
+  const size_t es = is_f32 ? sizeof(float) : 1;
+  if (out != in) memmove(out, in, (size_t)N * es);
+  if (flags) memset(flags, 0, (size_t)N);
+  uint8_t* fr = flags ? (uint8_t*)malloc((size_t)N) : NULL;
+  const int it_t = (tdsc && tdsc->enabled) ? tdsc->iterations : 0;
+  const int it_f = (fdsc && fdsc->enabled) ? fdsc->iterations : 0;
+  const int rounds = it_t > it_f ? it_t : it_f;
+  for (int r = 0; r < rounds && rc == ORC_OK; r++) {
+    orc_cut t1 = {0, 0.0, 0, 0, 0}, f1 = {0, 0.0, 0, 0, 0};
+    if (r < it_t) {
+      t1 = *tdsc;
+      t1.iterations = 1;
+    }
+    if (r < it_f) {
+      f1 = *fdsc;
+      f1.iterations = 1;
+    }
+    rc = is_f32 ? orc_clean_f32((const float*)out, (float*)out, fr, B, C, T, layout, &t1, &f1)
+                : orc_clean_u8((const uint8_t*)out, (uint8_t*)out, fr, B, C, T, layout, &t1, &f1);
+    if (flags)
+      for (int64_t i = 0; i < N; i++) flags[i] |= fr[i];
+  }
+  free(fr);
+  return rc;
+}
+
+int orc_clean_u8_interleaved(const uint8_t* in, uint8_t* out, uint8_t* flags, int64_t B, int64_t C, int64_t T,
+                             int layout, const orc_cut* tdsc, const orc_cut* fdsc) {
+  return clean_interleaved(in, out, flags, B, C, T, layout, tdsc, fdsc, 0);
+}
+
+int orc_clean_f32_interleaved(const float* in, float* out, uint8_t* flags, int64_t B, int64_t C, int64_t T,
+                              int layout, const orc_cut* tdsc, const orc_cut* fdsc) {
+  return clean_interleaved(in, out, flags, B, C, T, layout, tdsc, fdsc, 1);
+}

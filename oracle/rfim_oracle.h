@@ -81,6 +81,16 @@ void orc_fdsc_col_u8(uint8_t* x, uint8_t* f, int64_t n, double k, int iters, int
 void orc_tdsc_row_f32(float* x, uint8_t* f, int64_t n, double k, int iters, int replace);
 void orc_fdsc_col_f32(float* x, uint8_t* f, int64_t n, double k, int iters, int replace, int64_t bin);
 
+/* The combined cleaner in interleaved order: round i applies TDSC iteration i
+ * to every row, then FDSC iteration i to every column (single-iteration cuts
+ * on the current values), for max(iterations) rounds; flags OR over rounds. */
+int orc_clean_u8_interleaved(const uint8_t* in, uint8_t* out, uint8_t* flags,
+                             int64_t B, int64_t C, int64_t T, int layout,
+                             const orc_cut* tdsc, const orc_cut* fdsc);
+int orc_clean_f32_interleaved(const float* in, float* out, uint8_t* flags,
+                              int64_t B, int64_t C, int64_t T, int layout,
+                              const orc_cut* tdsc, const orc_cut* fdsc);
+
 /* The same float32 cuts with a diagnostic output (nullable): margin[i] is the
  * minimum over the sample's decisions of |(|x - mu| - k sigma)| / (k sigma),
  * its relative distance from the nearest threshold (INFINITY where sigma = 0). */

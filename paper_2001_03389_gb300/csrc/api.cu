@@ -51,6 +51,7 @@ struct rfim_ctx {
   int withhold = 0;
   int smem_target = 113 * 1024;
   int fused_lag = 1;
+  int order = 0;  // 0 = blocked (all TDSC iterations, then FDSC), 1 = interleaved rounds
   // graphs for rfim_clean_batch (each with its own counter blocks)
   std::map<std::vector<unsigned char>, std::pair<cudaGraphExec_t, unsigned*>> graphs;
   unsigned* capture_counters = nullptr;  // while capturing: counter blocks of the graph
@@ -348,7 +349,8 @@ int occupancy(void* fn, int smem) {
 }
 
 // Build the Params of one launch over jobs [j0, j1) with the given item kinds.
-// mode: 0 = TDSC only, 1 = FDSC only (reads `in`), 2 = fused TDSC->FDSC, 3 = FDSC reading `out`.
+// mode: 0 = TDSC only, 1 = FDSC only (reads `in`), 2 = fused TDSC->FDSC, 3 = FDSC reading `out`,
+// 5 = TDSC on `out` in place, OR-ing its flags into the mask (interleaved rounds).
 void fill_params(rfim_ctx* ctx, const Plan& pl, int j0, int j1, int mode, Params& p, unsigned* counters) {
   memset(&p, 0, sizeof p);
   p.n_jobs = j1 - j0;
@@ -356,7 +358,17 @@ void fill_params(rfim_ctx* ctx, const Plan& pl, int j0, int j1, int mode, Params
   p.td = cut_dev(pl.td);
   p.fd = cut_dev(pl.fd);
   if (mode == 1 || mode == 3) p.td.iterations = 0;
-  if (mode == 0) p.fd.iterations = 0;
+  if (mode == 0 || mode == 5) p.fd.iterations = 0;
+  if (mode == 5) {
+    for (int j = 0; j < p.n_jobs; j++) {
+      Job& J = p.jobs[j];
+      const size_t beam = (size_t)J.C * J.T * (pl.dtype == RFIM_F32 ? 4 : 1);
+      J.in = J.out;
+      J.src_lo = J.out;
+      J.src_hi = (const char*)J.out + beam;
+    }
+    p.td_mask_or = 1;
+  }
   p.mask_kind = pl.mask_kind;
   p.fd_reads_out = (mode == 2 || mode == 3) ? 1 : 0;
   p.wait_tdsc = mode == 2 ? 1 : 0;
@@ -366,7 +378,7 @@ void fill_params(rfim_ctx* ctx, const Plan& pl, int j0, int j1, int mode, Params
   p.counters = counters;
   p.status = ctx->d_status;
   p.dtype = pl.dtype == RFIM_F32 ? 1 : 0;
-  fill_segments(p, mode, ctx->fused_lag);
+  fill_segments(p, mode == 5 ? 0 : mode, ctx->fused_lag);
 }
 
 // float32 FDSC items OR their bits into the mask words they share: a launch
@@ -413,7 +425,22 @@ rfim_status run_plan(rfim_ctx* ctx, const Plan& pl, cudaStream_t st) {
   for (int j0 = 0; j0 < nj; j0 += MAX_JOBS) {
     const int j1 = std::min(nj, j0 + MAX_JOBS);
     rfim_status s;
-    if (pl.td.on && pl.fd.on) {
+    if (pl.td.on && pl.fd.on && ctx->order == 1) {
+      // interleaved: round r = TDSC iteration r on every row, then FDSC iteration r on every column
+      const int rounds = std::max(pl.td.it, pl.fd.it);
+      for (int r = 0; r < rounds; r++) {
+        if (r < pl.td.it) {
+          fill_params(ctx, pl, j0, j1, r == 0 ? 0 : 5, p, next_counters(ctx));
+          p.td.iterations = 1;
+          if ((s = launch_one(ctx, p, pl.max_T, st)) != RFIM_OK) return s;
+        }
+        if (r < pl.fd.it) {
+          fill_params(ctx, pl, j0, j1, 3, p, next_counters(ctx));
+          p.fd.iterations = 1;
+          if ((s = launch_one(ctx, p, pl.max_T, st)) != RFIM_OK) return s;
+        }
+      }
+    } else if (pl.td.on && pl.fd.on) {
       const bool fused = ctx->schedule != 2;
       if (fused) {
         fill_params(ctx, pl, j0, j1, 2, p, next_counters(ctx));
@@ -535,6 +562,9 @@ rfim_status rfim_set_option(rfim_ctx* ctx, const char* key, long long value) {
     if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 && value != 16 && value != 32)
       return fail(ctx, RFIM_ERR_ARG, "tile_samples must be 0, 1, 2, 4, 8, 16 or 32");
     ctx->tile_samples = (int)value;
+  } else if (k == "order") {
+    if (value != 0 && value != 1) return fail(ctx, RFIM_ERR_ARG, "order must be 0 (blocked) or 1 (interleaved)");
+    ctx->order = (int)value;
   } else if (k == "ctas_per_sm") {
     if (value < 0 || value > 32) return fail(ctx, RFIM_ERR_ARG, "ctas_per_sm must be in 0..32");
     ctx->ctas_per_sm = (int)value;
@@ -664,8 +694,8 @@ rfim_status rfim_clean_batch(rfim_ctx* ctx, const rfim_block* blocks, int n, con
   unsigned char* kp = key.data() + sizeof(Job) * pl.jobs.size();
   memcpy(kp, &pl.td, sizeof(CutNorm));
   memcpy(kp + 64, &pl.fd, sizeof(CutNorm));
-  int opts[8] = {pl.mask_kind, ctx->schedule, ctx->ctas_per_sm, ctx->fused_lag, ctx->withhold, (int)ctx->spin_limit_us,
-                 ctx->tile_samples, ctx->smem_target};
+  int opts[9] = {pl.mask_kind, ctx->schedule, ctx->ctas_per_sm, ctx->fused_lag, ctx->withhold, (int)ctx->spin_limit_us,
+                 ctx->tile_samples, ctx->smem_target, ctx->order};
   memcpy(kp + 128, opts, sizeof opts);
   auto it = ctx->graphs.find(key);
   if (it == ctx->graphs.end()) {
@@ -674,7 +704,8 @@ rfim_status rfim_clean_batch(rfim_ctx* ctx, const rfim_block* blocks, int n, con
       if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamCreate");
     }
     // A replayed graph reuses its counter blocks: give it its own, outside the ring.
-    const int launches = 2 * (((int)pl.jobs.size() + MAX_JOBS - 1) / MAX_JOBS);
+    const int rounds = ctx->order == 1 ? std::max(1, std::max(pl.td.it, pl.fd.it)) : 1;
+    const int launches = 2 * rounds * (((int)pl.jobs.size() + MAX_JOBS - 1) / MAX_JOBS);
     unsigned* gc = nullptr;
     cudaError_t e = cudaMalloc(&gc, sizeof(unsigned) * COUNTER_STRIDE * launches);
     if (e != cudaSuccess) return fail(ctx, RFIM_ERR_OOM, "graph counters: %s", cudaGetErrorString(e));

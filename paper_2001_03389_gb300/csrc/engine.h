@@ -65,6 +65,7 @@ struct Params {
   unsigned* counters;   // [0] queue head, [1 + j] TDSC rows done for job j
   unsigned* status;     // device status word (0 = ok, 5 = timeout)
   int dtype;            // 0 = uint8 (k_engine_u8), 1 = float32 (k_engine_f32)
+  int td_mask_or;       // TDSC rows OR their flags into the mask (interleaved rounds after the first)
 };
 
 __host__ __device__ inline int align16i(int x) { return (x + 15) & ~15; }

@@ -481,13 +481,14 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
       unsigned word = (unsigned)(bits >> head);
       const int valid = T - 32 * w;
       if (valid < 32) word &= (1u << valid) - 1u;
-      mrow[w] = word;
+      mrow[w] = P.td_mask_or ? (mrow[w] | word) : word;
     }
   } else if (P.mask_kind == MASK_BYTES && J.mask) {
     unsigned char* mb = static_cast<unsigned char*>(J.mask) + (size_t)row * T;
     for (int t = threadIdx.x; t < T; t += NT) {
       const int p = head + t;
-      mb[t] = (unsigned char)((fl4[p >> 2] >> (p & 3)) & 1u);
+      const unsigned char f = (unsigned char)((fl4[p >> 2] >> (p & 3)) & 1u);
+      mb[t] = P.td_mask_or ? (unsigned char)(mb[t] | f) : f;
     }
   }
   __syncthreads();

@@ -72,6 +72,10 @@ __device__ __forceinline__ void store16_partial(uint8_t* dst, const uint4& v, in
   for (int b = lo; b < hi; b++) dst[b] = (uint8_t)(word_of(v, b >> 2) >> (8 * (b & 3)));
 }
 
+__device__ __forceinline__ void or16_partial(uint8_t* dst, const uint4& v, int lo, int hi) {
+  for (int b = lo; b < hi; b++) dst[b] |= (uint8_t)(word_of(v, b >> 2) >> (8 * (b & 3)));
+}
+
 // n (<= 16) bytes of a row starting at global address a, bytes past n read as
 // 0.  Reads only inside [lo, hi).
 __device__ __forceinline__ uint4 load_seg16(const uint8_t* a, int n, const uint8_t* lo, const uint8_t* hi) {
@@ -605,10 +609,17 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
         const uint4 fbytes = make_uint4(bytes_from_bits4(fb), bytes_from_bits4(fb >> 4), bytes_from_bits4(fb >> 8),
                                         bytes_from_bits4(fb >> 12));
         if (mb_align && !edge) {
-          *reinterpret_cast<uint4*>(mbb + 16 * k) = fbytes;
+          uint4* mp = reinterpret_cast<uint4*>(mbb + 16 * k);
+          if (P.td_mask_or) {
+            const uint4 o = *mp;
+            *mp = make_uint4(o.x | fbytes.x, o.y | fbytes.y, o.z | fbytes.z, o.w | fbytes.w);
+          } else {
+            *mp = fbytes;
+          }
         } else {
           const int clo = k == 0 ? g.head : 0, chi = k == g.nch - 1 ? g.tail : 16;
-          store16_partial(mbb + 16 * k, fbytes, clo, chi);
+          if (P.td_mask_or) or16_partial(mbb + 16 * k, fbytes, clo, chi);
+          else store16_partial(mbb + 16 * k, fbytes, clo, chi);
         }
       }
     return fb;
@@ -635,7 +646,7 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
       uint32_t word = (uint32_t)(bits >> g.head);
       const int valid = T - 32 * wi;
       if (valid < 32) word &= (1u << valid) - 1u;
-      mrow[wi] = word;
+      mrow[wi] = P.td_mask_or ? (mrow[wi] | word) : word;
     }
   }
 }

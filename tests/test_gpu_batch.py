@@ -113,3 +113,30 @@ def test_batch_rejects_mixed_dtypes(ctx):
     blks = [rfim.Context.block(a, torch.empty_like(a)), rfim.Context.block(b, torch.empty_like(b))]
     with pytest.raises(rfim.RfimError):
         ctx.clean_batch(blks, rfim.make_cut(3.0), None)
+
+
+def test_batch_graph_interleaved(ctx, oracle):
+    # graph capture of interleaved rounds (two launches per round per beam group)
+    import torch
+
+    from gpu_util import unpack_bits
+    from paper_2001_03389_gb300 import rfim, synth
+
+    shapes = [(96, 700), (130, 333), (64, 2048)]
+    beams = synth.torch_ragged_batch(shapes, seed=19, device="cuda:0")
+    td = dict(k=2.5, iterations=3, replace="median")
+    fd = dict(k=2.5, iterations=2, replace="mean", bin=32)
+    try:
+        ctx.set_option("order", 1)
+        for _ in range(2):  # capture, then replay
+            o, m, b = _blocks(rfim, beams)
+            ctx.clean_batch(b, rfim.make_cut(**td), rfim.make_cut(**fd), flags=rfim.BATCH_GRAPH)
+            torch.cuda.synchronize()
+            for i, x in enumerate(beams):
+                C, T = shapes[i]
+                want, wf = oracle.clean(x.cpu().numpy()[None], "bct", tdsc=td, fdsc=fd, order="interleaved")
+                assert np.array_equal(o[i].cpu().numpy()[None], want)
+                assert np.array_equal(unpack_bits(m[i].cpu().numpy(), C, T)[None], wf > 0)
+        assert ctx.device_status() == rfim.OK
+    finally:
+        ctx.set_option("order", 0)

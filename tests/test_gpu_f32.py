@@ -219,3 +219,25 @@ def test_f32_btc_layout(oracle, ctx, C, T):
             assert np.array_equal(got[keep].view(np.uint32), x[keep].view(np.uint32))
             both = wf > 0
             assert np.all(np.abs(got[both].astype(np.float64) - want[both]) <= REL * np.abs(want[both]) + 1e-30)
+
+
+def test_f32_interleaved_order(oracle, ctx):
+    rng = np.random.default_rng(17)
+    x = chi2_block(rng, 2, 96, 403)
+    td = dict(k=2.5, iterations=3, replace="mean")
+    fd = dict(k=2.5, iterations=2, replace="median", bin=32)
+    want, wf = oracle.clean(x, "bct", tdsc=td, fdsc=fd, order="interleaved")
+    try:
+        ctx.set_option("order", 1)
+        for mf in ("bits", "bytes"):
+            got, gf = run_gpu(ctx, x, tdsc=td, fdsc=fd, mask_fmt=mf)
+            gflag = gf if mf == "bits" else gf > 0
+            if np.array_equal(gflag, wf > 0):
+                keep = ~(wf > 0)
+                assert np.array_equal(got[keep].view(np.uint32), x[keep].view(np.uint32))
+                both = wf > 0
+                assert np.all(np.abs(got[both].astype(np.float64) - want[both]) <= REL * np.abs(want[both]) + 1e-30)
+            else:
+                pytest.fail("interleaved float32 masks differ from the oracle")
+    finally:
+        ctx.set_option("order", 0)

@@ -273,3 +273,28 @@ def test_btc_batch(oracle, ctx):
         assert np.array_equal(o.cpu().numpy(), want)
         # BTC bit mask: rows are time samples, bits along channels
         assert np.array_equal(unpack_bits(m.cpu().numpy(), T, C)[None], wf > 0)
+
+
+def test_interleaved_order(oracle, ctx):
+    # round i: TDSC iteration i on every row, then FDSC iteration i on every column
+    from paper_2001_03389_gb300 import rfim
+
+    rng = np.random.default_rng(31)
+    x = noise_u8(rng, (3, 96, 777))
+    x[:, 5, :] = np.clip(x[:, 5, :].astype(int) + 60, 0, 255)
+    cases = [(dict(k=2.5, iterations=3, replace="median"), dict(k=2.5, iterations=2, replace="median", bin=32)),
+             (dict(k=2.0, iterations=2, replace="mean"), dict(k=2.0, iterations=3, replace="mean", bin=16))]
+    try:
+        ctx.set_option("order", 1)
+        for td, fd in cases:
+            want, wf = oracle.clean(x, "bct", tdsc=td, fdsc=fd, order="interleaved")
+            for mf in ("bits", "bytes"):
+                got, gf = run_gpu(ctx, x, tdsc=td, fdsc=fd, mask_fmt=mf)
+                assert np.array_equal(got, want)
+                assert np.array_equal(gf, wf > 0) if mf == "bits" else np.array_equal(gf, wf)
+            got, gf = run_gpu(ctx, x, tdsc=td, fdsc=fd, in_place=True)
+            assert np.array_equal(got, want) and np.array_equal(gf, wf > 0)
+        with pytest.raises(rfim.RfimError):
+            ctx.set_option("order", 2)
+    finally:
+        ctx.set_option("order", 0)

@@ -463,3 +463,42 @@ def test_f32_margin_diagnostic(oracle):
     y = np.full((1, 4, 3), 2.5, np.float32)
     _, fl2, mg2 = oracle.clean_f32_margin(y, "bct", fdsc=dict(k=2.0, iterations=2, bin=2))
     assert np.all(np.isinf(mg2)) and not fl2.any()
+
+
+def test_interleaved_order(oracle):
+    # Interleaved order (one TDSC iteration, then one FDSC iteration, per round)
+    # equals blocked order when each method runs once, equals the explicit
+    # sequence of single-iteration calls, and differs from blocked order on
+    # data where an FDSC replacement changes a later TDSC decision.
+    rng = np.random.default_rng(8)
+    td1 = dict(k=2.0, iterations=1, replace="mean")
+    fd1 = dict(k=2.0, iterations=1, replace="mean", bin=4)
+    x = noise_u8_local(rng, (2, 12, 40))
+    a = oracle.clean(x, "bct", tdsc=td1, fdsc=fd1)
+    b = oracle.clean(x, "bct", tdsc=td1, fdsc=fd1, order="interleaved")
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    td2, fd2 = dict(td1, iterations=2), dict(fd1, iterations=2)
+    y = x.copy()
+    fl = np.zeros_like(x)
+    for _ in range(2):
+        y, f = oracle.clean(y, "bct", tdsc=td1, fdsc=fd1)
+        fl |= f
+    got, gf = oracle.clean(x, "bct", tdsc=td2, fdsc=fd2, order="interleaved")
+    assert np.array_equal(got, y) and np.array_equal(gf, fl)
+    differs = False
+    for s in range(20):
+        z = noise_u8_local(np.random.default_rng(100 + s), (1, 8, 24))
+        if not np.array_equal(oracle.clean(z, "bct", tdsc=td2, fdsc=fd2)[0],
+                              oracle.clean(z, "bct", tdsc=td2, fdsc=fd2, order="interleaved")[0]):
+            differs = True
+            break
+    assert differs
+    with pytest.raises(ValueError):
+        oracle.clean(x, "bct", tdsc=td1, order="sideways")
+
+
+def noise_u8_local(rng, shape):
+    x = np.clip(np.rint(rng.normal(128, 16, shape)), 0, 255).astype(np.uint8)
+    flat = x.reshape(-1)
+    flat[rng.integers(0, flat.size, max(1, flat.size // 30))] = 250
+    return x
