@@ -707,8 +707,36 @@ __device__ __forceinline__ int toff(int r, int c, int pitch) {
 // 16 channels x 4 samples.  16 row words (lanes along time, so 8 lanes read 32
 // contiguous bytes of a row), four 4x4 byte transposes, and one 16-byte shared
 // store per sample row (the 16 channels are one swizzle unit).
-template <int UPR>  // units per round: their 16 x UPR row words are in flight together
-__device__ __forceinline__ void fd_load_full(uint8_t* tile, const uint8_t* src, int C, int T, int t0, int pitch) {
+// 4 bytes of a row at a (any alignment), reading only inside [lo, hi)
+__device__ __forceinline__ uint32_t ld_row4(const uint8_t* a, const uint8_t* lo, const uint8_t* hi) {
+  const int off = (int)((uintptr_t)a & 3);
+  if (off == 0) return *reinterpret_cast<const uint32_t*>(a);
+  const uint32_t* al = reinterpret_cast<const uint32_t*>(a - off);
+  if ((const uint8_t*)(al + 2) <= hi) return __funnelshift_r(al[0], al[1], 8 * off);
+  uint32_t w = 0;
+  for (int b = 0; b < 4; b++)
+    if (a + b < hi) w |= (uint32_t)a[b] << (8 * b);
+  (void)lo;
+  return w;
+}
+
+// 4 bytes of a row at a (any alignment)
+__device__ __forceinline__ void st_row4(uint8_t* a, uint32_t w) {
+  const int off = (int)((uintptr_t)a & 3);
+  if (off == 0) {
+    *reinterpret_cast<uint32_t*>(a) = w;
+  } else if (off == 2) {
+    reinterpret_cast<uint16_t*>(a)[0] = (uint16_t)w;
+    reinterpret_cast<uint16_t*>(a)[1] = (uint16_t)(w >> 16);
+  } else {
+    for (int b = 0; b < 4; b++) a[b] = (uint8_t)(w >> (8 * b));
+  }
+}
+
+template <int UPR, bool ALIGNED>  // units per round (their 16 x UPR row words are in flight together);
+                                  // ALIGNED: rows start on 4-byte boundaries
+__device__ __forceinline__ void fd_load_full(uint8_t* tile, const uint8_t* src, const uint8_t* src_end, int C, int T,
+                                             int t0, int pitch) {
   const int nunits = (C >> 4) * 8;
   for (int u0 = threadIdx.x; u0 < nunits; u0 += UPR * NT) {
     uint32_t w[UPR][16];
@@ -717,8 +745,13 @@ __device__ __forceinline__ void fd_load_full(uint8_t* tile, const uint8_t* src, 
       const int u = u0 + k * NT;
       if (u < nunits) {
         const uint8_t* a = src + (size_t)((u >> 3) * 16) * T + t0 + 4 * (u & 7);
+        if (ALIGNED) {
 #pragma unroll
-        for (int i = 0; i < 16; i++) w[k][i] = *reinterpret_cast<const uint32_t*>(a + (size_t)i * T);
+          for (int i = 0; i < 16; i++) w[k][i] = *reinterpret_cast<const uint32_t*>(a + (size_t)i * T);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 16; i++) w[k][i] = ld_row4(a + (size_t)i * T, src, src_end);
+        }
       }
     }
 #pragma unroll
@@ -739,6 +772,7 @@ __device__ __forceinline__ void fd_load_full(uint8_t* tile, const uint8_t* src, 
   }
 }
 
+template <bool ALIGNED>
 __device__ __forceinline__ void fd_store_full(const uint8_t* tile, uint8_t* dst, int C, int T, int t0, int pitch) {
   const int nunits = (C >> 4) * 8;
   for (int u = threadIdx.x; u < nunits; u += NT) {
@@ -756,8 +790,13 @@ __device__ __forceinline__ void fd_store_full(const uint8_t* tile, uint8_t* dst,
 #pragma unroll
     for (int g = 0; g < 4; g++) transpose4x4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3]);
     uint8_t* a = dst + (size_t)(cg * 16) * T + t0 + 4 * tq;
+    if (ALIGNED) {
 #pragma unroll
-    for (int i = 0; i < 16; i++) *reinterpret_cast<uint32_t*>(a + (size_t)i * T) = w[i];
+      for (int i = 0; i < 16; i++) *reinterpret_cast<uint32_t*>(a + (size_t)i * T) = w[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < 16; i++) st_row4(a + (size_t)i * T, w[i]);
+    }
   }
 }
 
@@ -927,7 +966,9 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
     // ---- load: units of 4 channels x 4 samples, lanes along time, transposed into [t][c];
     //      four units per thread are in flight at a time
     if (full && rows4) {
-      fd_load_full<1>(L.tile, src, C, T, t0, pitch);
+      fd_load_full<1, true>(L.tile, src, bhi, C, T, t0, pitch);
+    } else if (full) {
+      fd_load_full<1, false>(L.tile, src, bhi, C, T, t0, pitch);
     } else {
       const int nunits = nq * nt4;
       for (int ub = threadIdx.x; ub < nunits; ub += 4 * NT) {
@@ -1217,7 +1258,8 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
     __syncthreads();
 
     // ---- store: transpose back to [c][t], lanes along time
-    if (full && out4) fd_store_full(L.tile, dst, C, T, t0, pitch);
+    if (full && out4) fd_store_full<true>(L.tile, dst, C, T, t0, pitch);
+    else if (full) fd_store_full<false>(L.tile, dst, C, T, t0, pitch);
     else for (int u = threadIdx.x; u < nq * nt4; u += NT) {
       const int tq = u % nt4, cq = u / nt4;
       const int c = 4 * cq, tt = 4 * tq;
@@ -1300,6 +1342,16 @@ __device__ bool wait_rows(const Params& P, int job, unsigned need, int* flag) {
   return ok;
 }
 
+__device__ __forceinline__ int seg_of(const Params& P, int item) {
+  int lo = 0, hi = P.n_segs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (P.segs[mid].start <= item) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 // MINB = CTAs per SM the register allocation targets (the TDSC row stage is
 // 102 KB, so two CTAs share an SM).
 template <int MINB>
@@ -1313,13 +1365,7 @@ __global__ void __launch_bounds__(NT, MINB) k_engine_u8(const __grid_constant__ 
     const int item = s_item;
     __syncthreads();
     if (item >= P.n_items) return;
-    int lo = 0, hi = P.n_segs - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (P.segs[mid].start <= item) lo = mid;
-      else hi = mid - 1;
-    }
-    const Seg sg = P.segs[lo];
+    const Seg sg = P.segs[seg_of(P, item)];
     const int idx = item - sg.start;
     const Job& J = P.jobs[sg.job];
     if (sg.kind == 0) {
