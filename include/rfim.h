@@ -151,6 +151,9 @@ rfim_status rfim_destroy(rfim_ctx* ctx);
  *                     (uint8 tiles use at least 8, float32 tiles at most 8);
  *   "smem_target"     shared memory an FDSC tile may use, bytes (sets the automatic width);
  *   "fused_lag"       beams of TDSC rows queued ahead of a beam's FDSC items (0..8);
+ *   "stage_group_bytes"  rfim_clean_host: bytes of beams copied and cleaned per
+ *                     group (default 32 MB; at least one beam per group);
+ *   "stage_streams"   rfim_clean_host: CUDA streams the groups rotate over (1..4, default 3);
  *   "order"           order of the methods in rfim_clean and rfim_clean_batch:
  *                     0 = blocked (all TDSC iterations on every row, then all
  *                     FDSC iterations on every column; default), 1 = interleaved
@@ -197,8 +200,9 @@ rfim_status rfim_clean_batch(rfim_ctx* ctx, const rfim_block* blocks, int n, con
 /*
  * rfim_clean on HOST buffers (pinned memory recommended): the context copies
  * beams to device staging buffers, cleans them and copies results back,
- * overlapping the copies of one beam group with the cleaning of another on two
- * streams.  Synchronous: returns when out and mask are written.
+ * overlapping the copies of one beam group with the cleaning of another on a
+ * ring of streams ("stage_group_bytes", "stage_streams").  Synchronous:
+ * returns when out and mask are written.
  */
 rfim_status rfim_clean_host(rfim_ctx* ctx, const rfim_block* host_blk, const rfim_cut* tdsc,
                             const rfim_cut* fdsc);

@@ -52,6 +52,8 @@ struct rfim_ctx {
   int smem_target = 113 * 1024;
   int fused_lag = 1;
   int order = 0;  // 0 = blocked (all TDSC iterations, then FDSC), 1 = interleaved rounds
+  long long stage_group_bytes = 32ll << 20;  // rfim_clean_host: bytes per staged group
+  int stage_streams = 3;                     // rfim_clean_host: streams in the staging ring
   // graphs for rfim_clean_batch (each with its own counter blocks)
   std::map<std::vector<unsigned char>, std::pair<cudaGraphExec_t, unsigned*>> graphs;
   unsigned* capture_counters = nullptr;  // while capturing: counter blocks of the graph
@@ -562,6 +564,12 @@ rfim_status rfim_set_option(rfim_ctx* ctx, const char* key, long long value) {
     if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 && value != 16 && value != 32)
       return fail(ctx, RFIM_ERR_ARG, "tile_samples must be 0, 1, 2, 4, 8, 16 or 32");
     ctx->tile_samples = (int)value;
+  } else if (k == "stage_group_bytes") {
+    if (value < (1ll << 20) || value > (1ll << 34)) return fail(ctx, RFIM_ERR_ARG, "stage_group_bytes must be in 1 MB..16 GB");
+    ctx->stage_group_bytes = value;
+  } else if (k == "stage_streams") {
+    if (value < 1 || value > 4) return fail(ctx, RFIM_ERR_ARG, "stage_streams must be 1..4");
+    ctx->stage_streams = (int)value;
   } else if (k == "order") {
     if (value != 0 && value != 1) return fail(ctx, RFIM_ERR_ARG, "order must be 0 (blocked) or 1 (interleaved)");
     ctx->order = (int)value;
@@ -812,6 +820,10 @@ int ctx_device(rfim_ctx* ctx) { return ctx->device; }
 size_t ctx_hbm_budget(rfim_ctx* ctx) { return ctx->hbm_budget; }
 void ctx_set_error(rfim_ctx* ctx, const char* msg) { ctx->last_error = msg; }
 StreamService*& ctx_stream_service(rfim_ctx* ctx) { return ctx->stream; }
+void ctx_stage_options(rfim_ctx* ctx, size_t& group_bytes, int& streams) {
+  group_bytes = (size_t)ctx->stage_group_bytes;
+  streams = ctx->stage_streams;
+}
 void ctx_get_tunables(rfim_ctx* ctx, Tunables& t) {
   t.schedule = ctx->schedule;
   t.ctas_per_sm = ctx->ctas_per_sm;

@@ -28,25 +28,25 @@ size_t mask_beam_bytes(const rfim_block* b) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// Host staging: beams are cleaned in groups on two CUDA streams, so that the
-// host-to-device copy of one group, the cleaning of another and the copy back
-// of a third overlap.  Device buffers are owned by the context and grow on
+// Host staging: beams are cleaned in groups on up to four CUDA streams (a
+// ring), so that the host-to-device copy of one group, the cleaning of another
+// and the copy back of a third overlap.  Device buffers are owned by the context and grow on
 // demand; each group is cleaned in place in its staging buffer.
 // ---------------------------------------------------------------------------
+constexpr int STAGE_MAX_STREAMS = 4;
+
 struct HostStager {
   int dev = 0;
-  cudaStream_t st[2] = {nullptr, nullptr};
-  void* dbuf[2] = {nullptr, nullptr};
-  void* dmask[2] = {nullptr, nullptr};
+  cudaStream_t st[STAGE_MAX_STREAMS] = {};
+  void* dbuf[STAGE_MAX_STREAMS] = {};
+  void* dmask[STAGE_MAX_STREAMS] = {};
   size_t cap_buf = 0, cap_mask = 0;
 };
-
-static constexpr size_t GROUP_BYTES = 128ull << 20;
 
 HostStager* stager_create(rfim_ctx* ctx) {
   HostStager* s = new HostStager();
   s->dev = ctx_device(ctx);
-  for (int i = 0; i < 2; i++) {
+  for (int i = 0; i < STAGE_MAX_STREAMS; i++) {
     if (cudaStreamCreateWithFlags(&s->st[i], cudaStreamNonBlocking) != cudaSuccess) {
       stager_destroy(s);
       return nullptr;
@@ -57,7 +57,7 @@ HostStager* stager_create(rfim_ctx* ctx) {
 
 void stager_destroy(HostStager* s) {
   if (!s) return;
-  for (int i = 0; i < 2; i++) {
+  for (int i = 0; i < STAGE_MAX_STREAMS; i++) {
     if (s->st[i]) cudaStreamSynchronize(s->st[i]);
     cudaFree(s->dbuf[i]);
     cudaFree(s->dmask[i]);
@@ -74,15 +74,17 @@ rfim_status stager_run(HostStager* s, rfim_ctx* ctx, const rfim_block* hb, const
   }
   const size_t beam = (size_t)hb->channels * hb->samples * esize(hb->dtype);
   const size_t mbeam = mask_beam_bytes(hb);
-  const int group = (int)std::max<size_t>(1, std::min<size_t>((size_t)hb->beams, GROUP_BYTES / std::max<size_t>(beam, 1)));
+  size_t group_bytes;
+  int ns;
+  ctx_stage_options(ctx, group_bytes, ns);
+  ns = std::max(1, std::min(ns, STAGE_MAX_STREAMS));
+  const int group = (int)std::max<size_t>(1, std::min<size_t>((size_t)hb->beams, group_bytes / std::max<size_t>(beam, 1)));
   const size_t need = beam * group, needm = mbeam * group;
-  for (int i = 0; i < 2; i++) {
-    if (s->cap_buf < need) {
-      cudaStreamSynchronize(s->st[i]);
-    }
+  for (int i = 0; i < STAGE_MAX_STREAMS; i++) {
+    if (s->cap_buf < need || (needm && s->cap_mask < needm)) cudaStreamSynchronize(s->st[i]);
   }
   if (s->cap_buf < need) {
-    for (int i = 0; i < 2; i++) {
+    for (int i = 0; i < STAGE_MAX_STREAMS; i++) {
       cudaFree(s->dbuf[i]);
       s->dbuf[i] = nullptr;
       if (cudaMalloc(&s->dbuf[i], need) != cudaSuccess) {
@@ -94,7 +96,7 @@ rfim_status stager_run(HostStager* s, rfim_ctx* ctx, const rfim_block* hb, const
     s->cap_buf = need;
   }
   if (needm && s->cap_mask < needm) {
-    for (int i = 0; i < 2; i++) {
+    for (int i = 0; i < STAGE_MAX_STREAMS; i++) {
       cudaFree(s->dmask[i]);
       s->dmask[i] = nullptr;
       if (cudaMalloc(&s->dmask[i], needm) != cudaSuccess) {
@@ -111,7 +113,7 @@ rfim_status stager_run(HostStager* s, rfim_ctx* ctx, const rfim_block* hb, const
   rfim_status st = RFIM_OK;
   int gi = 0;
   for (int b0 = 0; b0 < hb->beams; b0 += group, gi++) {
-    const int i = gi & 1;
+    const int i = gi % ns;
     const int nb = std::min(group, hb->beams - b0);
     cudaStream_t str = s->st[i];
     cudaError_t e = cudaMemcpyAsync(s->dbuf[i], hin + (size_t)b0 * beam, (size_t)nb * beam, cudaMemcpyHostToDevice, str);
@@ -137,7 +139,7 @@ rfim_status stager_run(HostStager* s, rfim_ctx* ctx, const rfim_block* hb, const
       break;
     }
   }
-  for (int i = 0; i < 2; i++) {
+  for (int i = 0; i < ns; i++) {
     cudaError_t e = cudaStreamSynchronize(s->st[i]);
     if (e != cudaSuccess && st == RFIM_OK) {
       ctx_set_error(ctx, cudaGetErrorString(e));

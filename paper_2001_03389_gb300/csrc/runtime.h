@@ -29,6 +29,8 @@ size_t ctx_hbm_budget(rfim_ctx* ctx);
 void ctx_set_error(rfim_ctx* ctx, const char* msg);
 StreamService*& ctx_stream_service(rfim_ctx* ctx);
 void ctx_get_tunables(rfim_ctx* ctx, Tunables& t);
+// host staging: bytes per group and streams in the ring
+void ctx_stage_options(rfim_ctx* ctx, size_t& group_bytes, int& streams);
 // validation of one block and its cuts as a launch would do it (no launch)
 rfim_status ctx_validate(rfim_ctx* ctx, const rfim_block* b, const rfim_cut* tdsc, const rfim_cut* fdsc);
 void ctx_set_tunables(rfim_ctx* ctx, const Tunables& t);
