@@ -267,8 +267,9 @@ Job make_job(const rfim_block* b, int j, const CutNorm& fd, int tile_samples, in
   J.td_items = J.td_mode == 0 ? (C + TD_ROWS_PER_ITEM - 1) / TD_ROWS_PER_ITEM : C;
   if (b->dtype == RFIM_F32) {
     // float32: one CTA per TDSC row; FDSC sub-slab of 8, 4, 2 or 1 samples
-    J.td_mode = 1;
-    J.td_items = C;
+    // TDSC: two rows per item (a half CTA each) when both stages fit, else one
+    J.td_mode = 2 * td32_smem_bytes(T) <= MAX_SMEM_PER_CTA ? 0 : 1;
+    J.td_items = J.td_mode == 0 ? (C + 1) / 2 : C;
     J.ws = 1;
     for (int ws : {8, 4, 2})
       if ((tile_samples == 0 || ws <= tile_samples) && fd32_smem_bytes(ws, C, J.nb) <= smem_target) {

@@ -40,7 +40,8 @@ struct Job {
   int pitch;        // bytes per tile row (>= C * esize, pitch/4 = 1 mod 32)
   int fd_items;     // number of FDSC work items (ceil(T / 32))
   int rows;         // TDSC rows (C)
-  int td_mode;      // 0: one warp per row, 8 rows per item; 1: one row per item, whole CTA
+  int td_mode;      // uint8: 0 = one warp per row, 8 rows per item; 1 = one row per item, whole CTA.
+                    // float32: 0 = two rows per item, a half CTA each; 1 = one row per item
   int td_items;     // number of TDSC work items
 };
 

@@ -223,6 +223,65 @@ __device__ __forceinline__ int block_isum(int v, Red32* r) {
 }
 
 // ---------------------------------------------------------------------------
+// Thread groups of GN threads (a half CTA, or the whole CTA) that clean one
+// row each; h = group index, synchronised by named barrier 1 + h.
+// ---------------------------------------------------------------------------
+template <int GN>
+__device__ __forceinline__ void gsync(int h) {
+  asm volatile("bar.sync %0, %1;" ::"r"(h + 1), "r"(GN) : "memory");
+}
+
+template <int GN>
+__device__ __forceinline__ void grp_ff2(FF& a, FF& b, Red32* r, int t, int h) {
+  const int lane = t & 31, warp = t >> 5;
+  a = warp_ff(a);
+  b = warp_ff(b);
+  gsync<GN>(h);
+  if (lane == 0) {
+    r->f[4 * warp + 0] = a.hi;
+    r->f[4 * warp + 1] = a.lo;
+    r->f[4 * warp + 2] = b.hi;
+    r->f[4 * warp + 3] = b.lo;
+  }
+  gsync<GN>(h);
+  FF sa{0.f, 0.f}, sb{0.f, 0.f};
+#pragma unroll
+  for (int w = 0; w < GN / 32; w++) {
+    sa = ff_add(sa, FF{r->f[4 * w + 0], r->f[4 * w + 1]});
+    sb = ff_add(sb, FF{r->f[4 * w + 2], r->f[4 * w + 3]});
+  }
+  a = sa;
+  b = sb;
+}
+
+template <int GN>
+__device__ __forceinline__ double grp_dsum(double v, Red32* r, int t, int h) {
+  const int lane = t & 31, warp = t >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  gsync<GN>(h);
+  if (lane == 0) r->d[warp] = v;
+  gsync<GN>(h);
+  double s = 0.0;
+#pragma unroll
+  for (int w = 0; w < GN / 32; w++) s += r->d[w];
+  return s;
+}
+
+template <int GN>
+__device__ __forceinline__ int grp_isum(int v, Red32* r, int t, int h) {
+  const int lane = t & 31, warp = t >> 5;
+  v = __reduce_add_sync(0xffffffffu, v);
+  gsync<GN>(h);
+  if (lane == 0) r->i[warp] = v;
+  gsync<GN>(h);
+  int s = 0;
+#pragma unroll
+  for (int w = 0; w < GN / 32; w++) s += r->i[w];
+  return s;
+}
+
+// ---------------------------------------------------------------------------
 // TDSC on one float32 row (the whole CTA)
 // ---------------------------------------------------------------------------
 // Shared memory: the row's 16-byte chunk grid (element i of the row at
@@ -248,26 +307,29 @@ __device__ __forceinline__ void f4_set(float4& v, int i, float x) {
 
 // Lower median (rank floor((n-1)/2)) of the valid elements of the staged row:
 // bitwise search over the order keys, one bit per CTA-wide count.
-__device__ float row_median_f32(const float4* st, int nch, int head, int tail, int n, Red32* red) {
+template <int GN>
+__device__ float row_median_f32(const float4* st, int nch, int head, int tail, int n, Red32* red, int t, int h) {
   const int rank = (n - 1) >> 1;
   unsigned prefix = 0;
   for (int b = 31; b >= 0; b--) {
     const unsigned test = prefix | (1u << b);
     int cnt = 0;
-    for (int k = threadIdx.x; k < nch; k += NT) {
+    for (int k = t; k < nch; k += GN) {
       const float4 v = st[k];
       const int lo = k == 0 ? head : 0, hi = k == nch - 1 ? tail : 4;
 #pragma unroll
       for (int i = 0; i < 4; i++)
         if (i >= lo && i < hi) cnt += fkey(f4_get(v, i)) < test;
     }
-    cnt = block_isum(cnt, red);
+    cnt = grp_isum<GN>(cnt, red, t, h);
     if (cnt <= rank) prefix = test;
   }
   return key_f(prefix);
 }
 
-__device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned char* smem, Red32* red) {
+// GN threads clean the row: t = thread in the group, h = group (its barrier is 1 + h)
+template <int GN>
+__device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned char* smem, Red32* red, int t, int h) {
   const CutDev& cut = P.td;
   const int T = J.T;
   const float* beam_in = static_cast<const float*>(J.in);
@@ -284,10 +346,11 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
   float4* st = reinterpret_cast<float4*>(smem);
   unsigned char* fl4 = smem + 16 * nch;
   float* lst = reinterpret_cast<float*>(smem + 16 * nch + align16i(nch));
-  __shared__ int s_nlist;
+  __shared__ int s_nlist_g[2];
+  int& s_nlist = s_nlist_g[h];
 
   // ---- stage the row (edge chunks through guarded loads, padding zeroed)
-  for (int k = threadIdx.x; k < nch; k += NT) {
+  for (int k = t; k < nch; k += GN) {
     const float* a = cb + 4 * k;
     if (k > 0 && k < nch - 1) {
       const unsigned sdst = (unsigned)__cvta_generic_to_shared(st + k);
@@ -303,11 +366,11 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
     fl4[k] = 0;
   }
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
-  __syncthreads();
+  gsync<GN>(h);
 
   // ---- sums of the staged row (padding zeros add nothing)
   FF S{0.f, 0.f}, Q{0.f, 0.f};
-  for (int k = threadIdx.x; k < nch; k += NT) {
+  for (int k = t; k < nch; k += GN) {
     const float4 v = st[k];
     ff_acc(S, v.x);
     ff_acc_sq(Q, v.x);
@@ -318,10 +381,10 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
     ff_acc(S, v.w);
     ff_acc_sq(Q, v.w);
   }
-  block_ff2(S, Q, red);
+  grp_ff2<GN>(S, Q, red, t, h);
   // running sums of the current values (used by thread 0 only)
   double Sd = 0.0, Qd = 0.0;
-  if (threadIdx.x == 0) {
+  if (t == 0) {
     Sd = ff_d(S);
     Qd = ff_d(Q);
   }
@@ -331,31 +394,31 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
     float mu_f, mu_lo, lo_f, hi_f;
     int prec;
   };
-  __shared__ RowStat rs_s;
-  RowStat* rs_ = &rs_s;
+  __shared__ RowStat rs_g[2];
+  RowStat* rs_ = &rs_g[h];
   const double Tn = (double)T, rT = 1.0 / (double)T;
   const int I = cut.iterations;
 
   for (int it = 0; it < I; it++) {
     // statistics of the current values, finished in double by one thread
-    if (threadIdx.x == 0) {
+    if (t == 0) {
       const double mu = Sd * rT;
       const double var = Qd * rT - mu * mu;
       rs_->prec = !(var >= 1e-3 * (Qd * rT));
       rs_->var = var;
     }
-    __syncthreads();
+    gsync<GN>(h);
     if (rs_->prec) {
       // cancellation (or a constant row): FP64 two-pass over the current values
       double s = 0.0;
-      for (int k = threadIdx.x; k < nch; k += NT) {
+      for (int k = t; k < nch; k += GN) {
         const float4 v = st[k];
         s += ((double)v.x + (double)v.y) + ((double)v.z + (double)v.w);  // padding is 0
       }
-      s = block_dsum(s, red);
+      s = grp_dsum<GN>(s, red, t, h);
       const double m2 = s * rT;
       double ss = 0.0;
-      for (int k = threadIdx.x; k < nch; k += NT) {
+      for (int k = t; k < nch; k += GN) {
         const float4 v = st[k];
         const int lo = k == 0 ? head : 0, hi = k == nch - 1 ? tail : 4;
 #pragma unroll
@@ -365,13 +428,13 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
             ss += d * d;
           }
       }
-      ss = block_dsum(ss, red);
-      if (threadIdx.x == 0) {
+      ss = grp_dsum<GN>(ss, red, t, h);
+      if (t == 0) {
         rs_->var = ss * rT;
         Sd = s;  // the two-pass mean
       }
     }
-    if (threadIdx.x == 0) {
+    if (t == 0) {
       const double mu = Sd * rT;
       const double var = rs_->var;
       const double thr = cut.k * sqrt_fast(var);
@@ -384,19 +447,19 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
       rs_->hi_f = __double2float_ru((thr + dm) * (1.0 + 0x1p-20));
       rs_->lo_f = __double2float_rd((thr - dm) * (1.0 - 0x1p-20));
     }
-    __syncthreads();
+    gsync<GN>(h);
     Cut32 c;
     c.mu_f = rs_->mu_f;
     c.mu_lo = rs_->mu_lo;
     c.lo_f = rs_->lo_f;
     c.hi_f = rs_->hi_f;
     c.thr = &rs_->mu_thr[1];
-    const float r = cut.replace == REP_MEDIAN ? row_median_f32(st, nch, head, tail, T, red) : c.mu_f;
+    const float r = cut.replace == REP_MEDIAN ? row_median_f32<GN>(st, nch, head, tail, T, red, t, h) : c.mu_f;
 
     // decide and replace; the replaced values go to a list for the statistics update
-    if (threadIdx.x == 0) s_nlist = 0;
-    __syncthreads();
-    for (int k = threadIdx.x; k < nch; k += NT) {
+    if (t == 0) s_nlist = 0;
+    gsync<GN>(h);
+    for (int k = t; k < nch; k += GN) {
       float4 v = st[k];
       const int lo = k == 0 ? head : 0, hi = k == nch - 1 ? tail : 4;
       unsigned nib = 0;
@@ -416,24 +479,24 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
       }
     }
     if (it == I - 1) break;
-    __syncthreads();
+    gsync<GN>(h);
     // statistics of the next iteration: S' = S - sum(replaced) + nf r (same for Q)
     const int nflag = s_nlist;
     FF rs{0.f, 0.f}, rq{0.f, 0.f};
     if (nflag <= TD32_LIST) {
-      for (int i = threadIdx.x; i < nflag; i += NT) {
+      for (int i = t; i < nflag; i += GN) {
         ff_acc(rs, lst[i]);
         ff_acc_sq(rq, lst[i]);
       }
-      block_ff2(rs, rq, red);
-      if (threadIdx.x == 0) {
+      grp_ff2<GN>(rs, rq, red, t, h);
+      if (t == 0) {
         const double rd = (double)r;
         Sd = Sd - ff_d(rs) + (double)nflag * rd;
         Qd = Qd - ff_d(rq) + (double)nflag * rd * rd;
       }
     } else {
       // many replacements: sum the current row again
-      for (int k = threadIdx.x; k < nch; k += NT) {
+      for (int k = t; k < nch; k += GN) {
         const float4 v = st[k];
         ff_acc(rs, v.x);
         ff_acc_sq(rq, v.x);
@@ -444,19 +507,19 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
         ff_acc(rs, v.w);
         ff_acc_sq(rq, v.w);
       }
-      block_ff2(rs, rq, red);
-      if (threadIdx.x == 0) {
+      grp_ff2<GN>(rs, rq, red, t, h);
+      if (t == 0) {
         Sd = ff_d(rs);
         Qd = ff_d(rq);
       }
     }
   }
-  __syncthreads();
+  gsync<GN>(h);
 
   // ---- write the row and its mask
   const bool same_align = (((uintptr_t)rout) & 15) == (((uintptr_t)rin) & 15);
   float* ob = rout - head;
-  for (int k = threadIdx.x; k < nch; k += NT) {
+  for (int k = t; k < nch; k += GN) {
     const float4 v = st[k];
     const int lo = k == 0 ? head : 0, hi = k == nch - 1 ? tail : 4;
     if (same_align && lo == 0 && hi == 4) {
@@ -471,7 +534,7 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
     const int W32 = (T + 31) >> 5;
     unsigned* mrow = static_cast<unsigned*>(J.mask) + (size_t)row * W32;
     // word w covers chunk-grid positions head + 32 w ... head + 32 w + 31: chunks 8w .. 8w + 8
-    for (int w = threadIdx.x; w < W32; w += NT) {
+    for (int w = t; w < W32; w += GN) {
       unsigned long long bits = 0;
 #pragma unroll
       for (int j = 0; j < 9; j++) {
@@ -485,13 +548,13 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
     }
   } else if (P.mask_kind == MASK_BYTES && J.mask) {
     unsigned char* mb = static_cast<unsigned char*>(J.mask) + (size_t)row * T;
-    for (int t = threadIdx.x; t < T; t += NT) {
-      const int p = head + t;
+    for (int tt = t; tt < T; tt += GN) {
+      const int p = head + tt;
       const unsigned char f = (unsigned char)((fl4[p >> 2] >> (p & 3)) & 1u);
-      mb[t] = P.td_mask_or ? (unsigned char)(mb[t] | f) : f;
+      mb[tt] = P.td_mask_or ? (unsigned char)(mb[tt] | f) : f;
     }
   }
-  __syncthreads();
+  gsync<GN>(h);
 }
 
 // ---------------------------------------------------------------------------
@@ -832,7 +895,7 @@ __device__ bool wait_rows_f32(const Params& P, int job, unsigned need, int* flag
 
 __global__ void __launch_bounds__(NT, 2) k_engine_f32(const __grid_constant__ Params P) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ Red32 red;
+  __shared__ Red32 red[2];
   __shared__ int s_item, s_flag;
   for (;;) {
     if (threadIdx.x == 0) s_item = (int)atomicAdd(P.counters, 1u);
@@ -850,15 +913,24 @@ __global__ void __launch_bounds__(NT, 2) k_engine_f32(const __grid_constant__ Pa
     const int idx = item - sg.start;
     const Job& J = P.jobs[sg.job];
     if (sg.kind == 0) {
-      tdsc_row_f32(P, J, idx, smem, &red);
+      unsigned done = 1;
+      if (J.td_mode == 0) {
+        // two rows per item, one per half CTA (each half synchronises on its own barrier)
+        const int h = threadIdx.x / (NT / 2), t = threadIdx.x % (NT / 2);
+        const int row = 2 * idx + h;
+        if (row < J.rows) tdsc_row_f32<NT / 2>(P, J, row, smem + h * td32_smem_bytes(J.T), &red[h], t, h);
+        done = (unsigned)min(2, J.rows - 2 * idx);
+      } else {
+        tdsc_row_f32<NT>(P, J, idx, smem, &red[0], threadIdx.x, 0);
+      }
       __syncthreads();
       if (threadIdx.x == 0) {
         __threadfence();
-        if (sg.job != P.withhold_job) atomicAdd(P.counters + 1 + sg.job, 1u);
+        if (sg.job != P.withhold_job) atomicAdd(P.counters + 1 + sg.job, done);
       }
     } else {
       if (P.wait_tdsc && !wait_rows_f32(P, sg.job, (unsigned)J.rows, &s_flag)) continue;
-      fdsc_item_f32(P, J, idx, smem, &red);
+      fdsc_item_f32(P, J, idx, smem, &red[0]);
     }
   }
 }
@@ -868,7 +940,7 @@ int engine_smem_f32(const Params& p) {
   for (int j = 0; j < p.n_jobs; j++) {
     const Job& J = p.jobs[j];
     if (p.td.iterations > 0) {
-      const int td = td32_smem_bytes(J.T);
+      const int td = (J.td_mode == 0 ? 2 : 1) * td32_smem_bytes(J.T);
       s = s > td ? s : td;
     }
     if (p.fd.iterations > 0) {
