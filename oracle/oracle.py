@@ -20,7 +20,7 @@ SRC = os.path.join(HERE, "rfim_oracle.c")
 LIB = os.path.join(HERE, "liboracle.so")
 
 LAYOUT = {"bct": 0, "btc": 1}
-REPLACE = {"mean": 0, "median": 1}
+REPLACE = {"mean": 0, "median": 1, "random": 2}
 
 
 class OrcCut(ctypes.Structure):
@@ -65,6 +65,10 @@ def lib():
         L.orc_clean_u8_interleaved.restype = ctypes.c_int
         L.orc_clean_f32_interleaved.argtypes = [f32p, f32p, u8p, i64, i64, i64, ctypes.c_int, cutp, cutp]
         L.orc_clean_f32_interleaved.restype = ctypes.c_int
+        L.orc_mix64.argtypes = [ctypes.c_uint64]
+        L.orc_mix64.restype = ctypes.c_uint64
+        L.orc_draw.argtypes = [ctypes.c_int, ctypes.c_int, i64, i64, i64, ctypes.c_int, i64]
+        L.orc_draw.restype = i64
         f64p = ctypes.POINTER(ctypes.c_double)
         L.orc_clean_f32m.argtypes = [f32p, f32p, u8p, f64p, i64, i64, i64, ctypes.c_int, cutp, cutp]
         L.orc_clean_f32m.restype = ctypes.c_int
@@ -196,3 +200,13 @@ def clean_f32_margin(x: np.ndarray, layout: str = "bct", tdsc: dict | None = Non
     if rc != 0:
         raise OracleError(rc)
     return out, flags, margin
+
+
+def mix64(z: int) -> int:
+    """SplitMix64 output function of the random-replacement draws."""
+    return int(lib().orc_mix64(z & 0xFFFFFFFFFFFFFFFF))
+
+
+def draw(method: int, it: int, beam: int, line: int, index: int, attempt: int, n: int) -> int:
+    """Position in [0, n) of a random-replacement attempt (see rfim_oracle.h)."""
+    return int(lib().orc_draw(method, it, beam, line, index, attempt, n))

@@ -60,8 +60,41 @@ float orc_lower_median_f32(const float* x, int64_t n) {
 /*   |x - S/n| > k sqrt(Q/n - (S/n)^2)  <=>  (n x - S)^2 > k^2 (n Q - S^2) */
 /* evaluated on exact integers with one rounding for k^2 * R.          */
 /* ------------------------------------------------------------------ */
+/* ------------------------------------------------------------------ */
+/* Random replacement (Sec. IV, last paragraph: "random unflagged       */
+/* samples"): a flagged sample takes the current value of an unflagged  */
+/* sample of the same row (TDSC) or bin (FDSC), found by rejection      */
+/* sampling -- attempt a = 0..31 draws a position and takes it if that   */
+/* sample is unflagged in this iteration; after 32 misses the sample    */
+/* keeps its value.  Draws come from a counter-based hash: the SplitMix64 */
+/* output function (Steele, Lea, Flood 2014) of a key built from the    */
+/* method, iteration, beam, line, index and attempt.                     */
+/* ------------------------------------------------------------------ */
+uint64_t orc_mix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+/* position in [0, n) of attempt a; method 1 = TDSC (line = channel, index =
+ * time sample), 2 = FDSC (line = time sample, index = channel) */
+int64_t orc_draw(int method, int it, int64_t beam, int64_t line, int64_t index, int attempt, int64_t n) {
+  const uint64_t h = orc_mix64(orc_mix64(orc_mix64(orc_mix64((uint64_t)beam) ^ (uint64_t)line) ^ (uint64_t)index) ^
+                               ((uint64_t)method << 8 | (uint64_t)it << 16 | (uint64_t)attempt << 24));
+  return (int64_t)(((h >> 32) * (uint64_t)n) >> 32);
+}
+
+#define ORC_ATTEMPTS 32
+
 void orc_tdsc_row_u8(uint8_t* x, uint8_t* f, int64_t n, double k, int iters, int replace) {
+  orc_tdsc_row_u8x(x, f, n, k, iters, replace, 0, 0);
+}
+
+void orc_tdsc_row_u8x(uint8_t* x, uint8_t* f, int64_t n, double k, int iters, int replace, int64_t beam,
+                      int64_t line) {
   const double k2 = k * k;
+  uint8_t* fl = (uint8_t*)malloc((size_t)n);
   for (int it = 0; it < iters; it++) {
     int64_t S = 0, Q = 0;
     for (int64_t t = 0; t < n; t++) {
@@ -70,19 +103,32 @@ void orc_tdsc_row_u8(uint8_t* x, uint8_t* f, int64_t n, double k, int iters, int
     }
     const int64_t R = n * Q - S * S; /* n^2 sigma^2, exact */
     const double thr = k2 * (double)R;
-    uint8_t r;
+    uint8_t r = 0;
     if (replace == ORC_REPLACE_MEDIAN)
       r = orc_lower_median_u8(x, n);
-    else
+    else if (replace == ORC_REPLACE_MEAN)
       r = (uint8_t)((2 * S + n) / (2 * n)); /* mean, rounded half up */
     for (int64_t t = 0; t < n; t++) {
       const int64_t d = n * (int64_t)x[t] - S; /* n (x - mu) */
-      if ((double)(d * d) > thr) {
+      fl[t] = (double)(d * d) > thr;
+    }
+    for (int64_t t = 0; t < n; t++) {
+      if (!fl[t]) continue;
+      if (f) f[t] |= 1;
+      if (replace != ORC_REPLACE_RANDOM) {
         x[t] = r;
-        if (f) f[t] |= 1;
+        continue;
+      }
+      for (int a = 0; a < ORC_ATTEMPTS; a++) {
+        const int64_t u = orc_draw(1, it, beam, line, t, a, n);
+        if (!fl[u]) { /* unflagged samples are not changed in this iteration */
+          x[t] = x[u];
+          break;
+        }
       }
     }
   }
+  free(fl);
 }
 
 /* ------------------------------------------------------------------ */
@@ -112,12 +158,18 @@ static int64_t fdsc_lcm(int64_t n, int64_t bin) {
 }
 
 void orc_fdsc_col_u8(uint8_t* x, uint8_t* f, int64_t n, double k, int iters, int replace, int64_t bin) {
+  orc_fdsc_col_u8x(x, f, n, k, iters, replace, bin, 0, 0);
+}
+
+void orc_fdsc_col_u8x(uint8_t* x, uint8_t* f, int64_t n, double k, int iters, int replace, int64_t bin,
+                      int64_t beam, int64_t line) {
   const double k2 = k * k;
   const int64_t nb = (n + bin - 1) / bin;
   const int64_t L = fdsc_lcm(n, bin);
   int64_t* S = (int64_t*)malloc((size_t)nb * sizeof(int64_t));
   int64_t* D = (int64_t*)malloc((size_t)n * sizeof(int64_t));
   uint8_t* r = (uint8_t*)malloc((size_t)nb);
+  uint8_t* fl = (uint8_t*)malloc((size_t)n);
   for (int it = 0; it < iters; it++) {
     for (int64_t g = 0; g < nb; g++) {
       const int64_t c0 = g * bin, c1 = (c0 + bin < n) ? c0 + bin : n, G = c1 - c0;
@@ -136,16 +188,29 @@ void orc_fdsc_col_u8(uint8_t* x, uint8_t* f, int64_t n, double k, int iters, int
       V += D[c] * D[c];
     }
     const double thr = k2 * (double)V;
+    for (int64_t c = 0; c < n; c++) fl[c] = (double)(n * D[c] * D[c]) > thr;
     for (int64_t c = 0; c < n; c++) {
-      if ((double)(n * D[c] * D[c]) > thr) {
-        x[c] = r[c / bin];
-        if (f) f[c] |= 2;
+      if (!fl[c]) continue;
+      if (f) f[c] |= 2;
+      const int64_t g = c / bin, c0 = g * bin;
+      if (replace != ORC_REPLACE_RANDOM) {
+        x[c] = r[g];
+        continue;
+      }
+      const int64_t G = ((g + 1) * bin < n ? bin : n - g * bin);
+      for (int a = 0; a < ORC_ATTEMPTS; a++) {
+        const int64_t u = c0 + orc_draw(2, it, beam, line, c, a, G);
+        if (!fl[u]) {
+          x[c] = x[u];
+          break;
+        }
       }
     }
   }
   free(S);
   free(D);
   free(r);
+  free(fl);
 }
 
 /* ------------------------------------------------------------------ */
@@ -165,6 +230,12 @@ void orc_tdsc_row_f32(float* x, uint8_t* f, int64_t n, double k, int iters, int 
 }
 
 void orc_tdsc_row_f32m(float* x, uint8_t* f, double* margin, int64_t n, double k, int iters, int replace) {
+  orc_tdsc_row_f32x(x, f, margin, n, k, iters, replace, 0, 0);
+}
+
+void orc_tdsc_row_f32x(float* x, uint8_t* f, double* margin, int64_t n, double k, int iters, int replace,
+                       int64_t beam, int64_t line) {
+  uint8_t* fl = (uint8_t*)malloc((size_t)n);
   for (int it = 0; it < iters; it++) {
     double s = 0.0;
     for (int64_t t = 0; t < n; t++) s += (double)x[t];
@@ -179,12 +250,25 @@ void orc_tdsc_row_f32m(float* x, uint8_t* f, double* margin, int64_t n, double k
     const float r = (replace == ORC_REPLACE_MEDIAN) ? orc_lower_median_f32(x, n) : (float)mu;
     for (int64_t t = 0; t < n; t++) {
       if (margin) note_margin(margin + t, fabs((double)x[t] - mu), thr);
-      if (fabs((double)x[t] - mu) > thr) {
+      fl[t] = fabs((double)x[t] - mu) > thr;
+    }
+    for (int64_t t = 0; t < n; t++) {
+      if (!fl[t]) continue;
+      if (f) f[t] |= 1;
+      if (replace != ORC_REPLACE_RANDOM) {
         x[t] = r;
-        if (f) f[t] |= 1;
+        continue;
+      }
+      for (int a = 0; a < ORC_ATTEMPTS; a++) {
+        const int64_t u = orc_draw(1, it, beam, line, t, a, n);
+        if (!fl[u]) {
+          x[t] = x[u];
+          break;
+        }
       }
     }
   }
+  free(fl);
 }
 
 void orc_fdsc_col_f32(float* x, uint8_t* f, int64_t n, double k, int iters, int replace, int64_t bin) {
@@ -193,10 +277,16 @@ void orc_fdsc_col_f32(float* x, uint8_t* f, int64_t n, double k, int iters, int 
 
 void orc_fdsc_col_f32m(float* x, uint8_t* f, double* margin, int64_t n, double k, int iters, int replace,
                        int64_t bin) {
+  orc_fdsc_col_f32x(x, f, margin, n, k, iters, replace, bin, 0, 0);
+}
+
+void orc_fdsc_col_f32x(float* x, uint8_t* f, double* margin, int64_t n, double k, int iters, int replace,
+                       int64_t bin, int64_t beam, int64_t line) {
   const int64_t nb = (n + bin - 1) / bin;
   double* m = (double*)malloc((size_t)nb * sizeof(double));
   double* d = (double*)malloc((size_t)n * sizeof(double));
   float* r = (float*)malloc((size_t)nb * sizeof(float));
+  uint8_t* fl = (uint8_t*)malloc((size_t)n);
   for (int it = 0; it < iters; it++) {
     for (int64_t g = 0; g < nb; g++) {
       const int64_t c0 = g * bin, c1 = (c0 + bin < n) ? c0 + bin : n;
@@ -219,15 +309,30 @@ void orc_fdsc_col_f32m(float* x, uint8_t* f, double* margin, int64_t n, double k
     const double thr = k * sqrt(ss / (double)n);
     for (int64_t c = 0; c < n; c++) {
       if (margin) note_margin(margin + c, fabs(d[c] - mu), thr);
-      if (fabs(d[c] - mu) > thr) {
-        x[c] = r[c / bin];
-        if (f) f[c] |= 2;
+      fl[c] = fabs(d[c] - mu) > thr;
+    }
+    for (int64_t c = 0; c < n; c++) {
+      if (!fl[c]) continue;
+      if (f) f[c] |= 2;
+      const int64_t g = c / bin, c0 = g * bin;
+      if (replace != ORC_REPLACE_RANDOM) {
+        x[c] = r[g];
+        continue;
+      }
+      const int64_t G = ((g + 1) * bin < n ? bin : n - g * bin);
+      for (int a = 0; a < ORC_ATTEMPTS; a++) {
+        const int64_t u = c0 + orc_draw(2, it, beam, line, c, a, G);
+        if (!fl[u]) {
+          x[c] = x[u];
+          break;
+        }
       }
     }
   }
   free(m);
   free(d);
   free(r);
+  free(fl);
 }
 
 /* ------------------------------------------------------------------ */
@@ -237,7 +342,8 @@ static int check_cut(const orc_cut* c, int is_fdsc, int64_t C) {
   if (!c || !c->enabled) return ORC_OK;
   if (!(c->k > 0.0) || !isfinite(c->k)) return ORC_ERR_ARG;
   if (c->iterations < 1 || c->iterations > 16) return ORC_ERR_ARG;
-  if (c->replace != ORC_REPLACE_MEAN && c->replace != ORC_REPLACE_MEDIAN) return ORC_ERR_ARG;
+  if (c->replace != ORC_REPLACE_MEAN && c->replace != ORC_REPLACE_MEDIAN && c->replace != ORC_REPLACE_RANDOM)
+    return ORC_ERR_ARG;
   if (is_fdsc && (c->bin < 1 || c->bin > C)) return ORC_ERR_ARG;
   return ORC_OK;
 }
@@ -284,7 +390,7 @@ int orc_clean_u8(const uint8_t* in, uint8_t* out, uint8_t* flags, int64_t B, int
           v[t] = out[at(b, c, t, C, T, layout)];
           fl[t] = 0;
         }
-        orc_tdsc_row_u8(v, fl, T, tdsc->k, tdsc->iterations, tdsc->replace);
+        orc_tdsc_row_u8x(v, fl, T, tdsc->k, tdsc->iterations, tdsc->replace, b, c);
         for (int64_t t = 0; t < T; t++) {
           out[at(b, c, t, C, T, layout)] = v[t];
           if (flags) flags[at(b, c, t, C, T, layout)] |= fl[t];
@@ -298,7 +404,7 @@ int orc_clean_u8(const uint8_t* in, uint8_t* out, uint8_t* flags, int64_t B, int
           v[c] = out[at(b, c, t, C, T, layout)];
           fl[c] = 0;
         }
-        orc_fdsc_col_u8(v, fl, C, fdsc->k, fdsc->iterations, fdsc->replace, fdsc->bin);
+        orc_fdsc_col_u8x(v, fl, C, fdsc->k, fdsc->iterations, fdsc->replace, fdsc->bin, b, t);
         for (int64_t c = 0; c < C; c++) {
           out[at(b, c, t, C, T, layout)] = v[c];
           if (flags) flags[at(b, c, t, C, T, layout)] |= fl[c];
@@ -336,7 +442,7 @@ int orc_clean_f32m(const float* in, float* out, uint8_t* flags, double* margin, 
           fl[t] = 0;
           if (mg) mg[t] = INFINITY;
         }
-        orc_tdsc_row_f32m(v, fl, mg, T, tdsc->k, tdsc->iterations, tdsc->replace);
+        orc_tdsc_row_f32x(v, fl, mg, T, tdsc->k, tdsc->iterations, tdsc->replace, b, c);
         for (int64_t t = 0; t < T; t++) {
           out[at(b, c, t, C, T, layout)] = v[t];
           if (flags) flags[at(b, c, t, C, T, layout)] |= fl[t];
@@ -352,7 +458,7 @@ int orc_clean_f32m(const float* in, float* out, uint8_t* flags, double* margin, 
           fl[c] = 0;
           if (mg) mg[c] = INFINITY;
         }
-        orc_fdsc_col_f32m(v, fl, mg, C, fdsc->k, fdsc->iterations, fdsc->replace, fdsc->bin);
+        orc_fdsc_col_f32x(v, fl, mg, C, fdsc->k, fdsc->iterations, fdsc->replace, fdsc->bin, b, t);
         for (int64_t c = 0; c < C; c++) {
           out[at(b, c, t, C, T, layout)] = v[c];
           if (flags) flags[at(b, c, t, C, T, layout)] |= fl[c];

@@ -53,6 +53,7 @@ extern "C" {
 /* replacement strategy */
 #define ORC_REPLACE_MEAN 0
 #define ORC_REPLACE_MEDIAN 1
+#define ORC_REPLACE_RANDOM 2 /* a random unflagged sample of the same row / bin */
 /* return codes */
 #define ORC_OK 0
 #define ORC_ERR_ARG 1
@@ -80,6 +81,22 @@ void orc_tdsc_row_u8(uint8_t* x, uint8_t* f, int64_t n, double k, int iters, int
 void orc_fdsc_col_u8(uint8_t* x, uint8_t* f, int64_t n, double k, int iters, int replace, int64_t bin);
 void orc_tdsc_row_f32(float* x, uint8_t* f, int64_t n, double k, int iters, int replace);
 void orc_fdsc_col_f32(float* x, uint8_t* f, int64_t n, double k, int iters, int replace, int64_t bin);
+
+/* Random replacement: SplitMix64 output function, and the position in
+ * [0, n) of attempt `attempt` for (method 1 = TDSC / 2 = FDSC, iteration,
+ * beam, line, index) -- line/index = channel/time for TDSC, time/channel for
+ * FDSC (where the position is within the bin). */
+uint64_t orc_mix64(uint64_t z);
+int64_t orc_draw(int method, int it, int64_t beam, int64_t line, int64_t index, int attempt, int64_t n);
+/* the row/column cuts with the beam and line that key the random draws */
+void orc_tdsc_row_u8x(uint8_t* x, uint8_t* f, int64_t n, double k, int iters, int replace, int64_t beam,
+                      int64_t line);
+void orc_fdsc_col_u8x(uint8_t* x, uint8_t* f, int64_t n, double k, int iters, int replace, int64_t bin,
+                      int64_t beam, int64_t line);
+void orc_tdsc_row_f32x(float* x, uint8_t* f, double* margin, int64_t n, double k, int iters, int replace,
+                       int64_t beam, int64_t line);
+void orc_fdsc_col_f32x(float* x, uint8_t* f, double* margin, int64_t n, double k, int iters, int replace,
+                       int64_t bin, int64_t beam, int64_t line);
 
 /* The combined cleaner in interleaved order: round i applies TDSC iteration i
  * to every row, then FDSC iteration i to every column (single-iteration cuts

@@ -502,3 +502,73 @@ def noise_u8_local(rng, shape):
     flat = x.reshape(-1)
     flat[rng.integers(0, flat.size, max(1, flat.size // 30))] = 250
     return x
+
+
+def test_random_replacement_generator(oracle):
+    # SplitMix64 (Steele, Lea, Flood 2014) seeded with 0: its first two outputs
+    assert oracle.mix64(0) == 0xE220A8397B1DCDAF
+    assert oracle.mix64(0x9E3779B97F4A7C15) == 0x6E789E6AA1B965F4
+    # draws fall in [0, n) and spread over it
+    seen = {oracle.draw(1, 0, 3, 7, i, 0, 10) for i in range(400)}
+    assert seen == set(range(10))
+
+
+def test_random_replacement_takes_unflagged_values(oracle):
+    # one iteration: a flagged sample takes the value of an unflagged sample of
+    # the same row (TDSC) or bin (FDSC) -- the first draw that hits one
+    rng = np.random.default_rng(12)
+    x = noise_u8_local(rng, (2, 16, 300))
+    td = dict(k=1.5, iterations=1, replace="random")
+    out, fl = oracle.clean(x, "bct", tdsc=td)
+    for b in range(2):
+        for c in range(16):
+            row, o, f = x[b, c], out[b, c], fl[b, c] > 0
+            assert f.any() and (~f).any()
+            assert np.array_equal(o[~f], row[~f])
+            for t in np.flatnonzero(f):
+                for a in range(32):
+                    u = oracle.draw(1, 0, b, c, t, a, row.size)
+                    if not f[u]:
+                        assert o[t] == row[u]
+                        break
+                else:
+                    assert o[t] == row[t]
+    fd = dict(k=1.5, iterations=1, replace="random", bin=8)
+    out, fl = oracle.clean(x, "bct", fdsc=fd)
+    for b in range(2):
+        for t in range(0, 300, 37):
+            col, o, f = x[b, :, t], out[b, :, t], fl[b, :, t] > 0
+            assert np.array_equal(o[~f], col[~f])
+            for c in np.flatnonzero(f):
+                g0 = (c // 8) * 8
+                for a in range(32):
+                    u = g0 + oracle.draw(2, 0, b, t, c, a, 8)
+                    if not f[u]:
+                        assert o[c] == col[u]
+                        break
+                else:
+                    assert o[c] == col[c]
+
+
+def test_random_replacement_statistics_and_edge_cases(oracle):
+    # the replaced values average to the mean of the kept samples
+    rng = np.random.default_rng(4)
+    x = np.clip(np.rint(rng.normal(100, 10, (1, 4, 20000))), 0, 255).astype(np.uint8)
+    x[0, :, ::50] = 250
+    out, fl = oracle.clean(x, "bct", tdsc=dict(k=3.0, iterations=1, replace="random"))
+    f = fl[0] > 0
+    assert abs(out[0][f].astype(float).mean() - x[0][~f].astype(float).mean()) < 1.0
+    # everything flagged (|x - mu| = sigma > k sigma for k < 1): nothing to draw, values stay
+    z = np.tile(np.array([0, 255], np.uint8), (1, 2, 50))
+    out, fl = oracle.clean(z, "bct", tdsc=dict(k=0.5, iterations=2, replace="random"))
+    assert np.array_equal(out, z) and (fl == 1).all()
+    # float32 follows the same rule
+    y = z.astype(np.float32)
+    out32, fl32 = oracle.clean(y, "bct", tdsc=dict(k=0.5, iterations=1, replace="random"))
+    assert np.array_equal(out32, y) and (fl32 == 1).all()
+    xf = x.astype(np.float32)
+    o8, f8 = oracle.clean(x, "bct", tdsc=dict(k=3.0, iterations=2, replace="random"),
+                          fdsc=dict(k=3.0, iterations=2, replace="random", bin=2))
+    o32, f32 = oracle.clean(xf, "bct", tdsc=dict(k=3.0, iterations=2, replace="random"),
+                            fdsc=dict(k=3.0, iterations=2, replace="random", bin=2))
+    assert np.array_equal(f8, f32) and np.array_equal(o8.astype(np.float32), o32)
