@@ -91,7 +91,22 @@ typedef enum { RFIM_U8 = 0, RFIM_F32 = 1 } rfim_dtype;
  */
 typedef enum { RFIM_LAYOUT_BCT = 0, RFIM_LAYOUT_BTC = 1 } rfim_layout;
 
-typedef enum { RFIM_REPLACE_MEAN = 0, RFIM_REPLACE_MEDIAN = 1 } rfim_replace;
+/*
+ * Replacement strategies (Sec. IV, last paragraph): the mean, the lower median,
+ * or a random unflagged sample.  RANDOM: a flagged sample takes the current
+ * value of an unflagged sample of the same row (TDSC) or bin (FDSC), found by
+ * rejection sampling: attempt a = 0..31 draws position
+ *   u = ((h >> 32) * n) >> 32,  h = M(M(M(M(beam) ^ line) ^ index) ^ (method << 8 | it << 16 | a << 24)),
+ * with M the SplitMix64 output function (Steele, Lea, Flood 2014: z += 0x9E3779B97F4A7C15,
+ * then the two xor-shift-multiply rounds), n the row length (TDSC) or bin
+ * size (FDSC, u relative to the bin's first channel), method 1 = TDSC (line =
+ * channel, index = time sample), 2 = FDSC (line = time sample, index =
+ * channel), beam = the beam's index within its block, it = the iteration; the
+ * first draw that hits an unflagged sample wins, and after 32 misses the
+ * sample keeps its value.  uint8 TDSC rows with RANDOM hold at most 78,609
+ * samples.
+ */
+typedef enum { RFIM_REPLACE_MEAN = 0, RFIM_REPLACE_MEDIAN = 1, RFIM_REPLACE_RANDOM = 2 } rfim_replace;
 
 /*
  * Flag-mask output.

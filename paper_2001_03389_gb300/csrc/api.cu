@@ -128,7 +128,7 @@ rfim_status check_cut(rfim_ctx* ctx, const rfim_cut* c, int C, bool fdsc, CutNor
     return fail(ctx, RFIM_ERR_ARG, "k must be finite and in [1e-3, 1e6], got %g", c->k);
   if (c->iterations < 1 || c->iterations > 16)
     return fail(ctx, RFIM_ERR_ARG, "iterations must be in 1..16, got %d", c->iterations);
-  if (c->replace != RFIM_REPLACE_MEAN && c->replace != RFIM_REPLACE_MEDIAN)
+  if (c->replace != RFIM_REPLACE_MEAN && c->replace != RFIM_REPLACE_MEDIAN && c->replace != RFIM_REPLACE_RANDOM)
     return fail(ctx, RFIM_ERR_ARG, "unknown replacement strategy %d", (int)c->replace);
   int bin = c->fdsc_bin;
   if (fdsc) {
@@ -202,17 +202,20 @@ rfim_status check_impl(rfim_ctx* ctx, const rfim_block* b, const CutNorm& td, co
                   TD32_MAX_T);
     if (fd.on) {
       const int C = b->channels, nb = (C + fd.bin - 1) / fd.bin;
-      if (fd32_smem_bytes(1, C, nb) > MAX_SMEM_PER_CTA)
+      if (fd32_smem_bytes(1, C, nb, fd.rep == RFIM_REPLACE_RANDOM) > MAX_SMEM_PER_CTA)
         return fail(ctx, RFIM_ERR_RANGE, "FDSC: %d float32 channels do not fit the on-chip tile", C);
     }
     return RFIM_OK;
   }
   if (td.on && td_row_mode(b->samples) < 0)
     return fail(ctx, RFIM_ERR_ARG, "TDSC rows longer than 98273 samples are not available in this build");
+  if (td.on && td.rep == RFIM_REPLACE_RANDOM && td_random_row_mode(b->samples) < 0)
+    return fail(ctx, RFIM_ERR_ARG, "uint8 TDSC with random replacement: rows longer than 78609 samples are not "
+                "available in this build");
   if (fd.on) {
     // the smallest FDSC tile (8 samples x all channels) must fit one CTA's shared memory
     const int C = b->channels, nb = (C + fd.bin - 1) / fd.bin;
-    if (fd_smem_bytes(8, fd_pitch(C), nb, C) > MAX_SMEM_PER_CTA)
+    if (fd_smem_bytes(8, fd_pitch(C), nb, C, fd.rep == RFIM_REPLACE_RANDOM) > MAX_SMEM_PER_CTA)
       return fail(ctx, RFIM_ERR_RANGE, "FDSC: %d channels do not fit the on-chip tile", C);
   }
   return RFIM_OK;
@@ -226,10 +229,10 @@ struct Plan {
   rfim_dtype dtype = RFIM_U8;
 };
 
-int pick_ws_opt(int tile_samples, int C, int nb, int pitch, int budget) {
+int pick_ws_opt(int tile_samples, int C, int nb, int pitch, int budget, bool rnd) {
   if (tile_samples > 0) return tile_samples < 8 ? 8 : tile_samples;  // uint8 tiles are 8, 16 or 32 wide
   for (int ws : {32, 16, 8})
-    if (fd_smem_bytes(ws, pitch, nb, C) <= budget) return ws;
+    if (fd_smem_bytes(ws, pitch, nb, C, rnd) <= budget) return ws;
   return 8;
 }
 
@@ -251,6 +254,7 @@ Job make_job(const rfim_block* b, int j, const CutNorm& fd, int tile_samples, in
     J.mask = nullptr;
   J.src_lo = J.in;
   J.src_hi = (const char*)J.in + beam * es;
+  J.beam = j;
   J.C = C;
   J.T = T;
   J.rows = C;
@@ -261,7 +265,7 @@ Job make_job(const rfim_block* b, int j, const CutNorm& fd, int tile_samples, in
   J.m_full = (unsigned long long)(L / G);
   J.m_last = (unsigned long long)(L / J.last_g);
   J.pitch = fd_pitch(C * (int)es);
-  J.ws = pick_ws_opt(tile_samples, C, J.nb, J.pitch, smem_target);
+  J.ws = pick_ws_opt(tile_samples, C, J.nb, J.pitch, smem_target, fd.on && fd.rep == RFIM_REPLACE_RANDOM);
   J.fd_items = (T + FD_ITEM_T - 1) / FD_ITEM_T;
   J.td_mode = td_row_mode(T) == 1 ? 1 : 0;
   J.td_items = J.td_mode == 0 ? (C + TD_ROWS_PER_ITEM - 1) / TD_ROWS_PER_ITEM : C;
@@ -272,7 +276,7 @@ Job make_job(const rfim_block* b, int j, const CutNorm& fd, int tile_samples, in
     J.td_items = J.td_mode == 0 ? (C + 1) / 2 : C;
     J.ws = 1;
     for (int ws : {8, 4, 2})
-      if ((tile_samples == 0 || ws <= tile_samples) && fd32_smem_bytes(ws, C, J.nb) <= smem_target) {
+      if ((tile_samples == 0 || ws <= tile_samples) && fd32_smem_bytes(ws, C, J.nb, fd.on && fd.rep == RFIM_REPLACE_RANDOM) <= smem_target) {
         J.ws = ws;
         break;
       }
@@ -281,9 +285,17 @@ Job make_job(const rfim_block* b, int j, const CutNorm& fd, int tile_samples, in
   return J;
 }
 
+// uint8 TDSC with random replacement: warp or CTA rows by the stage the flags need
+void random_row_mode(Job& J, const rfim_block* b, const CutNorm& td) {
+  if (b->dtype != RFIM_U8 || !td.on || td.rep != RFIM_REPLACE_RANDOM) return;
+  J.td_mode = td_random_row_mode(b->samples) == 1 ? 1 : 0;
+  J.td_items = J.td_mode == 0 ? (b->channels + TD_ROWS_PER_ITEM - 1) / TD_ROWS_PER_ITEM : b->channels;
+}
+
 void add_block_jobs(rfim_ctx* ctx, Plan& pl, const rfim_block* b) {
   for (int j = 0; j < b->beams; j++) {
     pl.jobs.push_back(make_job(b, j, pl.fd, ctx->tile_samples, ctx->smem_target));
+    random_row_mode(pl.jobs.back(), b, pl.td);
     pl.max_T = std::max(pl.max_T, b->samples);
   }
 }
@@ -877,7 +889,10 @@ rfim_status launch_blocks_fixed(const rfim_block* blocks, int n, const rfim_cut*
   memset(&p, 0, sizeof p);
   p.n_jobs = beams;
   for (int i = 0, j0 = 0; i < n; j0 += blocks[i].beams, i++)
-    for (int j = 0; j < blocks[i].beams; j++) p.jobs[j0 + j] = make_job(&blocks[i], j, fd, 0, 113 * 1024);
+    for (int j = 0; j < blocks[i].beams; j++) {
+      p.jobs[j0 + j] = make_job(&blocks[i], j, fd, 0, 113 * 1024);
+      random_row_mode(p.jobs[j0 + j], &blocks[i], td);
+    }
   const rfim_block* b = &blocks[0];
   const int mode = (td.on && fd.on) ? 2 : (td.on ? 0 : 1);
   p.td = cut_dev(td);

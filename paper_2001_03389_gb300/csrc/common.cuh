@@ -220,6 +220,34 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
   return t;
 }
 
+// ---------------------------------------------------------------------------
+// Random replacement draws: the SplitMix64 output function (Steele, Lea,
+// Flood, "Fast splittable pseudorandom number generators", 2014) of a key
+// built from (beam, line, index, method, iteration, attempt).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// key of a (beam, line): mix64(mix64(beam) ^ line)
+__device__ __forceinline__ unsigned long long draw_key(int beam, int line) {
+  return mix64(mix64((unsigned long long)beam) ^ (unsigned long long)line);
+}
+
+// position in [0, n) of attempt a (method 1 = TDSC, 2 = FDSC)
+__device__ __forceinline__ unsigned draw_pos(unsigned long long key, int index, int method, int it, int a,
+                                             unsigned n) {
+  const unsigned long long h = mix64(mix64(key ^ (unsigned long long)index) ^
+                                     ((unsigned long long)method << 8 | (unsigned long long)it << 16 |
+                                      (unsigned long long)a << 24));
+  return (unsigned)(((h >> 32) * (unsigned long long)n) >> 32);
+}
+
+constexpr int DRAW_ATTEMPTS = 32;
+
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");

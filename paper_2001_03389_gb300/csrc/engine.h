@@ -12,7 +12,7 @@ constexpr int FD_ITEM_T = 32;      // time samples per uint8 FDSC work item (one
 // float32 FDSC work items are one sub-slab (Job::ws = 1, 2, 4 or 8 samples): the
 // items that share a 128-byte line of each channel row run side by side.
 
-enum ReplaceKind { REP_MEAN = 0, REP_MEDIAN = 1 };
+enum ReplaceKind { REP_MEAN = 0, REP_MEDIAN = 1, REP_RANDOM = 2 };
 enum MaskKind { MASK_NONE = 0, MASK_BITS = 1, MASK_BYTES = 2 };
 
 // One sigma cut as the kernels see it.
@@ -43,6 +43,7 @@ struct Job {
   int td_mode;      // uint8: 0 = one warp per row, 8 rows per item; 1 = one row per item, whole CTA.
                     // float32: 0 = two rows per item, a half CTA each; 1 = one row per item
   int td_items;     // number of TDSC work items
+  int beam;         // index of the beam within its block (keys the random-replacement draws)
 };
 
 // A run of consecutive queue items: `count` items of one kind for one job.
@@ -78,10 +79,12 @@ __host__ __device__ inline int align16i(int x) { return (x + 15) & ~15; }
 // 8 lanes of 4 neighbouring columns hit 32 distinct banks.
 __host__ __device__ inline int fd_nbp(int nb) { return nb + ((8 - nb) % 32 + 32) % 32; }
 
-__host__ __device__ inline int fd_smem_bytes(int ws, int pitch, int nb, int C) {
+// rnd: random replacement adds one word per channel (the flags of the
+// iteration in progress, bit = tile row)
+__host__ __device__ inline int fd_smem_bytes(int ws, int pitch, int nb, int C, bool rnd = false) {
   const int nbp = fd_nbp(nb);
   return ws * pitch + 2 * align16i(ws * nbp * 4) + align16i(ws * nbp * 2) + align16i(ws * 8) + align16i(ws * 8) +
-         align16i(C * 4) + align16i(ws * nb * 4) + 4 * (NT / 32);
+         align16i(C * 4) + align16i(ws * nb * 4) + 4 * (NT / 32) + (rnd ? align16i(C * 4) : 0);
 }
 
 // Tile row pitch: C bytes rounded up to 128, so that the XOR swizzle of the 16-byte
@@ -99,6 +102,15 @@ constexpr int TD_WARP_CHUNKS = 800;
 constexpr int TD_WARP_STAGE = TD_WARP_CHUNKS * 16;
 constexpr int TD_CTA_CHUNKS = 6144;
 constexpr int TD_ROWS_PER_ITEM = NT / 32;
+// Random replacement keeps two 16-bit flag words per chunk beside the staged
+// row (this iteration's flags, and the OR over iterations): warp rows up to 640
+// chunks, longer rows (up to 4915 chunks) by the whole CTA.
+__host__ __device__ inline int td_random_row_mode(long long T) {
+  const long long nch = (T + 30) / 16 + 1;
+  if (20 * nch <= TD_WARP_STAGE) return 0;
+  if (20 * nch <= TD_CTA_CHUNKS * 16) return 1;
+  return -1;
+}
 
 // Row mode for rows of T bytes: 0 = warp rows, 1 = CTA rows, -1 = too long.
 inline int td_row_mode(long long T) {
@@ -125,10 +137,11 @@ __host__ __device__ inline int td32_smem_bytes(int T) {
   const int nch = (T + 6) / 4 + 1;
   return 16 * nch + align16i(nch) + 4 * TD32_LIST;
 }
-__host__ __device__ inline int fd32_smem_bytes(int ws, int C, int nb) {
+// rnd: random replacement adds one flag word per channel
+__host__ __device__ inline int fd32_smem_bytes(int ws, int C, int nb, bool rnd = false) {
   const int U = ws * nb;
   return align16i(ws * C * 4) + align16i(C * 4) + align16i(U * 8) * 2 + align16i(U * 4) + align16i(ws * 8) +
-         align16i(ws * 4) * 3;
+         align16i(ws * 4) * 3 + (rnd ? align16i(C * 4) : 0);
 }
 int engine_smem_f32(const Params& p);
 void* engine_kernel_f32();

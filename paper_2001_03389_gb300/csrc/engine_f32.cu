@@ -398,6 +398,7 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
   RowStat* rs_ = &rs_g[h];
   const double Tn = (double)T, rT = 1.0 / (double)T;
   const int I = cut.iterations;
+  const bool rnd = cut.replace == REP_RANDOM;
 
   for (int it = 0; it < I; it++) {
     // statistics of the current values, finished in double by one thread
@@ -459,6 +460,42 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
     // decide and replace; the replaced values go to a list for the statistics update
     if (t == 0) s_nlist = 0;
     gsync<GN>(h);
+    if (rnd) {
+      // random replacement: this iteration's flags first (high nibble of fl4),
+      // then each flagged sample copies the first drawn sample that is unflagged
+      // (those are never written in this iteration)
+      for (int k = t; k < nch; k += GN) {
+        const float4 v = st[k];
+        const int lo = k == 0 ? head : 0, hi = k == nch - 1 ? tail : 4;
+        unsigned nib = 0;
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+          if (i >= lo && i < hi && flag32(f4_get(v, i), c)) nib |= 1u << i;
+        fl4[k] = (unsigned char)((fl4[k] & 0xFu) | nib | (nib << 4));
+      }
+      gsync<GN>(h);
+      const float* sf = reinterpret_cast<const float*>(st) + head;  // sample tt at sf[tt]
+      const unsigned long long key = draw_key(J.beam, row);
+      for (int k = t; k < nch; k += GN) {
+        const unsigned nib = fl4[k] >> 4;
+        if (!nib) continue;
+        float4 v = st[k];
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+          if (!((nib >> i) & 1u)) continue;
+          const int tt = 4 * k + i - head;
+          for (int a = 0; a < DRAW_ATTEMPTS; a++) {
+            const unsigned u = draw_pos(key, tt, 1, it, a, (unsigned)T);
+            const unsigned pu = (unsigned)head + u;
+            if (!((fl4[pu >> 2] >> (4 + (pu & 3))) & 1u)) {
+              f4_set(v, i, sf[u]);
+              break;
+            }
+          }
+        }
+        st[k] = v;
+      }
+    } else
     for (int k = t; k < nch; k += GN) {
       float4 v = st[k];
       const int lo = k == 0 ? head : 0, hi = k == nch - 1 ? tail : 4;
@@ -481,7 +518,7 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
     if (it == I - 1) break;
     gsync<GN>(h);
     // statistics of the next iteration: S' = S - sum(replaced) + nf r (same for Q)
-    const int nflag = s_nlist;
+    const int nflag = rnd ? TD32_LIST + 1 : s_nlist;  // random: the replaced-with values vary, sum the row again
     FF rs{0.f, 0.f}, rq{0.f, 0.f};
     if (nflag <= TD32_LIST) {
       for (int i = t; i < nflag; i += GN) {
@@ -576,6 +613,7 @@ struct Fd32Layout {
   float* thr_lo;  // ws
   float* thr_hi;  // ws
   int* prec;      // ws: column needs the FP64 two-pass
+  unsigned* fcur; // C (random replacement only): flags of the iteration in progress (bit = t - t0)
 };
 
 __device__ __forceinline__ Fd32Layout fd32_layout(unsigned char* smem, int ws, int C, int nb) {
@@ -599,6 +637,8 @@ __device__ __forceinline__ Fd32Layout fd32_layout(unsigned char* smem, int ws, i
   L.thr_hi = reinterpret_cast<float*>(p);
   p += align16i(ws * 4);
   L.prec = reinterpret_cast<int*>(p);
+  p += align16i(ws * 4);
+  L.fcur = reinterpret_cast<unsigned*>(p);
   return L;
 }
 
@@ -628,7 +668,10 @@ __device__ void fdsc_item_f32(const Params& P, const Job& J, int item, unsigned 
   const bool vec = ((((uintptr_t)src) | ((uintptr_t)dst)) & 15) == 0 && (T & 3) == 0;
   const double Cn = (double)C, rC = 1.0 / (double)C;
 
+  const bool rnd = cut.replace == REP_RANDOM;
   for (int c = threadIdx.x; c < C; c += NT) L.fm[c] = 0;
+  if (rnd)
+    for (int c = threadIdx.x; c < C; c += NT) L.fcur[c] = 0;  // each unit clears its own bits after use
 
   for (int t0 = t_item; t0 < t_end; t0 += Ws) {
     const int w = min(Ws, t_end - t0);
@@ -803,6 +846,30 @@ __device__ void fdsc_item_f32(const Params& P, const Job& J, int item, unsigned 
         band_bounds_f(L.thr_lo[t], L.thr_hi[t], fabsf(m.y), cc.lo_f, cc.hi_f);
         const unsigned bit = 1u << (t0 + t - t_item);
         const int rot = g % n;
+        if (rnd) {
+          // random replacement: this iteration's flags of the bin go to fcur
+          // first, so each draw tests the flag of the value it would copy
+          const unsigned tb = 1u << t;
+          for (int j = 0; j < n; j++)
+            if (flag32(L.tile[(c0 + j) * Ws + t], cc)) {
+              atomicOr(&L.fcur[c0 + j], tb);
+              atomicOr(&L.fm[c0 + j], bit);
+            }
+          const unsigned long long key = draw_key(J.beam, t0 + t);
+          for (int j = 0; j < n; j++) {
+            if (!(L.fcur[c0 + j] & tb)) continue;
+            for (int a = 0; a < DRAW_ATTEMPTS; a++) {
+              const int uu = (int)draw_pos(key, c0 + j, 2, it, a, (unsigned)n);
+              if (!(L.fcur[c0 + uu] & tb)) {
+                L.tile[(c0 + j) * Ws + t] = L.tile[(c0 + uu) * Ws + t];
+                break;
+              }
+            }
+          }
+          for (int j = 0; j < n; j++)
+            if (L.fcur[c0 + j] & tb) atomicAnd(&L.fcur[c0 + j], ~tb);
+          continue;
+        }
         float r = m.x;
         if (cut.replace == REP_MEDIAN) {
           // the median only where the bin has a flag
@@ -944,7 +1011,7 @@ int engine_smem_f32(const Params& p) {
       s = s > td ? s : td;
     }
     if (p.fd.iterations > 0) {
-      const int fd = fd32_smem_bytes(J.ws, J.C, J.nb);
+      const int fd = fd32_smem_bytes(J.ws, J.C, J.nb, p.fd.replace == REP_RANDOM);
       s = s > fd ? s : fd;
     }
   }

@@ -465,7 +465,8 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
   // single: every flagged sample ends at one value (the median, or the mean of a
   // one-iteration cut), so one keep interval (the intersection) decides everything
   const bool median = cut.replace == REP_MEDIAN;
-  const bool single = median || cut.iterations == 1;
+  const bool random = cut.replace == REP_RANDOM;
+  const bool single = !random && (median || cut.iterations == 1);
   const unsigned long long npad = 16ull * (unsigned)g.nch - (unsigned)T;  // zero bytes in the chunk grid
   const int I = cut.iterations;
   const float rcpT = 1.0f / (float)T, rcp2T = 0.5f / (float)T;
@@ -526,6 +527,64 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
     if (I == 1)
       r_med = median ? med_finish<LANES>(ms, st, g.nch, T, npad, scr, gl)
                      : udiv_q((unsigned)(2 * S + (unsigned long long)T), 2u * (unsigned)T, rcp2T);
+  } else if (random) {
+    // Each iteration records its flags per chunk first (fcur), then replaces a
+    // flagged byte by the first drawn byte that fcur marks unflagged: those are
+    // never written in this iteration, so the draws see the values they test.
+    uint16_t* fcur = reinterpret_cast<uint16_t*>(st + g.nch);
+    uint16_t* facc = fcur + g.nch;  // flags OR-ed over the iterations
+    const uint8_t* sb = reinterpret_cast<const uint8_t*>(st) + g.head;  // row byte t at sb[t]
+    const unsigned long long key = draw_key(J.beam, row);
+    for (int k = gl; k < g.nch; k += LANES) facc[k] = 0;
+    for (int it = 0; it < I; it++) {
+      int lo, hi;
+      tdsc_keep_warp(S, Q, T, rcpT, cut.k2, lo, hi);
+      const ByteKeep kp = make_keep(lo, hi);
+      for (int k = gl; k < g.nch; k += LANES) {
+        const uint4 w = st[k];
+        const uint4 vm = (k == 0 || k == g.nch - 1) ? chunk_valid(g, k) : make_uint4(~0u, ~0u, ~0u, ~0u);
+        const uint4 f = make_uint4(outside_exact(w.x, kp) & vm.x, outside_exact(w.y, kp) & vm.y,
+                                   outside_exact(w.z, kp) & vm.z, outside_exact(w.w, kp) & vm.w);
+        fcur[k] = (uint16_t)chunk_bits16(f);
+      }
+      grp_sync<LANES>();
+      long long dS = 0, dQ = 0;
+      for (int k = gl; k < g.nch; k += LANES) {
+        const uint32_t fb = fcur[k];
+        if (!fb) continue;
+        uint4 w = st[k];
+        uint32_t rem = fb;
+        while (rem) {
+          const int b = __ffs(rem) - 1;
+          rem &= rem - 1;
+          const int t = 16 * k + b - g.head;
+          const uint32_t old = (word_of(w, b >> 2) >> (8 * (b & 3))) & 0xFFu;
+          uint32_t nv = old;
+          for (int a = 0; a < DRAW_ATTEMPTS; a++) {
+            const unsigned u = draw_pos(key, t, 1, it, a, (unsigned)T);
+            const unsigned pu = (unsigned)g.head + u;
+            if (!((fcur[pu >> 4] >> (pu & 15)) & 1u)) {
+              nv = sb[u];
+              break;
+            }
+          }
+          const uint32_t sh = 8 * (b & 3), msk = 0xFFu << sh;
+          if (b < 4) w.x = (w.x & ~msk) | (nv << sh);
+          else if (b < 8) w.y = (w.y & ~msk) | (nv << sh);
+          else if (b < 12) w.z = (w.z & ~msk) | (nv << sh);
+          else w.w = (w.w & ~msk) | (nv << sh);
+          dS += (long long)nv - (long long)old;
+          dQ += (long long)(nv * nv) - (long long)(old * old);
+        }
+        st[k] = w;
+        facc[k] |= (uint16_t)fb;
+      }
+      unsigned long long d[2] = {(unsigned long long)dS, (unsigned long long)dQ};
+      grp_sum<LANES, 2>(d, scr);  // (the CTA variant's barriers also publish the new row)
+      if (LANES == 32) __syncwarp();
+      S += d[0];
+      Q += d[1];
+    }
   } else {
     for (int it = 0; it < I; it++) {
       int lo, hi;
@@ -575,7 +634,13 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
       const bool edge = (k == 0 || k == g.nch - 1);
       const uint4 vm = (edge && !single) ? chunk_valid(g, k) : make_uint4(~0u, ~0u, ~0u, ~0u);
       uint4 y, f;
-      if (single) {
+      if (random) {
+        // the row already holds the output; the flags were kept per chunk
+        y = w;
+        const uint32_t a = reinterpret_cast<const uint16_t*>(st + g.nch)[g.nch + k];
+        f = make_uint4(bytes_from_bits4(a) << 7, bytes_from_bits4(a >> 4) << 7, bytes_from_bits4(a >> 8) << 7,
+                       bytes_from_bits4(a >> 12) << 7);
+      } else if (single) {
         // padding bytes of edge chunks are never stored and their flag bits fall
         // outside the row's mask words, so no masking is needed here
         f = outside4(w, kk);
@@ -672,6 +737,7 @@ struct FdLayout {
   unsigned* fmask;        // C: FDSC flag bits of the item (bit = t - t_item)
   unsigned* list;         // ws x nb flagged (t, bin) pairs, one segment per warp
   unsigned* cnt;          // per-warp list lengths
+  unsigned* fcur;         // C (random replacement only): flags of the iteration in progress (bit = tile row)
 };
 
 __device__ __forceinline__ FdLayout fd_layout(unsigned char* smem, int ws, int pitch, int nb, int C) {
@@ -695,6 +761,8 @@ __device__ __forceinline__ FdLayout fd_layout(unsigned char* smem, int ws, int p
   L.list = reinterpret_cast<unsigned*>(p);
   p += align16i(ws * nb * 4);
   L.cnt = reinterpret_cast<unsigned*>(p);
+  p += 4 * (NT / 32);
+  L.fcur = reinterpret_cast<unsigned*>(p);
   return L;
 }
 
@@ -957,7 +1025,10 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
   const unsigned long long multF = (unsigned long long)C * mf * mf;
   const unsigned long long multL = (unsigned long long)C * ml * ml;
 
+  const bool rnd = cut.replace == REP_RANDOM;
   for (int c = threadIdx.x; c < C; c += NT) L.fmask[c] = 0;
+  if (rnd)
+    for (int c = threadIdx.x; c < C; c += NT) L.fcur[c] = 0;  // each bin clears its own bits after use
 
   for (int t0 = t_item; t0 < t_end; t0 += Ws) {
     const int ws = min(Ws, t_end - t0);
@@ -1127,6 +1198,58 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
         const unsigned gsz = lastbin ? (unsigned)Gl : (unsigned)G;
         const unsigned bit = 1u << (t0 + t - t_item);
         const unsigned long long mm = lastbin ? ml : mf;
+        if (rnd) {
+          // Random replacement: the bin's flags of this iteration go to fcur
+          // first, so each draw tests the flag of the value it would copy
+          // (unflagged values are never written in this iteration).
+          const unsigned s_old = L.Sg[t * NBP + gi], q_old = L.Qg[t * NBP + gi];
+          const unsigned A = L.A[2 * t + (lastbin ? 1 : 0)];
+          int lo, hi;
+          if (fast32 && gsz == 32) {
+            lo = s_old <= A ? 0 : (int)((s_old - A + 31) >> 5);
+            const unsigned hv = (s_old + A) >> 5;
+            hi = hv > 255 ? 255 : (int)hv;
+          } else {
+            keep_from(s_old, A, gsz, lastbin ? rcpL : rcpG, lo, hi);
+          }
+          const int c0 = gi * G;
+          const BinView bv{L.tile, t, c0, (int)gsz, pitch};
+          const unsigned tb = 1u << t;
+          for (unsigned i = 0; i < gsz; i++) {
+            const int x = bv.byte(i);
+            if (x < lo || x > hi) {
+              atomicOr(&L.fcur[c0 + i], tb);
+              atomicOr(&L.fmask[c0 + i], bit);
+            }
+          }
+          const unsigned long long key = draw_key(J.beam, t0 + t);
+          unsigned s_new = s_old, q_new = q_old;
+          for (unsigned i = 0; i < gsz; i++) {
+            if (!(L.fcur[c0 + i] & tb)) continue;
+            const unsigned x = bv.byte(i);
+            unsigned y = x;
+            for (int a = 0; a < DRAW_ATTEMPTS; a++) {
+              const unsigned u = draw_pos(key, c0 + (int)i, 2, it, a, gsz);
+              if (!(L.fcur[c0 + u] & tb)) {
+                y = bv.byte(u);
+                break;
+              }
+            }
+            if (y != x) {
+              bv.byte(i) = (uint8_t)y;
+              s_new += y - x;
+              q_new += y * y - x * x;
+            }
+          }
+          for (unsigned i = 0; i < gsz; i++)
+            if (L.fcur[c0 + i] & tb) atomicAnd(&L.fcur[c0 + i], ~tb);
+          if (s_new != s_old || q_new != q_old) {
+            L.Sg[t * NBP + gi] = s_new;
+            L.Qg[t * NBP + gi] = q_new;
+            atomicAdd(&L.V[t], fd_contrib(mm, gsz, s_new, q_new) - fd_contrib(mm, gsz, s_old, q_old));
+          }
+          continue;
+        }
         if (fast32 && gsz == 32) {
           // the bin in registers: two 16-byte loads, half order staggered by lane
           uint32_t w[8];
@@ -1405,7 +1528,7 @@ int engine_smem_u8(const Params& p) {
       s = s > td ? s : td;
     }
     if (p.fd.iterations > 0) {
-      const int fd = fd_smem_bytes(J.ws, J.pitch, J.nb, J.C);
+      const int fd = fd_smem_bytes(J.ws, J.pitch, J.nb, J.C, p.fd.replace == REP_RANDOM);
       s = s > fd ? s : fd;
     }
   }

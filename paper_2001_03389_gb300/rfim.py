@@ -24,13 +24,13 @@ _lib = ctypes.CDLL(LIB_PATH)
 OK, ERR_ARG, ERR_RANGE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BUSY, ERR_STATE = range(8)
 U8, F32 = 0, 1
 LAYOUT_BCT, LAYOUT_BTC = 0, 1
-REPLACE_MEAN, REPLACE_MEDIAN = 0, 1
+REPLACE_MEAN, REPLACE_MEDIAN, REPLACE_RANDOM = 0, 1, 2
 MASK_NONE, MASK_BITS, MASK_BYTES = 0, 1, 2
 BATCH_GRAPH, BATCH_AUTOTUNE = 1, 2
 RFIM_NOALLOC_MAX_BEAMS = 160
 
 _LAYOUTS = {"bct": LAYOUT_BCT, "btc": LAYOUT_BTC}
-_REPLACE = {"mean": REPLACE_MEAN, "median": REPLACE_MEDIAN}
+_REPLACE = {"mean": REPLACE_MEAN, "median": REPLACE_MEDIAN, "random": REPLACE_RANDOM}
 _MASKS = {None: MASK_NONE, "none": MASK_NONE, "bits": MASK_BITS, "bytes": MASK_BYTES}
 
 
