@@ -144,7 +144,7 @@ __host__ __device__ inline int fd32_smem_bytes(int ws, int C, int nb, bool rnd =
          align16i(ws * 4) * 3 + (rnd ? align16i(C * 4) : 0);
 }
 int engine_smem_f32(const Params& p);
-void* engine_kernel_f32();
+void* engine_kernel_f32(const Params& p);
 int launch_engine_f32(const Params& p, const LaunchCfg& cfg, void* stream);
 
 // layout conversion (transpose.cu): out[b][c][r] = in[b][r][c] for rows x cols
@@ -153,7 +153,7 @@ int launch_transpose(const void* in, void* out, int batch, int rows, int cols, i
 int launch_transpose_bits(const void* in_bct, void* out_btc, int batch, int C, int T, void* stream);
 
 inline int engine_smem(const Params& p) { return p.dtype ? engine_smem_f32(p) : engine_smem_u8(p); }
-inline void* engine_kernel(const Params& p) { return p.dtype ? engine_kernel_f32() : engine_kernel_u8(p); }
+inline void* engine_kernel(const Params& p) { return p.dtype ? engine_kernel_f32(p) : engine_kernel_u8(p); }
 inline int launch_engine(const Params& p, const LaunchCfg& cfg, void* stream) {
   return p.dtype ? launch_engine_f32(p, cfg, stream) : launch_engine_u8(p, cfg, stream);
 }

@@ -328,7 +328,7 @@ __device__ float row_median_f32(const float4* st, int nch, int head, int tail, i
 }
 
 // GN threads clean the row: t = thread in the group, h = group (its barrier is 1 + h)
-template <int GN>
+template <int GN, bool RND>
 __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned char* smem, Red32* red, int t, int h) {
   const CutDev& cut = P.td;
   const int T = J.T;
@@ -396,9 +396,9 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
   };
   __shared__ RowStat rs_g[2];
   RowStat* rs_ = &rs_g[h];
-  const double Tn = (double)T, rT = 1.0 / (double)T;
+  const double rT = 1.0 / (double)T;
   const int I = cut.iterations;
-  const bool rnd = cut.replace == REP_RANDOM;
+  const bool rnd = RND && cut.replace == REP_RANDOM;  // (RND: the kernel build that holds random replacement)
 
   for (int it = 0; it < I; it++) {
     // statistics of the current values, finished in double by one thread
@@ -655,6 +655,7 @@ __device__ float bin_median_f32(const float* tile, int c0, int n, int ws, int t)
   return key_f(prefix);
 }
 
+template <bool RND>
 __device__ void fdsc_item_f32(const Params& P, const Job& J, int item, unsigned char* smem, Red32* red) {
   const CutDev& cut = P.fd;
   const int C = J.C, T = J.T, G = cut.bin, NB = J.nb, Gl = J.last_g;
@@ -666,9 +667,9 @@ __device__ void fdsc_item_f32(const Params& P, const Job& J, int item, unsigned 
   const Fd32Layout L = fd32_layout(smem, Ws, C, NB);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool vec = ((((uintptr_t)src) | ((uintptr_t)dst)) & 15) == 0 && (T & 3) == 0;
-  const double Cn = (double)C, rC = 1.0 / (double)C;
+  const double rC = 1.0 / (double)C;
 
-  const bool rnd = cut.replace == REP_RANDOM;
+  const bool rnd = RND && cut.replace == REP_RANDOM;
   for (int c = threadIdx.x; c < C; c += NT) L.fm[c] = 0;
   if (rnd)
     for (int c = threadIdx.x; c < C; c += NT) L.fcur[c] = 0;  // each unit clears its own bits after use
@@ -960,6 +961,9 @@ __device__ bool wait_rows_f32(const Params& P, int job, unsigned need, int* flag
   return ok;
 }
 
+// RND: random replacement is compiled in (a separate build, so that the mean
+// and median paths carry none of it)
+template <bool RND>
 __global__ void __launch_bounds__(NT, 2) k_engine_f32(const __grid_constant__ Params P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Red32 red[2];
@@ -985,10 +989,10 @@ __global__ void __launch_bounds__(NT, 2) k_engine_f32(const __grid_constant__ Pa
         // two rows per item, one per half CTA (each half synchronises on its own barrier)
         const int h = threadIdx.x / (NT / 2), t = threadIdx.x % (NT / 2);
         const int row = 2 * idx + h;
-        if (row < J.rows) tdsc_row_f32<NT / 2>(P, J, row, smem + h * td32_smem_bytes(J.T), &red[h], t, h);
+        if (row < J.rows) tdsc_row_f32<NT / 2, RND>(P, J, row, smem + h * td32_smem_bytes(J.T), &red[h], t, h);
         done = (unsigned)min(2, J.rows - 2 * idx);
       } else {
-        tdsc_row_f32<NT>(P, J, idx, smem, &red[0], threadIdx.x, 0);
+        tdsc_row_f32<NT, RND>(P, J, idx, smem, &red[0], threadIdx.x, 0);
       }
       __syncthreads();
       if (threadIdx.x == 0) {
@@ -997,7 +1001,7 @@ __global__ void __launch_bounds__(NT, 2) k_engine_f32(const __grid_constant__ Pa
       }
     } else {
       if (P.wait_tdsc && !wait_rows_f32(P, sg.job, (unsigned)J.rows, &s_flag)) continue;
-      fdsc_item_f32(P, J, idx, smem, &red[0]);
+      fdsc_item_f32<RND>(P, J, idx, smem, &red[0]);
     }
   }
 }
@@ -1018,11 +1022,16 @@ int engine_smem_f32(const Params& p) {
   return s;
 }
 
-void* engine_kernel_f32() { return reinterpret_cast<void*>(&k_engine_f32); }
+void* engine_kernel_f32(const Params& p) {
+  const bool rnd = (p.td.iterations > 0 && p.td.replace == REP_RANDOM) ||
+                   (p.fd.iterations > 0 && p.fd.replace == REP_RANDOM);
+  return rnd ? reinterpret_cast<void*>(&k_engine_f32<true>) : reinterpret_cast<void*>(&k_engine_f32<false>);
+}
 
 int launch_engine_f32(const Params& p, const LaunchCfg& cfg, void* stream) {
-  k_engine_f32<<<cfg.grid, NT, cfg.smem, (cudaStream_t)stream>>>(p);
-  return (int)cudaGetLastError();
+  void* args[] = {const_cast<Params*>(&p)};
+  return (int)cudaLaunchKernel(engine_kernel_f32(p), dim3(cfg.grid), dim3(NT), args, (size_t)cfg.smem,
+                               (cudaStream_t)stream);
 }
 
 }  // namespace rfim

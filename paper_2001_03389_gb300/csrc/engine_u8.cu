@@ -412,7 +412,7 @@ __device__ __forceinline__ void td_stats_pass(const uint4* st, int nch, int gl, 
   }
 }
 
-template <int LANES>
+template <int LANES, bool RND>
 __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, unsigned long long* scr, int gl) {
   const CutDev& cut = P.td;
   const int T = J.T;
@@ -465,7 +465,7 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
   // single: every flagged sample ends at one value (the median, or the mean of a
   // one-iteration cut), so one keep interval (the intersection) decides everything
   const bool median = cut.replace == REP_MEDIAN;
-  const bool random = cut.replace == REP_RANDOM;
+  const bool random = RND && cut.replace == REP_RANDOM;  // (RND: the kernel build that holds random replacement)
   const bool single = !random && (median || cut.iterations == 1);
   const unsigned long long npad = 16ull * (unsigned)g.nch - (unsigned)T;  // zero bytes in the chunk grid
   const int I = cut.iterations;
@@ -997,6 +997,7 @@ __device__ __forceinline__ void store4_row(uint8_t* a, uint32_t w, int n) {
   for (int b = 0; b < n; b++) a[b] = (uint8_t)(w >> (8 * b));
 }
 
+template <bool RND>
 __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned char* smem) {
   const CutDev& cut = P.fd;
   const int C = J.C, T = J.T, G = cut.bin, NB = J.nb, Gl = J.last_g;
@@ -1025,7 +1026,7 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
   const unsigned long long multF = (unsigned long long)C * mf * mf;
   const unsigned long long multL = (unsigned long long)C * ml * ml;
 
-  const bool rnd = cut.replace == REP_RANDOM;
+  const bool rnd = RND && cut.replace == REP_RANDOM;
   for (int c = threadIdx.x; c < C; c += NT) L.fmask[c] = 0;
   if (rnd)
     for (int c = threadIdx.x; c < C; c += NT) L.fcur[c] = 0;  // each bin clears its own bits after use
@@ -1476,8 +1477,9 @@ __device__ __forceinline__ int seg_of(const Params& P, int item) {
 }
 
 // MINB = CTAs per SM the register allocation targets (the TDSC row stage is
-// 102 KB, so two CTAs share an SM).
-template <int MINB>
+// 102 KB, so two CTAs share an SM).  RND: random replacement is compiled in
+// (a separate build, so that the mean and median paths carry none of it).
+template <int MINB, bool RND>
 __global__ void __launch_bounds__(NT, MINB) k_engine_u8(const __grid_constant__ Params P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long scr[GRP_SUM_MAX * (NT / 32)];
@@ -1497,11 +1499,11 @@ __global__ void __launch_bounds__(NT, MINB) k_engine_u8(const __grid_constant__ 
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         const int row = idx * TD_ROWS_PER_ITEM + warp;
         if (row < J.rows)
-          tdsc_row_u8<32>(P, J, row, reinterpret_cast<uint4*>(smem + warp * TD_WARP_STAGE), scr, lane);
+          tdsc_row_u8<32, RND>(P, J, row, reinterpret_cast<uint4*>(smem + warp * TD_WARP_STAGE), scr, lane);
         const int left = J.rows - idx * TD_ROWS_PER_ITEM;
         done = (unsigned)(left < TD_ROWS_PER_ITEM ? left : TD_ROWS_PER_ITEM);
       } else {
-        tdsc_row_u8<NT>(P, J, idx, reinterpret_cast<uint4*>(smem), scr, threadIdx.x);
+        tdsc_row_u8<NT, RND>(P, J, idx, reinterpret_cast<uint4*>(smem), scr, threadIdx.x);
         done = 1;
       }
       __syncthreads();
@@ -1511,7 +1513,7 @@ __global__ void __launch_bounds__(NT, MINB) k_engine_u8(const __grid_constant__ 
       }
     } else {
       if (P.wait_tdsc && !wait_rows(P, sg.job, (unsigned)J.rows, &s_flag)) continue;
-      fdsc_item_u8(P, J, idx, smem);
+      fdsc_item_u8<RND>(P, J, idx, smem);
     }
   }
 }
@@ -1536,8 +1538,9 @@ int engine_smem_u8(const Params& p) {
 }
 
 void* engine_kernel_u8(const Params& p) {
-  (void)p;
-  return (void*)k_engine_u8<2>;
+  const bool rnd = (p.td.iterations > 0 && p.td.replace == REP_RANDOM) ||
+                   (p.fd.iterations > 0 && p.fd.replace == REP_RANDOM);
+  return rnd ? (void*)k_engine_u8<2, true> : (void*)k_engine_u8<2, false>;
 }
 
 int launch_engine_u8(const Params& p, const LaunchCfg& cfg, void* stream) {
