@@ -306,6 +306,8 @@ CutDev cut_dev(const CutNorm& c) {
   if (c.on) {
     d.k2 = make_k2(c.k);
     d.k = c.k;
+    d.k_hi = (float)c.k;
+    d.k_lo = (float)(c.k - (double)d.k_hi);
     d.iterations = c.it;
     d.replace = c.rep;
     d.bin = c.bin;

@@ -19,6 +19,7 @@ enum MaskKind { MASK_NONE = 0, MASK_BITS = 1, MASK_BYTES = 2 };
 struct CutDev {
   ExactK2 k2;      // uint8: exact form of fl(k*k)
   double k;        // float32 path
+  float k_hi, k_lo;  // float32 path: k as float-float (k_hi + k_lo = k to ~2^-48)
   int iterations;  // 0 = method disabled
   int replace;     // ReplaceKind
   int bin;         // FDSC channels per bin
@@ -141,7 +142,7 @@ __host__ __device__ inline int td32_smem_bytes(int T) {
 __host__ __device__ inline int fd32_smem_bytes(int ws, int C, int nb, bool rnd = false) {
   const int U = ws * nb;
   return align16i(ws * C * 4) + align16i(C * 4) + align16i(U * 8) * 2 + align16i(U * 4) + align16i(ws * 8) +
-         align16i(ws * 4) * 3 + (rnd ? align16i(C * 4) : 0);
+         align16i(ws * 4) * 2 + (rnd ? align16i(C * 4) : 0);
 }
 int engine_smem_f32(const Params& p);
 void* engine_kernel_f32(const Params& p);

@@ -10,7 +10,9 @@
 // instruction costs ~20 SM cycles on this part.  So:
 //  - sums and sums of squares are accumulated per thread in float-float
 //    (TwoSum compensation, exact products by FMA) and merged in float-float;
-//    only the per-row / per-column finish (mean, variance, sqrt) is FP64;
+//  - the finish (mean, variance, sqrt, k sigma) is float-float too (~2^-46
+//    relative), computed by every thread of the row from the same merged sums,
+//    so no thread waits for another to broadcast it;
 //  - the variance is Q/n - mu^2 from those sums; when that cancels badly
 //    (mu^2 > 1000 sigma^2) the row or column is redone with an FP64 two-pass;
 //  - each sample is decided in FP32 against bounds widened by 2^-20 (and by
@@ -96,6 +98,28 @@ __device__ __forceinline__ FF ff_div_int(FF a, int g) {
 
 __device__ __forceinline__ double ff_d(FF a) { return (double)a.hi + (double)a.lo; }
 
+// a double as float-float (~2^-48 relative)
+__device__ __forceinline__ FF ff_from_d(double v) {
+  const float hi = __double2float_rn(v);
+  return FF{hi, __double2float_rn(v - (double)hi)};
+}
+
+// sqrt of a float-float v >= 0 (0 otherwise): the float32 root refined by one
+// Newton step, s = s0 + (v - s0^2) / (2 s0), with s0^2 formed exactly by FMA.
+__device__ __forceinline__ FF ff_sqrt(FF v) {
+  if (!(v.hi > 0.f)) return FF{0.f, 0.f};
+  const float s0 = __fsqrt_rn(v.hi);
+  const float p = __fmul_rn(s0, s0);
+  const float pe = __fmaf_rn(s0, s0, -p);  // s0^2 = p + pe
+  // v - s0^2: v.hi - p is exact (the two are within a rounding of each other)
+  const float r = __fadd_rn(__fsub_rn(__fsub_rn(v.hi, p), pe), v.lo);
+  const float c = __fdiv_rn(r, __fmul_rn(2.f, s0));
+  FF o;
+  o.hi = __fadd_rn(s0, c);
+  o.lo = __fsub_rn(c, __fsub_rn(o.hi, s0));
+  return o;
+}
+
 __device__ __forceinline__ FF shfl_ff(FF a, int o) {
   return FF{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
 }
@@ -127,7 +151,7 @@ __device__ __forceinline__ double sqrt_fast(double v) {
 // doubles are read only inside the band: mu = mu_hi + mu_lo (exact), thr at *thr.
 struct Cut32 {
   float mu_f, mu_lo, lo_f, hi_f;
-  const double* thr;
+  float thr_hi, thr_lo;  // thr as float-float
 };
 
 // thr and the rounding error dm = |mu - mu_f| (both >= 0) -> float32 bounds.
@@ -143,16 +167,28 @@ __device__ __forceinline__ void band_bounds_f(float thr_lo, float thr_hi, float 
 }
 
 // The double expression, kept out of line so that it runs only inside the band.
-__device__ __noinline__ bool flag64(float y, float mu_hi, float mu_lo, const double* thr) {
+__device__ __noinline__ bool flag64(float y, float mu_hi, float mu_lo, float thr_hi, float thr_lo) {
   const double mu = (double)mu_hi + (double)mu_lo;
-  return fabs((double)y - mu) > *thr;
+  return fabs((double)y - mu) > (double)thr_hi + (double)thr_lo;
 }
 
 __device__ __forceinline__ bool flag32(float y, const Cut32& c) {
   const float a = fabsf(__fsub_rn(y, c.mu_f));
   if (a > c.hi_f) return true;
   if (!(a > c.lo_f)) return false;
-  return flag64(y, c.mu_f, c.mu_lo, c.thr);
+  return flag64(y, c.mu_f, c.mu_lo, c.thr_hi, c.thr_lo);
+}
+
+// The cut of mean mu and threshold thr (float-float, mu normalised so that
+// |mu - mu.hi| = |mu.lo|).
+__device__ __forceinline__ Cut32 make_cut32(FF mu, FF thr) {
+  Cut32 c;
+  c.mu_f = mu.hi;
+  c.mu_lo = mu.lo;
+  c.thr_hi = thr.hi;
+  c.thr_lo = thr.lo;
+  band_bounds_f(__fadd_rd(thr.hi, thr.lo), __fadd_ru(thr.hi, thr.lo), fabsf(mu.lo), c.lo_f, c.hi_f);
+  return c;
 }
 
 // Total order of floats as unsigned keys (-0 before +0).
@@ -346,8 +382,12 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
   float4* st = reinterpret_cast<float4*>(smem);
   unsigned char* fl4 = smem + 16 * nch;
   float* lst = reinterpret_cast<float*>(smem + 16 * nch + align16i(nch));
-  __shared__ int s_nlist_g[2];
-  int& s_nlist = s_nlist_g[h];
+  __shared__ int s_cnt_g[2][2];  // per group: replaced-value counts of alternate iterations
+  int* s_cnt = s_cnt_g[h];
+  if (t == 0) {  // (published by the staging barrier)
+    s_cnt[0] = 0;
+    s_cnt[1] = 0;
+  }
 
   // ---- stage the row (edge chunks through guarded loads, padding zeroed)
   for (int k = t; k < nch; k += GN) {
@@ -382,42 +422,27 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
     ff_acc_sq(Q, v.w);
   }
   grp_ff2<GN>(S, Q, red, t, h);
-  // running sums of the current values (used by thread 0 only)
-  double Sd = 0.0, Qd = 0.0;
-  if (t == 0) {
-    Sd = ff_d(S);
-    Qd = ff_d(Q);
-  }
-  struct RowStat {
-    double mu_thr[2];
-    double var;
-    float mu_f, mu_lo, lo_f, hi_f;
-    int prec;
-  };
-  __shared__ RowStat rs_g[2];
-  RowStat* rs_ = &rs_g[h];
+  // S, Q: running sums of the current values, the same in every thread of the
+  // group (the merges above add in the same order everywhere)
   const double rT = 1.0 / (double)T;
+  const FF kff{cut.k_hi, cut.k_lo};
   const int I = cut.iterations;
   const bool rnd = RND && cut.replace == REP_RANDOM;  // (RND: the kernel build that holds random replacement)
 
   for (int it = 0; it < I; it++) {
-    // statistics of the current values, finished in double by one thread
-    if (t == 0) {
-      const double mu = Sd * rT;
-      const double var = Qd * rT - mu * mu;
-      rs_->prec = !(var >= 1e-3 * (Qd * rT));
-      rs_->var = var;
-    }
-    gsync<GN>(h);
-    if (rs_->prec) {
+    // statistics of the current values, finished in float-float by every thread
+    FF mu = ff_div_int(S, T);
+    const FF mq = ff_div_int(Q, T);
+    FF var = ff_add(mq, ff_neg(ff_mul(mu, mu)));
+    if (!(var.hi >= 1e-3f * mq.hi)) {  // (the same in every thread)
       // cancellation (or a constant row): FP64 two-pass over the current values
-      double s = 0.0;
+      double sd = 0.0;
       for (int k = t; k < nch; k += GN) {
         const float4 v = st[k];
-        s += ((double)v.x + (double)v.y) + ((double)v.z + (double)v.w);  // padding is 0
+        sd += ((double)v.x + (double)v.y) + ((double)v.z + (double)v.w);  // padding is 0
       }
-      s = grp_dsum<GN>(s, red, t, h);
-      const double m2 = s * rT;
+      sd = grp_dsum<GN>(sd, red, t, h);
+      const double m2 = sd * rT;
       double ss = 0.0;
       for (int k = t; k < nch; k += GN) {
         const float4 v = st[k];
@@ -430,36 +455,16 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
           }
       }
       ss = grp_dsum<GN>(ss, red, t, h);
-      if (t == 0) {
-        rs_->var = ss * rT;
-        Sd = s;  // the two-pass mean
-      }
+      mu = ff_from_d(m2);
+      var = ff_from_d(ss * rT);
+      S = ff_from_d(sd);  // the two-pass sum carries on
     }
-    if (t == 0) {
-      const double mu = Sd * rT;
-      const double var = rs_->var;
-      const double thr = cut.k * sqrt_fast(var);
-      rs_->mu_thr[0] = mu;
-      rs_->mu_thr[1] = thr;
-      const float mu_f = __double2float_rn(mu);
-      rs_->mu_f = mu_f;
-      rs_->mu_lo = __double2float_rn(mu - (double)mu_f);
-      const double dm = fabs(mu - (double)mu_f);
-      rs_->hi_f = __double2float_ru((thr + dm) * (1.0 + 0x1p-20));
-      rs_->lo_f = __double2float_rd((thr - dm) * (1.0 - 0x1p-20));
-    }
-    gsync<GN>(h);
-    Cut32 c;
-    c.mu_f = rs_->mu_f;
-    c.mu_lo = rs_->mu_lo;
-    c.lo_f = rs_->lo_f;
-    c.hi_f = rs_->hi_f;
-    c.thr = &rs_->mu_thr[1];
+    const Cut32 c = make_cut32(mu, ff_mul(kff, ff_sqrt(var)));
     const float r = cut.replace == REP_MEDIAN ? row_median_f32<GN>(st, nch, head, tail, T, red, t, h) : c.mu_f;
 
-    // decide and replace; the replaced values go to a list for the statistics update
-    if (t == 0) s_nlist = 0;
-    gsync<GN>(h);
+    // decide and replace; the replaced values go to a list for the statistics
+    // update (its length counter was zeroed before the last barrier)
+    int& s_nlist = s_cnt[it & 1];
     if (rnd) {
       // random replacement: this iteration's flags first (high nibble of fl4),
       // then each flagged sample copies the first drawn sample that is unflagged
@@ -516,6 +521,7 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
       }
     }
     if (it == I - 1) break;
+    if (t == 0) s_cnt[(it + 1) & 1] = 0;  // the next iteration's counter (last read before the previous merge)
     gsync<GN>(h);
     // statistics of the next iteration: S' = S - sum(replaced) + nf r (same for Q)
     const int nflag = rnd ? TD32_LIST + 1 : s_nlist;  // random: the replaced-with values vary, sum the row again
@@ -526,11 +532,11 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
         ff_acc_sq(rq, lst[i]);
       }
       grp_ff2<GN>(rs, rq, red, t, h);
-      if (t == 0) {
-        const double rd = (double)r;
-        Sd = Sd - ff_d(rs) + (double)nflag * rd;
-        Qd = Qd - ff_d(rq) + (double)nflag * rd * rd;
-      }
+      const float nf = (float)nflag;  // exact (nflag < 2^24)
+      const float pr = __fmul_rn(nf, r);
+      const float r2 = __fmul_rn(r, r);
+      S = ff_add(ff_add(S, ff_neg(rs)), FF{pr, __fmaf_rn(nf, r, -pr)});
+      Q = ff_add(ff_add(Q, ff_neg(rq)), ff_mul(FF{r2, __fmaf_rn(r, r, -r2)}, FF{nf, 0.f}));
     } else {
       // many replacements: sum the current row again
       for (int k = t; k < nch; k += GN) {
@@ -545,10 +551,8 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
         ff_acc_sq(rq, v.w);
       }
       grp_ff2<GN>(rs, rq, red, t, h);
-      if (t == 0) {
-        Sd = ff_d(rs);
-        Qd = ff_d(rq);
-      }
+      S = rs;
+      Q = rq;
     }
   }
   gsync<GN>(h);
@@ -609,10 +613,9 @@ struct Fd32Layout {
   float2* um;     // units: bin mean as float-float
   float2* uv;     // units: sum of squared deviations as float-float
   float* uq;      // units: sum of squares (cancellation check)
-  double* thr;    // ws: column thresholds k * sigma'
+  float2* thr;    // ws: column thresholds k * sigma' (float-float)
   float* thr_lo;  // ws
   float* thr_hi;  // ws
-  int* prec;      // ws: column needs the FP64 two-pass
   unsigned* fcur; // C (random replacement only): flags of the iteration in progress (bit = t - t0)
 };
 
@@ -630,13 +633,11 @@ __device__ __forceinline__ Fd32Layout fd32_layout(unsigned char* smem, int ws, i
   p += align16i(U * 8);
   L.uq = reinterpret_cast<float*>(p);
   p += align16i(U * 4);
-  L.thr = reinterpret_cast<double*>(p);
+  L.thr = reinterpret_cast<float2*>(p);
   p += align16i(ws * 8);
   L.thr_lo = reinterpret_cast<float*>(p);
   p += align16i(ws * 4);
   L.thr_hi = reinterpret_cast<float*>(p);
-  p += align16i(ws * 4);
-  L.prec = reinterpret_cast<int*>(p);
   p += align16i(ws * 4);
   L.fcur = reinterpret_cast<unsigned*>(p);
   return L;
@@ -665,6 +666,7 @@ __device__ void fdsc_item_f32(const Params& P, const Job& J, int item, unsigned 
   const float* src = static_cast<const float*>(P.fd_reads_out ? J.out : J.in);
   float* dst = static_cast<float*>(J.out);
   const Fd32Layout L = fd32_layout(smem, Ws, C, NB);
+  const FF kff{cut.k_hi, cut.k_lo};
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool vec = ((((uintptr_t)src) | ((uintptr_t)dst)) & 15) == 0 && (T & 3) == 0;
   const double rC = 1.0 / (double)C;
@@ -757,7 +759,9 @@ __device__ void fdsc_item_f32(const Params& P, const Job& J, int item, unsigned 
         L.uq[u] = q.hi;
       }
       __syncthreads();
-      // ---- per column: sigma' over all channels (mu' = 0: every bin's deviations sum to 0)
+      // ---- per column: sigma' over all channels (mu' = 0: every bin's deviations
+      //      sum to 0), finished in float-float; a column whose one-pass sums
+      //      cancel (mu^2 > 1000 sigma^2) takes the FP64 two-pass of the definition
       for (int t = warp; t < w; t += NT / 32) {
         FF v{0.f, 0.f};
         float qs = 0.f;
@@ -766,41 +770,32 @@ __device__ void fdsc_item_f32(const Params& P, const Job& J, int item, unsigned 
           v = ff_add(v, FF{a.x, a.y});
           qs += L.uq[g * w + t];
         }
-        v = warp_ff(v);
+        v = warp_ff(v);  // (the same in every lane)
         qs = warp_sum(qs);
+        FF thr;
+        if (v.hi >= 1e-3f * qs) {
+          thr = ff_mul(kff, ff_sqrt(ff_div_int(v, C)));
+        } else {
+          double sd = 0.0;
+          for (int c = lane; c < C; c += 32) {
+            const float2 m = L.um[(c / G) * w + t];
+            sd += (double)L.tile[c * Ws + t] - ((double)m.x + (double)m.y);
+          }
+          sd = warp_sum(sd);
+          const double mup = sd * rC;
+          double ss = 0.0;
+          for (int c = lane; c < C; c += 32) {
+            const float2 m = L.um[(c / G) * w + t];
+            const double e = ((double)L.tile[c * Ws + t] - ((double)m.x + (double)m.y)) - mup;
+            ss += e * e;
+          }
+          ss = warp_sum(ss);
+          thr = ff_from_d(cut.k * sqrt_fast(ss * rC));
+        }
         if (lane == 0) {
-          const double V = ff_d(v);
-          const int prec = !(V >= 1e-3 * (double)qs);
-          L.prec[t] = prec;
-          const double thr = cut.k * sqrt_fast(V * rC);
-          L.thr[t] = thr;
-          L.thr_lo[t] = __double2float_rd(thr);
-          L.thr_hi[t] = __double2float_ru(thr);
-        }
-      }
-      __syncthreads();
-      // ---- cancellation: the column's FP64 two-pass of the definition
-      for (int t = warp; t < w; t += NT / 32) {
-        if (!L.prec[t]) continue;
-        double sd = 0.0;
-        for (int c = lane; c < C; c += 32) {
-          const float2 m = L.um[(c / G) * w + t];
-          sd += (double)L.tile[c * Ws + t] - ((double)m.x + (double)m.y);
-        }
-        sd = warp_sum(sd);
-        const double mup = sd * rC;
-        double ss = 0.0;
-        for (int c = lane; c < C; c += 32) {
-          const float2 m = L.um[(c / G) * w + t];
-          const double e = ((double)L.tile[c * Ws + t] - ((double)m.x + (double)m.y)) - mup;
-          ss += e * e;
-        }
-        ss = warp_sum(ss);
-        if (lane == 0) {
-          const double thr = cut.k * sqrt_fast(ss * rC);
-          L.thr[t] = thr;
-          L.thr_lo[t] = __double2float_rd(thr);
-          L.thr_hi[t] = __double2float_ru(thr);
+          L.thr[t] = make_float2(thr.hi, thr.lo);
+          L.thr_lo[t] = __fadd_rd(thr.hi, thr.lo);
+          L.thr_hi[t] = __fadd_ru(thr.hi, thr.lo);
         }
       }
       __syncthreads();
@@ -817,7 +812,8 @@ __device__ void fdsc_item_f32(const Params& P, const Job& J, int item, unsigned 
             const float2 m = L.um[g * 4 + t];
             cc[t].mu_f = m.x;
             cc[t].mu_lo = m.y;
-            cc[t].thr = &L.thr[t];
+            cc[t].thr_hi = L.thr[t].x;
+            cc[t].thr_lo = L.thr[t].y;
             band_bounds_f(L.thr_lo[t], L.thr_hi[t], fabsf(m.y), cc[t].lo_f, cc[t].hi_f);
           }
 #pragma unroll 2
@@ -843,7 +839,8 @@ __device__ void fdsc_item_f32(const Params& P, const Job& J, int item, unsigned 
         Cut32 cc;
         cc.mu_f = m.x;
         cc.mu_lo = m.y;
-        cc.thr = &L.thr[t];
+        cc.thr_hi = L.thr[t].x;
+        cc.thr_lo = L.thr[t].y;
         band_bounds_f(L.thr_lo[t], L.thr_hi[t], fabsf(m.y), cc.lo_f, cc.hi_f);
         const unsigned bit = 1u << (t0 + t - t_item);
         const int rot = g % n;
