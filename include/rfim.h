@@ -43,6 +43,11 @@
  *   - rfim_clean runs all TDSC iterations on every row, then all FDSC
  *     iterations on every column of the TDSC output.
  *
+ * Row lengths: uint8 TDSC takes rows up to 372,181 samples, where (255 T)^2
+ * reaches 2^53 (RFIM_ERR_RANGE beyond); rows longer than 98,273 samples do not
+ * fit the on-chip stage and are read from memory in every pass (slower, same
+ * results).  float32 TDSC takes rows up to 52,000 samples (RFIM_ERR_ARG beyond).
+ *
  * Conventions for every call below:
  *   - Pointers inside rfim_block are DEVICE pointers owned by the caller,
  *     except for rfim_clean_host.  `out == in` cleans in place; any other

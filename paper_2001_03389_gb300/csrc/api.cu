@@ -208,7 +208,7 @@ rfim_status check_impl(rfim_ctx* ctx, const rfim_block* b, const CutNorm& td, co
     return RFIM_OK;
   }
   if (td.on && td_row_mode(b->samples) < 0)
-    return fail(ctx, RFIM_ERR_ARG, "TDSC rows longer than 98273 samples are not available in this build");
+    return fail(ctx, RFIM_ERR_RANGE, "TDSC rows longer than %lld samples are not available", TD_MAX_T);
   if (td.on && td.rep == RFIM_REPLACE_RANDOM && td_random_row_mode(b->samples) < 0)
     return fail(ctx, RFIM_ERR_ARG, "uint8 TDSC with random replacement: rows longer than 78609 samples are not "
                 "available in this build");
@@ -267,7 +267,8 @@ Job make_job(const rfim_block* b, int j, const CutNorm& fd, int tile_samples, in
   J.pitch = fd_pitch(C * (int)es);
   J.ws = pick_ws_opt(tile_samples, C, J.nb, J.pitch, smem_target, fd.on && fd.rep == RFIM_REPLACE_RANDOM);
   J.fd_items = (T + FD_ITEM_T - 1) / FD_ITEM_T;
-  J.td_mode = td_row_mode(T) == 1 ? 1 : 0;
+  const int tm = td_row_mode(T);  // (-1 only with TDSC off: no TDSC items then)
+  J.td_mode = tm < 0 ? 1 : tm;
   J.td_items = J.td_mode == 0 ? (C + TD_ROWS_PER_ITEM - 1) / TD_ROWS_PER_ITEM : C;
   if (b->dtype == RFIM_F32) {
     // float32: one CTA per TDSC row; FDSC sub-slab of 8, 4, 2 or 1 samples

@@ -41,7 +41,8 @@ struct Job {
   int pitch;        // bytes per tile row (>= C * esize, pitch/4 = 1 mod 32)
   int fd_items;     // number of FDSC work items (ceil(T / 32))
   int rows;         // TDSC rows (C)
-  int td_mode;      // uint8: 0 = one warp per row, 8 rows per item; 1 = one row per item, whole CTA.
+  int td_mode;      // uint8: 0 = one warp per row, 8 rows per item; 1 = one row per item, whole CTA;
+                    //        2 = one row per item, whole CTA, row read from global memory (no stage).
                     // float32: 0 = two rows per item, a half CTA each; 1 = one row per item
   int td_items;     // number of TDSC work items
   int beam;         // index of the beam within its block (keys the random-replacement draws)
@@ -114,10 +115,15 @@ __host__ __device__ inline int td_random_row_mode(long long T) {
 }
 
 // Row mode for rows of T bytes: 0 = warp rows, 1 = CTA rows, -1 = too long.
+// TDSC rows longer than the CTA stage are read from global memory in every
+// pass (mode 2), up to the exactness bound of the uint8 decisions,
+// (255 T)^2 < 2^53.
+constexpr long long TD_MAX_T = 372181;
 inline int td_row_mode(long long T) {
   const long long nch = (T + 30) / 16 + 1;  // worst-case alignment of the row start
   if (nch <= TD_WARP_CHUNKS) return 0;
   if (nch <= TD_CTA_CHUNKS) return 1;
+  if (T <= TD_MAX_T) return 2;
   return -1;
 }
 

@@ -355,8 +355,8 @@ __device__ __forceinline__ void med_update(MedSearch& m, const unsigned long lon
   m.pts[3] = m.pts[2] + 1;
 }
 
-template <int LANES>
-__device__ unsigned med_finish(MedSearch& m, const uint4* st, int nch, int T, unsigned long long npad,
+template <int LANES, typename Rd>
+__device__ unsigned med_finish(MedSearch& m, const Rd& rd, int nch, int T, unsigned long long npad,
                                unsigned long long* scr, int gl) {
   while (m.lo < m.hi) {
     uint32_t p4[4];
@@ -364,7 +364,7 @@ __device__ unsigned med_finish(MedSearch& m, const uint4* st, int nch, int T, un
     for (int i = 0; i < 4; i++) p4[i] = med_probe4(m, i);
     unsigned f32[4] = {0, 0, 0, 0};
     for (int k = gl; k < nch; k += LANES) {
-      const uint4 w = st[k];
+      const uint4 w = rd(k);
 #pragma unroll
       for (int i = 0; i < 4; i++) {
         f32[i] = sad4(w.x, p4[i], f32[i]);
@@ -386,12 +386,12 @@ __device__ unsigned med_finish(MedSearch& m, const uint4* st, int nch, int T, un
 // kept samples, number of flagged samples and, with PROBE, the SAD sums of the
 // median probes.  Padding bytes of the edge chunks are 0; the caller corrects
 // the flagged count for them.
-template <int LANES, bool ODD, bool PROBE>
-__device__ __forceinline__ void td_stats_pass(const uint4* st, int nch, int gl, const ByteKeep& kp,
+template <int LANES, bool ODD, bool PROBE, typename Rd>
+__device__ __forceinline__ void td_stats_pass(const Rd& rd, int nch, int gl, const ByteKeep& kp,
                                               const uint32_t (&p4)[4], unsigned (&f32)[4], unsigned& s_in,
                                               unsigned long long& q_in, unsigned& n_out) {
   for (int k = gl; k < nch; k += LANES) {
-    const uint4 w = st[k];
+    const uint4 w = rd(k);
     if (PROBE) {
 #pragma unroll
       for (int i = 0; i < 4; i++) {
@@ -412,7 +412,10 @@ __device__ __forceinline__ void td_stats_pass(const uint4* st, int nch, int gl, 
   }
 }
 
-template <int LANES, bool RND>
+// STREAM: the row is longer than the shared-memory stage; every pass reads its
+// 16-byte chunks from global memory (L2) instead, edge chunks masked as the
+// staging would, and `st` only holds the output pass's flag words.
+template <int LANES, bool RND, bool STREAM = false>
 __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, unsigned long long* scr, int gl) {
   const CutDev& cut = P.td;
   const int T = J.T;
@@ -428,26 +431,36 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
   g.nch = (g.head + T + 15) >> 4;
   g.tail = g.head + T - ((g.nch - 1) << 4);
 
+  // chunk k of the row (edge chunks with their padding bytes zeroed)
+  auto rd = [&](int k) -> uint4 {
+    if (!STREAM) return st[k];
+    const uint8_t* a = g.cb + 16 * k;
+    if (k > 0 && k < g.nch - 1) return ld16_na(a);  // interior chunks lie inside the row
+    return and4(load16_guarded(a, blo, bhi), chunk_valid(g, k));
+  };
+
   // ---- pass 1: stage the row with asynchronous copies (every chunk in flight at
   //      once, no registers held), fix up the edge chunks, then S and Q
-  for (int k = gl; k < g.nch; k += LANES) {
-    const uint8_t* a = g.cb + 16 * k;
-    if (a >= blo && a + 16 <= bhi) {
-      const unsigned sdst = (unsigned)__cvta_generic_to_shared(st + k);
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sdst), "l"(a) : "memory");
-    } else {
-      st[k] = load16_guarded(a, blo, bhi);
+  if (!STREAM) {
+    for (int k = gl; k < g.nch; k += LANES) {
+      const uint8_t* a = g.cb + 16 * k;
+      if (a >= blo && a + 16 <= bhi) {
+        const unsigned sdst = (unsigned)__cvta_generic_to_shared(st + k);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sdst), "l"(a) : "memory");
+      } else {
+        st[k] = load16_guarded(a, blo, bhi);
+      }
     }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+    grp_sync<LANES>();
   }
-  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
-  grp_sync<LANES>();
   unsigned long long sq[2];
   {
     unsigned s = 0;
     unsigned long long q = 0;
     for (int k = gl; k < g.nch; k += LANES) {
-      uint4 w = st[k];
-      if (k == 0 || k == g.nch - 1) {
+      uint4 w = rd(k);
+      if (!STREAM && (k == 0 || k == g.nch - 1)) {
         w = and4(w, chunk_valid(g, k));
         st[k] = w;
       }
@@ -465,7 +478,7 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
   // single: every flagged sample ends at one value (the median, or the mean of a
   // one-iteration cut), so one keep interval (the intersection) decides everything
   const bool median = cut.replace == REP_MEDIAN;
-  const bool random = RND && cut.replace == REP_RANDOM;  // (RND: the kernel build that holds random replacement)
+  const bool random = RND && !STREAM && cut.replace == REP_RANDOM;  // (RND: the build that holds random replacement)
   const bool single = !random && (median || cut.iterations == 1);
   const unsigned long long npad = 16ull * (unsigned)g.nch - (unsigned)T;  // zero bytes in the chunk grid
   const int I = cut.iterations;
@@ -498,17 +511,17 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
       unsigned long long q_in = 0;
       if (kp.all) {
         // empty keep interval: every sample is flagged
-        if (probe) td_stats_pass<LANES, false, true>(st, g.nch, gl, make_keep(0, 255), p4, f32, s_in, q_in, n_out);
+        if (probe) td_stats_pass<LANES, false, true>(rd, g.nch, gl, make_keep(0, 255), p4, f32, s_in, q_in, n_out);
         s_in = 0;
         q_in = 0;
         n_out = (gl == 0) ? (unsigned)T : 0u;
       } else {
         if (kp.odd) {
-          if (probe) td_stats_pass<LANES, true, true>(st, g.nch, gl, kp, p4, f32, s_in, q_in, n_out);
-          else td_stats_pass<LANES, true, false>(st, g.nch, gl, kp, p4, f32, s_in, q_in, n_out);
+          if (probe) td_stats_pass<LANES, true, true>(rd, g.nch, gl, kp, p4, f32, s_in, q_in, n_out);
+          else td_stats_pass<LANES, true, false>(rd, g.nch, gl, kp, p4, f32, s_in, q_in, n_out);
         } else {
-          if (probe) td_stats_pass<LANES, false, true>(st, g.nch, gl, kp, p4, f32, s_in, q_in, n_out);
-          else td_stats_pass<LANES, false, false>(st, g.nch, gl, kp, p4, f32, s_in, q_in, n_out);
+          if (probe) td_stats_pass<LANES, false, true>(rd, g.nch, gl, kp, p4, f32, s_in, q_in, n_out);
+          else td_stats_pass<LANES, false, false>(rd, g.nch, gl, kp, p4, f32, s_in, q_in, n_out);
         }
       }
       unsigned long long red[7] = {s_in, q_in, n_out, f32[0], f32[1], f32[2], f32[3]};
@@ -519,13 +532,13 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
 #pragma unroll
         for (int i = 0; i < 4; i++) f[i] -= npad * (unsigned long long)(ms.pts[i] > 255 ? 255 : ms.pts[i]);
         med_update(ms, f, T);
-        r_med = med_finish<LANES>(ms, st, g.nch, T, npad, scr, gl);
+        r_med = med_finish<LANES>(ms, rd, g.nch, T, npad, scr, gl);
       }
       S = red[0] + red[2] * r_med;
       Q = red[1] + red[2] * r_med * r_med;
     }
     if (I == 1)
-      r_med = median ? med_finish<LANES>(ms, st, g.nch, T, npad, scr, gl)
+      r_med = median ? med_finish<LANES>(ms, rd, g.nch, T, npad, scr, gl)
                      : udiv_q((unsigned)(2 * S + (unsigned long long)T), 2u * (unsigned)T, rcp2T);
   } else if (random) {
     // Each iteration records its flags per chunk first (fcur), then replaces a
@@ -599,7 +612,7 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
       unsigned s2 = 0;
       unsigned long long q2 = 0;
       for (int k = gl; k < g.nch; k += LANES) {
-        const uint4 w = st[k];
+        const uint4 w = rd(k);
         const uint4 vm = (k == 0 || k == g.nch - 1) ? chunk_valid(g, k) : make_uint4(~0u, ~0u, ~0u, ~0u);
 #pragma unroll
         for (int i = 0; i < 4; i++) {
@@ -630,7 +643,7 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
   uint16_t* f16 = reinterpret_cast<uint16_t*>(st);  // flag bits of chunk k overwrite consumed staged bytes
   auto final_chunk = [&](const int k) -> uint32_t {
     uint32_t fb = 0;
-      const uint4 w = st[k];
+      const uint4 w = rd(k);
       const bool edge = (k == 0 || k == g.nch - 1);
       const uint4 vm = (edge && !single) ? chunk_valid(g, k) : make_uint4(~0u, ~0u, ~0u, ~0u);
       uint4 y, f;
@@ -1476,6 +1489,13 @@ __device__ __forceinline__ int seg_of(const Params& P, int item) {
   return lo;
 }
 
+// TDSC of one row longer than the shared-memory stage (the whole CTA, rows read
+// from global memory in every pass); out of line, as such rows are rare.
+__device__ __noinline__ void tdsc_row_u8_long(const Params& P, const Job& J, int row, uint4* st,
+                                              unsigned long long* scr) {
+  tdsc_row_u8<NT, false, true>(P, J, row, st, scr, threadIdx.x);
+}
+
 // MINB = CTAs per SM the register allocation targets (the TDSC row stage is
 // 102 KB, so two CTAs share an SM).  RND: random replacement is compiled in
 // (a separate build, so that the mean and median paths carry none of it).
@@ -1502,8 +1522,11 @@ __global__ void __launch_bounds__(NT, MINB) k_engine_u8(const __grid_constant__ 
           tdsc_row_u8<32, RND>(P, J, row, reinterpret_cast<uint4*>(smem + warp * TD_WARP_STAGE), scr, lane);
         const int left = J.rows - idx * TD_ROWS_PER_ITEM;
         done = (unsigned)(left < TD_ROWS_PER_ITEM ? left : TD_ROWS_PER_ITEM);
-      } else {
+      } else if (J.td_mode == 1) {
         tdsc_row_u8<NT, RND>(P, J, idx, reinterpret_cast<uint4*>(smem), scr, threadIdx.x);
+        done = 1;
+      } else {
+        tdsc_row_u8_long(P, J, idx, reinterpret_cast<uint4*>(smem), scr);
         done = 1;
       }
       __syncthreads();

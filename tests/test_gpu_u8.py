@@ -48,7 +48,8 @@ def test_cfg1_paper_canvas(oracle, ctx):
 
 
 @pytest.mark.parametrize("C,T", [(1, 1), (1, 33), (3, 5), (7, 31), (37, 32), (64, 100), (100, 257), (130, 1000),
-                                 (33, 4099), (5, 12500), (3, 12769), (3, 12770), (2, 25000), (1, 98273)])
+                                 (33, 4099), (5, 12500), (3, 12769), (3, 12770), (2, 25000), (1, 98273),
+                                 (1, 98274), (2, 131073), (1, 372181)])
 @pytest.mark.parametrize("rep", ["mean", "median"])
 def test_tdsc_shapes(oracle, ctx, C, T, rep):
     rng = np.random.default_rng(C * 1000 + T)
@@ -101,6 +102,28 @@ def test_in_place(oracle, ctx):
     check(oracle, ctx, x, td=td, fd=fd, in_place=True)
     check(oracle, ctx, x, td=td, api="tdsc", in_place=True)
     check(oracle, ctx, x, fd=fd, api="fdsc", in_place=True)
+
+
+def test_long_rows_read_from_memory(oracle, ctx):
+    # rows beyond the on-chip stage (98,273 samples): every pass reads the row
+    # from memory; misaligned, in place, byte masks, fused with FDSC
+    import torch
+
+    from paper_2001_03389_gb300 import rfim
+
+    rng = np.random.default_rng(17)
+    x = noise_u8(rng, (2, 3, 200003))
+    x[:, 1, 5000:5100] = 255
+    td = dict(k=2.5, iterations=3, replace="median")
+    fd = dict(k=2.5, iterations=2, replace="mean", bin=2)
+    check(oracle, ctx, x, td=td, fd=fd, in_off=3, out_off=9)
+    check(oracle, ctx, x, td=dict(td, replace="mean"), api="tdsc", in_place=True, in_off=1)
+    check(oracle, ctx, x, td=td, fd=fd, mask_fmt="bytes", in_off=7)
+    # the exactness bound of the uint8 decisions: (255 T)^2 < 2^53
+    y = torch.zeros((1, 1, 372182), dtype=torch.uint8, device="cuda:0")
+    with pytest.raises(rfim.RfimError) as e:
+        ctx.tdsc(ctx.block(y, torch.empty_like(y)), rfim.make_cut(3.0))
+    assert e.value.status == rfim.ERR_RANGE
 
 
 def test_degenerate_rows(oracle, ctx):
@@ -200,10 +223,6 @@ def test_validation_errors(ctx):
     with pytest.raises(rfim.RfimError) as e:
         ctx.tdsc(blk2, rfim.make_cut(3.0))
     assert e.value.status == rfim.ERR_ARG  # partial overlap of out and in
-    row = torch.zeros((1, 1, 98274), dtype=torch.uint8, device="cuda:0")
-    with pytest.raises(rfim.RfimError) as e:
-        ctx.tdsc(ctx.block(row, torch.empty_like(row)), rfim.make_cut(3.0))
-    assert e.value.status == rfim.ERR_ARG  # longer than the on-chip row stage
     long_row = torch.zeros((1, 1, 372200), dtype=torch.uint8, device="cuda:0")
     with pytest.raises(rfim.RfimError) as e:
         ctx.tdsc(ctx.block(long_row, torch.empty_like(long_row)), rfim.make_cut(3.0))
