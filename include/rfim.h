@@ -46,7 +46,10 @@
  * Row lengths: uint8 TDSC takes rows up to 372,181 samples, where (255 T)^2
  * reaches 2^53 (RFIM_ERR_RANGE beyond); rows longer than 98,273 samples do not
  * fit the on-chip stage and are read from memory in every pass (slower, same
- * results).  float32 TDSC takes rows up to 52,000 samples (RFIM_ERR_ARG beyond).
+ * results).  float32 TDSC rows longer than 52,000 samples are read from memory
+ * in every pass, replaying the earlier iterations' decisions.  Random
+ * replacement needs the staged row: uint8 rows of at most 78,609 samples,
+ * float32 rows of at most 52,000 (RFIM_ERR_ARG beyond).
  *
  * Conventions for every call below:
  *   - Pointers inside rfim_block are DEVICE pointers owned by the caller,
@@ -108,8 +111,8 @@ typedef enum { RFIM_LAYOUT_BCT = 0, RFIM_LAYOUT_BTC = 1 } rfim_layout;
  * channel, index = time sample), 2 = FDSC (line = time sample, index =
  * channel), beam = the beam's index within its block, it = the iteration; the
  * first draw that hits an unflagged sample wins, and after 32 misses the
- * sample keeps its value.  uint8 TDSC rows with RANDOM hold at most 78,609
- * samples.
+ * sample keeps its value.  TDSC rows with RANDOM hold at most 78,609 samples
+ * (uint8) or 52,000 (float32).
  */
 typedef enum { RFIM_REPLACE_MEAN = 0, RFIM_REPLACE_MEDIAN = 1, RFIM_REPLACE_RANDOM = 2 } rfim_replace;
 

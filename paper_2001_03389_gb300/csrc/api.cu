@@ -87,7 +87,17 @@ rfim_status fail(rfim_ctx* ctx, rfim_status s, const char* fmt, ...) {
   return s;
 }
 
+// A failed runtime call (a launch with a bad configuration, say) also leaves
+// its error as the thread's last CUDA error, which the caller's next CUDA
+// call would report; errors that do not corrupt the context are cleared here
+// and returned as a status only.
+rfim_status clear_cuda_error() {
+  (void)cudaGetLastError();
+  return RFIM_ERR_CUDA;
+}
+
 rfim_status cuda_fail(rfim_ctx* ctx, cudaError_t e, const char* what) {
+  clear_cuda_error();
   return fail(ctx, RFIM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
@@ -197,9 +207,9 @@ rfim_status check_impl(rfim_ctx* ctx, const rfim_block* b, const CutNorm& td, co
   if (b->layout != RFIM_LAYOUT_BCT)
     return fail(ctx, RFIM_ERR_ARG, "BTC blocks are cleaned through a context's BCT scratch (not here)");
   if (b->dtype == RFIM_F32) {
-    if (td.on && b->samples > TD32_MAX_T)
-      return fail(ctx, RFIM_ERR_ARG, "float32 TDSC rows longer than %d samples are not available in this build",
-                  TD32_MAX_T);
+    if (td.on && td.rep == RFIM_REPLACE_RANDOM && b->samples > TD32_MAX_T)
+      return fail(ctx, RFIM_ERR_ARG, "float32 TDSC with random replacement: rows longer than %d samples are not "
+                  "available in this build", TD32_MAX_T);
     if (fd.on) {
       const int C = b->channels, nb = (C + fd.bin - 1) / fd.bin;
       if (fd32_smem_bytes(1, C, nb, fd.rep == RFIM_REPLACE_RANDOM) > MAX_SMEM_PER_CTA)
@@ -273,7 +283,7 @@ Job make_job(const rfim_block* b, int j, const CutNorm& fd, int tile_samples, in
   if (b->dtype == RFIM_F32) {
     // float32: one CTA per TDSC row; FDSC sub-slab of 8, 4, 2 or 1 samples
     // TDSC: two rows per item (a half CTA each) when both stages fit, else one
-    J.td_mode = 2 * td32_smem_bytes(T) <= MAX_SMEM_PER_CTA ? 0 : 1;
+    J.td_mode = 2 * td32_smem_bytes(T) <= MAX_SMEM_PER_CTA ? 0 : T <= TD32_MAX_T ? 1 : 2;
     J.td_items = J.td_mode == 0 ? (C + 1) / 2 : C;
     J.ws = 1;
     for (int ws : {8, 4, 2})
@@ -358,7 +368,7 @@ int occupancy(void* fn, int smem) {
   OccKey k{fn, smem};
   auto it = cache.find(k);
   if (it != cache.end()) return it->second;
-  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448 - 1024);
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM_PER_CTA);
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, NT, smem) != cudaSuccess) n = 1;
   if (n < 1) n = 1;
@@ -916,16 +926,16 @@ rfim_status launch_blocks_fixed(const rfim_block* blocks, int n, const rfim_cut*
   void* fn = engine_kernel(p);
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-    return RFIM_ERR_CUDA;
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448 - 1024) != cudaSuccess ||
+    return clear_cuda_error();
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM_PER_CTA) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, cfg.smem) != cudaSuccess)
-    return RFIM_ERR_CUDA;
+    return clear_cuda_error();
   cfg.grid = std::max(1, std::min(p.n_items, sms * std::max(1, per_sm)));
   // the shared counters and status word keep the previous call's values: clear them
   if (cudaMemsetAsync(counters, 0, sizeof(unsigned) * (1 + p.n_jobs), st) != cudaSuccess ||
       cudaMemsetAsync(status, 0, sizeof(unsigned), st) != cudaSuccess || clear_f32_fdsc_masks(p, st) != cudaSuccess)
-    return RFIM_ERR_CUDA;
-  if (launch_engine(p, cfg, st) != (int)cudaSuccess) return RFIM_ERR_CUDA;
+    return clear_cuda_error();
+  if (launch_engine(p, cfg, st) != (int)cudaSuccess) return clear_cuda_error();
   return RFIM_OK;
 }
 

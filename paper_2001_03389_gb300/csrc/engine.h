@@ -43,7 +43,8 @@ struct Job {
   int rows;         // TDSC rows (C)
   int td_mode;      // uint8: 0 = one warp per row, 8 rows per item; 1 = one row per item, whole CTA;
                     //        2 = one row per item, whole CTA, row read from global memory (no stage).
-                    // float32: 0 = two rows per item, a half CTA each; 1 = one row per item
+                    // float32: 0 = two rows per item, a half CTA each; 1 = one row per item;
+                    //          2 = one row per item, read from global memory in every pass (no stage)
   int td_items;     // number of TDSC work items
   int beam;         // index of the beam within its block (keys the random-replacement draws)
 };
@@ -136,7 +137,8 @@ int engine_smem_u8(const Params& p);
 void* engine_kernel_u8(const Params& p);
 int launch_engine_u8(const Params& p, const LaunchCfg& cfg, void* stream);
 
-// float32 engine: TDSC rows of up to TD32_MAX_T samples staged per CTA; FDSC tile
+// float32 engine: TDSC rows of up to TD32_MAX_T samples staged per CTA (longer rows
+// are read from memory in every pass); FDSC tile
 // of ws x C floats plus per-(t, bin) and per-column scratch.
 constexpr int TD32_LIST = 1024;  // replaced values kept per iteration for the statistics update
 constexpr int TD32_MAX_T = 52000;

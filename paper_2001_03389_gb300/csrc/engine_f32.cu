@@ -599,6 +599,107 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
 }
 
 // ---------------------------------------------------------------------------
+// TDSC on one float32 row longer than the shared-memory stage (the whole CTA).
+// Nothing is staged: every pass reads the row from memory and replays the
+// decisions of the earlier iterations on the fly, y <- r_j where iteration j's
+// cut flags y.  The same statistics, finish and decisions as tdsc_row_f32; the
+// median is the same radix select, one pass per key bit.  Out of line, as such
+// rows are rare.
+// ---------------------------------------------------------------------------
+__device__ __noinline__ void tdsc_row_f32_long(const Params& P, const Job& J, int row, Red32* red) {
+  const CutDev& cut = P.td;
+  const int T = J.T, t = threadIdx.x, lane = t & 31;
+  const float* rin = static_cast<const float*>(J.in) + (size_t)row * T;
+  float* rout = static_cast<float*>(J.out) + (size_t)row * T;
+  const int I = cut.iterations;
+  const double rT = 1.0 / (double)T;
+  const FF kff{cut.k_hi, cut.k_lo};
+  __shared__ Cut32 s_cut[16];
+  __shared__ float s_rep[16];
+  // value of sample i after iterations 0..n-1 (fl: flagged by any of them)
+  auto cur = [&](int i, int n, bool& fl) -> float {
+    float y = rin[i];
+    for (int j = 0; j < n; j++)
+      if (flag32(y, s_cut[j])) {
+        y = s_rep[j];
+        fl = true;
+      }
+    return y;
+  };
+  for (int it = 0; it < I; it++) {
+    FF S{0.f, 0.f}, Q{0.f, 0.f};
+    for (int i = t; i < T; i += NT) {
+      bool fl = false;
+      const float y = cur(i, it, fl);
+      ff_acc(S, y);
+      ff_acc_sq(Q, y);
+    }
+    grp_ff2<NT>(S, Q, red, t, 0);  // (the same in every thread)
+    FF mu = ff_div_int(S, T);
+    const FF mq = ff_div_int(Q, T);
+    FF var = ff_add(mq, ff_neg(ff_mul(mu, mu)));
+    if (!(var.hi >= 1e-3f * mq.hi)) {
+      // cancellation (or a constant row): FP64 two-pass
+      double sd = 0.0;
+      for (int i = t; i < T; i += NT) {
+        bool fl = false;
+        sd += (double)cur(i, it, fl);
+      }
+      sd = grp_dsum<NT>(sd, red, t, 0);
+      const double m2 = sd * rT;
+      double ss = 0.0;
+      for (int i = t; i < T; i += NT) {
+        bool fl = false;
+        const double d = (double)cur(i, it, fl) - m2;
+        ss += d * d;
+      }
+      ss = grp_dsum<NT>(ss, red, t, 0);
+      mu = ff_from_d(m2);
+      var = ff_from_d(ss * rT);
+    }
+    const Cut32 c = make_cut32(mu, ff_mul(kff, ff_sqrt(var)));
+    float r = c.mu_f;
+    if (cut.replace == REP_MEDIAN) {
+      const int rank = (T - 1) >> 1;
+      unsigned prefix = 0;
+      for (int b = 31; b >= 0; b--) {
+        const unsigned test = prefix | (1u << b);
+        int cnt = 0;
+        for (int i = t; i < T; i += NT) {
+          bool fl = false;
+          cnt += fkey(cur(i, it, fl)) < test;
+        }
+        cnt = grp_isum<NT>(cnt, red, t, 0);
+        if (cnt <= rank) prefix = test;
+      }
+      r = key_f(prefix);
+    }
+    if (t == 0) {
+      s_cut[it] = c;
+      s_rep[it] = r;
+    }
+    gsync<NT>(0);
+  }
+  // ---- output and mask: a warp per 32-sample mask word
+  const int W32 = (T + 31) >> 5;
+  unsigned* mrow = (P.mask_kind == MASK_BITS && J.mask) ? static_cast<unsigned*>(J.mask) + (size_t)row * W32 : nullptr;
+  unsigned char* mb =
+      (P.mask_kind == MASK_BYTES && J.mask) ? static_cast<unsigned char*>(J.mask) + (size_t)row * T : nullptr;
+  for (int w = t >> 5; w < W32; w += NT / 32) {
+    const int i = 32 * w + lane;
+    bool fl = false;
+    if (i < T) {
+      const float y = cur(i, I, fl);  // (read before the write: out may be in)
+      rout[i] = y;
+      if (mb) mb[i] = P.td_mask_or ? (unsigned char)(mb[i] | (fl ? 1u : 0u)) : (unsigned char)(fl ? 1u : 0u);
+    }
+    const unsigned bits = __ballot_sync(0xffffffffu, fl);
+    if (mrow && lane == 0) mrow[w] = P.td_mask_or ? (mrow[w] | bits) : bits;
+  }
+  gsync<NT>(0);
+}
+
+// ---------------------------------------------------------------------------
 // FDSC on one item: one sub-slab of ws time samples x C channels of a float32
 // beam (16 bytes of each channel row for ws = 4).  Consecutive items, which
 // share the 128-byte lines of the rows, run at the same time, so the lines in
@@ -988,8 +1089,10 @@ __global__ void __launch_bounds__(NT, 2) k_engine_f32(const __grid_constant__ Pa
         const int row = 2 * idx + h;
         if (row < J.rows) tdsc_row_f32<NT / 2, RND>(P, J, row, smem + h * td32_smem_bytes(J.T), &red[h], t, h);
         done = (unsigned)min(2, J.rows - 2 * idx);
-      } else {
+      } else if (J.td_mode == 1) {
         tdsc_row_f32<NT, RND>(P, J, idx, smem, &red[0], threadIdx.x, 0);
+      } else {
+        tdsc_row_f32_long(P, J, idx, &red[0]);
       }
       __syncthreads();
       if (threadIdx.x == 0) {
@@ -1007,7 +1110,7 @@ int engine_smem_f32(const Params& p) {
   int s = 16;
   for (int j = 0; j < p.n_jobs; j++) {
     const Job& J = p.jobs[j];
-    if (p.td.iterations > 0) {
+    if (p.td.iterations > 0 && J.td_mode != 2) {  // (mode 2 rows are not staged)
       const int td = (J.td_mode == 0 ? 2 : 1) * td32_smem_bytes(J.T);
       s = s > td ? s : td;
     }

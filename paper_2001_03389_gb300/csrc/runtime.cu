@@ -119,6 +119,7 @@ rfim_status stager_run(HostStager* s, rfim_ctx* ctx, const rfim_block* hb, const
     cudaError_t e = cudaMemcpyAsync(s->dbuf[i], hin + (size_t)b0 * beam, (size_t)nb * beam, cudaMemcpyHostToDevice, str);
     if (e != cudaSuccess) {
       ctx_set_error(ctx, cudaGetErrorString(e));
+      (void)cudaGetLastError();  // reported here: not left for the caller's next call
       st = RFIM_ERR_CUDA;
       break;
     }
@@ -135,6 +136,7 @@ rfim_status stager_run(HostStager* s, rfim_ctx* ctx, const rfim_block* hb, const
       e = cudaMemcpyAsync(hmask + (size_t)b0 * mbeam, s->dmask[i], (size_t)nb * mbeam, cudaMemcpyDeviceToHost, str);
     if (e != cudaSuccess) {
       ctx_set_error(ctx, cudaGetErrorString(e));
+      (void)cudaGetLastError();  // reported here: not left for the caller's next call
       st = RFIM_ERR_CUDA;
       break;
     }
@@ -143,6 +145,7 @@ rfim_status stager_run(HostStager* s, rfim_ctx* ctx, const rfim_block* hb, const
     cudaError_t e = cudaStreamSynchronize(s->st[i]);
     if (e != cudaSuccess && st == RFIM_OK) {
       ctx_set_error(ctx, cudaGetErrorString(e));
+      (void)cudaGetLastError();  // reported here: not left for the caller's next call
       st = RFIM_ERR_CUDA;
     }
   }

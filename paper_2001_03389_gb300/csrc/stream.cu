@@ -171,6 +171,7 @@ void dispatch_loop(StreamService* s) {
                                          s->has_fd ? &s->fd : nullptr, ctr, ctr + 1 + MAX_JOBS, s->streams[lane]);
     cudaError_t e = cudaSuccess;
     if (st == RFIM_OK) e = cudaLaunchHostFunc(s->streams[lane], batch_done, &b);
+    if (e != cudaSuccess) (void)cudaGetLastError();
     lk.lock();
     if (st != RFIM_OK || e != cudaSuccess) {
       // the batch never ran: report the fault and complete its chunks as failed
@@ -363,6 +364,7 @@ rfim_status svc_push(StreamService* s, int beam, const void* chunk, bool on_devi
       if (e == cudaSuccess) e = cudaStreamSynchronize(s->copy_stream);
     }
     if (e != cudaSuccess) {
+      (void)cudaGetLastError();  // reported by the status: not left for the caller's next call
       std::lock_guard<std::mutex> g(s->mu);
       s->free_slots.push_back(slot);
       return RFIM_ERR_CUDA;

@@ -89,6 +89,21 @@ def test_tdsc_f32_shapes(oracle, ctx, C, T, rep):
         check_f32(oracle, ctx, x, td=dict(k=k, iterations=it, replace=rep), api="tdsc")
 
 
+@pytest.mark.parametrize("C,T", [(1, 52001), (2, 100003)])
+@pytest.mark.parametrize("rep", ["mean", "median"])
+def test_tdsc_f32_long_rows(oracle, ctx, C, T, rep):
+    # rows beyond the on-chip stage (52,000 samples): read from memory in every
+    # pass, the earlier iterations replayed; misaligned, in place, byte masks
+    rng = np.random.default_rng(C * 31 + T)
+    x = chi2_block(rng, 2, C, T)
+    for it, k in [(1, 3.0), (3, 2.5)]:
+        check_f32(oracle, ctx, x, td=dict(k=k, iterations=it, replace=rep), api="tdsc")
+    td = dict(k=2.5, iterations=2, replace=rep)
+    check_f32(oracle, ctx, x, td=td, fd=dict(k=2.5, iterations=2, replace="mean", bin=C), in_off=4, out_off=12)
+    check_f32(oracle, ctx, x, td=td, api="tdsc", in_place=True, in_off=8)
+    check_f32(oracle, ctx, x, td=td, api="tdsc", mask_fmt="bytes")
+
+
 @pytest.mark.parametrize("C,T,bin", [(1, 40, 1), (4, 33, 4), (32, 64, 32), (37, 70, 32), (64, 31, 7),
                                      (100, 50, 3), (130, 96, 32), (96, 40, 96), (4096, 40, 32), (257, 33, 16)])
 @pytest.mark.parametrize("rep", ["mean", "median"])
@@ -191,8 +206,8 @@ def test_f32_validation(ctx):
     from paper_2001_03389_gb300 import rfim
 
     row = torch.zeros((1, 1, 60000), dtype=torch.float32, device="cuda:0")
-    with pytest.raises(rfim.RfimError) as e:
-        ctx.tdsc(ctx.block(row, torch.empty_like(row)), rfim.make_cut(3.0))
+    with pytest.raises(rfim.RfimError) as e:  # random replacement needs the staged row
+        ctx.tdsc(ctx.block(row, torch.empty_like(row)), rfim.make_cut(3.0, replace="random"))
     assert e.value.status == rfim.ERR_ARG
     big = torch.zeros((1, 40000, 4), dtype=torch.float32, device="cuda:0")
     with pytest.raises(rfim.RfimError) as e:
