@@ -265,6 +265,20 @@ __device__ __forceinline__ void grp_sum(unsigned long long (&v)[N], unsigned lon
   }
 }
 
+// grp_sum of non-negative row sums: a warp row holds at most 12,769 samples
+// (TD_WARP_CHUNKS), so every partial and total (at most 12,769 * 255^2 for
+// sums of squares) fits 32 bits and the warp reduces in 32-bit shuffles.
+template <int LANES, int N>
+__device__ __forceinline__ void grp_sum_row(unsigned long long (&v)[N], unsigned long long* scr) {
+  static_assert(TD_WARP_CHUNKS * 16 * 255ull * 255ull < (1ull << 32), "warp-row sums fit 32 bits");
+  if (LANES == 32) {
+#pragma unroll
+    for (int i = 0; i < N; i++) v[i] = warp_sum((unsigned)v[i]);
+  } else {
+    grp_sum<LANES, N>(v, scr);
+  }
+}
+
 template <int LANES>
 __device__ __forceinline__ void grp_sync() {
   if (LANES == 32) __syncwarp();
@@ -374,7 +388,7 @@ __device__ unsigned med_finish(MedSearch& m, const Rd& rd, int nch, int T, unsig
       }
     }
     unsigned long long f[4] = {f32[0], f32[1], f32[2], f32[3]};
-    grp_sum<LANES, 4>(f, scr);
+    grp_sum_row<LANES, 4>(f, scr);
 #pragma unroll
     for (int i = 0; i < 4; i++) f[i] -= npad * (unsigned long long)(m.pts[i] > 255 ? 255 : m.pts[i]);
     med_update(m, f, T);
@@ -472,7 +486,7 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
     sq[1] = q;
   }
   if (LANES == 32) __syncwarp();
-  grp_sum<LANES, 2>(sq, scr);  // (the CTA variant's barriers also publish the staged row)
+  grp_sum_row<LANES, 2>(sq, scr);  // (the CTA variant's barriers also publish the staged row)
   unsigned long long S = sq[0], Q = sq[1];
 
   // single: every flagged sample ends at one value (the median, or the mean of a
@@ -525,7 +539,7 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
         }
       }
       unsigned long long red[7] = {s_in, q_in, n_out, f32[0], f32[1], f32[2], f32[3]};
-      grp_sum<LANES, 7>(red, scr);
+      grp_sum_row<LANES, 7>(red, scr);
       if (!kp.all && klo > 0) red[2] -= npad;  // the zero padding bytes were counted as flagged
       if (probe) {
         unsigned long long f[4] = {red[3], red[4], red[5], red[6]};
@@ -624,7 +638,7 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
         }
       }
       unsigned long long d[2] = {s2, q2};
-      grp_sum<LANES, 2>(d, scr);
+      grp_sum_row<LANES, 2>(d, scr);
       S = d[0];
       Q = d[1];
     }
