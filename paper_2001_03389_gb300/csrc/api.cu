@@ -279,7 +279,9 @@ Job make_job(const rfim_block* b, int j, const CutNorm& fd, int tile_samples, in
   J.fd_items = (T + FD_ITEM_T - 1) / FD_ITEM_T;
   const int tm = td_row_mode(T);  // (-1 only with TDSC off: no TDSC items then)
   J.td_mode = tm < 0 ? 1 : tm;
-  J.td_items = J.td_mode == 0 ? (C + TD_ROWS_PER_ITEM - 1) / TD_ROWS_PER_ITEM : C;
+  J.td_items = J.td_mode == 0   ? (C + TD_ROWS_PER_ITEM - 1) / TD_ROWS_PER_ITEM
+               : J.td_mode == 3 ? (C + 4 * TD_ROWS_PER_ITEM - 1) / (4 * TD_ROWS_PER_ITEM)
+                                : C;
   if (b->dtype == RFIM_F32) {
     // float32: one CTA per TDSC row; FDSC sub-slab of 8, 4, 2 or 1 samples
     // TDSC: two rows per item (a half CTA each) when both stages fit, else one

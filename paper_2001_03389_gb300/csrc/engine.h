@@ -42,7 +42,8 @@ struct Job {
   int fd_items;     // number of FDSC work items (ceil(T / 32))
   int rows;         // TDSC rows (C)
   int td_mode;      // uint8: 0 = one warp per row, 8 rows per item; 1 = one row per item, whole CTA;
-                    //        2 = one row per item, whole CTA, row read from global memory (no stage).
+                    //        2 = one row per item, whole CTA, row read from global memory (no stage);
+                    //        3 = a quarter warp per row, 32 rows per item.
                     // float32: 0 = two rows per item, a half CTA each; 1 = one row per item;
                     //          2 = one row per item, read from global memory in every pass (no stage)
   int td_items;     // number of TDSC work items
@@ -120,8 +121,13 @@ __host__ __device__ inline int td_random_row_mode(long long T) {
 // pass (mode 2), up to the exactness bound of the uint8 decisions,
 // (255 T)^2 < 2^53.
 constexpr long long TD_MAX_T = 372181;
+// Rows of up to TD_QUAD_CHUNKS chunks (about 3,150 samples) take a quarter warp
+// each, four rows per warp in a quarter of the warp's stage (mode 3), so that
+// the per-row steps (thresholds, reductions) are shared by fewer lanes.
+constexpr int TD_QUAD_CHUNKS = TD_WARP_CHUNKS / 4;
 inline int td_row_mode(long long T) {
   const long long nch = (T + 30) / 16 + 1;  // worst-case alignment of the row start
+  if (nch <= TD_QUAD_CHUNKS) return 3;
   if (nch <= TD_WARP_CHUNKS) return 0;
   if (nch <= TD_CTA_CHUNKS) return 1;
   if (T <= TD_MAX_T) return 2;

@@ -166,12 +166,13 @@ __device__ __forceinline__ void keep_from(unsigned S, unsigned A, unsigned d, fl
   hi = hv > 255 ? 255 : (int)hv;
 }
 
-// TDSC keep interval of a row; all 32 lanes of the calling warp cooperate.
+// TDSC keep interval of a row; the lanes of the calling group (up to 32) cooperate.
+template <int LANES>
 __device__ __forceinline__ void tdsc_keep_warp(unsigned long long S, unsigned long long Q, int T, float rcpT,
                                                const ExactK2& k2, int& lo, int& hi) {
   const unsigned long long Tl = (unsigned long long)T;
   const unsigned long long R = Tl * Q - S * S;
-  const unsigned A = max_keep_grp<32>(R, 1ull, 255u * (unsigned)T, k2);
+  const unsigned A = max_keep_grp<(LANES < 32 ? LANES : 32)>(R, 1ull, 255u * (unsigned)T, k2);
   keep_from((unsigned)S, A, (unsigned)T, rcpT, lo, hi);
 }
 
@@ -239,41 +240,63 @@ __device__ __forceinline__ uint32_t chunk_bits(const uint4& f) {
 }
 
 // ---------------------------------------------------------------------------
-// group reductions: LANES = 32 (one warp per row) or NT (the CTA)
+// group reductions: LANES = 8 (a quarter warp per row), 32 (one warp per row)
+// or NT (the CTA).  Groups of 8 are aligned lane octets; the four groups of a
+// warp may diverge, so every group primitive names only its own lanes.
 // ---------------------------------------------------------------------------
 constexpr int GRP_SUM_MAX = 8;  // values one grp_sum may reduce (scratch: GRP_SUM_MAX * NT/32 words)
+
+template <int LANES>
+__device__ __forceinline__ unsigned grp_mask() {
+  if constexpr (LANES >= 32) return 0xffffffffu;
+  else return ((1u << LANES) - 1u) << ((threadIdx.x & 31) & ~(LANES - 1));
+}
+
+// sum over the lanes of a group of at most 32 lanes (every lane gets it)
+template <int LANES, typename V>
+__device__ __forceinline__ V grp_lane_sum(V v) {
+  const unsigned m = grp_mask<LANES>();
+#pragma unroll
+  for (int o = 1; o < LANES; o <<= 1) v += __shfl_xor_sync(m, v, o);
+  return v;
+}
 
 template <int LANES, int N>
 __device__ __forceinline__ void grp_sum(unsigned long long (&v)[N], unsigned long long* scr) {
   static_assert(N <= GRP_SUM_MAX, "grp_sum scratch holds GRP_SUM_MAX values per warp");
+  if constexpr (LANES <= 32) {
 #pragma unroll
-  for (int i = 0; i < N; i++) v[i] = warp_sum(v[i]);
-  if (LANES == 32) return;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) {
+    for (int i = 0; i < N; i++) v[i] = grp_lane_sum<LANES>(v[i]);
+  } else {
 #pragma unroll
-    for (int i = 0; i < N; i++) scr[i * (NT / 32) + warp] = v[i];
-  }
-  __syncthreads();
+    for (int i = 0; i < N; i++) v[i] = warp_sum(v[i]);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) {
 #pragma unroll
-  for (int i = 0; i < N; i++) {
-    unsigned long long s = 0;
+      for (int i = 0; i < N; i++) scr[i * (NT / 32) + warp] = v[i];
+    }
+    __syncthreads();
 #pragma unroll
-    for (int w = 0; w < NT / 32; w++) s += scr[i * (NT / 32) + w];
-    v[i] = s;
+    for (int i = 0; i < N; i++) {
+      unsigned long long s = 0;
+#pragma unroll
+      for (int w = 0; w < NT / 32; w++) s += scr[i * (NT / 32) + w];
+      v[i] = s;
+    }
   }
 }
 
-// grp_sum of non-negative row sums: a warp row holds at most 12,769 samples
-// (TD_WARP_CHUNKS), so every partial and total (at most 12,769 * 255^2 for
-// sums of squares) fits 32 bits and the warp reduces in 32-bit shuffles.
+// grp_sum of non-negative row sums: a warp or quarter-warp row holds at most
+// 12,769 samples (TD_WARP_CHUNKS), so every partial and total (at most
+// 12,769 * 255^2 for sums of squares) fits 32 bits and the lanes reduce in
+// 32-bit shuffles.
 template <int LANES, int N>
 __device__ __forceinline__ void grp_sum_row(unsigned long long (&v)[N], unsigned long long* scr) {
   static_assert(TD_WARP_CHUNKS * 16 * 255ull * 255ull < (1ull << 32), "warp-row sums fit 32 bits");
-  if (LANES == 32) {
+  if constexpr (LANES <= 32) {
 #pragma unroll
-    for (int i = 0; i < N; i++) v[i] = warp_sum((unsigned)v[i]);
+    for (int i = 0; i < N; i++) v[i] = grp_lane_sum<LANES>((unsigned)v[i]);
   } else {
     grp_sum<LANES, N>(v, scr);
   }
@@ -281,7 +304,7 @@ __device__ __forceinline__ void grp_sum_row(unsigned long long (&v)[N], unsigned
 
 template <int LANES>
 __device__ __forceinline__ void grp_sync() {
-  if (LANES == 32) __syncwarp();
+  if constexpr (LANES <= 32) __syncwarp(grp_mask<LANES>());
   else __syncthreads();
 }
 
@@ -485,14 +508,15 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
     sq[0] = s;
     sq[1] = q;
   }
-  if (LANES == 32) __syncwarp();
+  if (LANES <= 32) __syncwarp(grp_mask<LANES>());
   grp_sum_row<LANES, 2>(sq, scr);  // (the CTA variant's barriers also publish the staged row)
   unsigned long long S = sq[0], Q = sq[1];
 
   // single: every flagged sample ends at one value (the median, or the mean of a
   // one-iteration cut), so one keep interval (the intersection) decides everything
   const bool median = cut.replace == REP_MEDIAN;
-  const bool random = RND && !STREAM && cut.replace == REP_RANDOM;  // (RND: the build that holds random replacement)
+  // (RND: the build that holds random replacement; it runs on warp or CTA rows)
+  const bool random = RND && !STREAM && LANES >= 32 && cut.replace == REP_RANDOM;
   const bool single = !random && (median || cut.iterations == 1);
   const unsigned long long npad = 16ull * (unsigned)g.nch - (unsigned)T;  // zero bytes in the chunk grid
   const int I = cut.iterations;
@@ -510,7 +534,7 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
     med_init(ms, S, Q, T);
     for (int it = 0; it < I; it++) {
       int lo, hi;
-      tdsc_keep_warp(S, Q, T, rcpT, cut.k2, lo, hi);
+      tdsc_keep_warp<LANES>(S, Q, T, rcpT, cut.k2, lo, hi);
       klo = lo > klo ? lo : klo;
       khi = hi < khi ? hi : khi;
       if (it == I - 1) break;
@@ -565,7 +589,7 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
     for (int k = gl; k < g.nch; k += LANES) facc[k] = 0;
     for (int it = 0; it < I; it++) {
       int lo, hi;
-      tdsc_keep_warp(S, Q, T, rcpT, cut.k2, lo, hi);
+      tdsc_keep_warp<LANES>(S, Q, T, rcpT, cut.k2, lo, hi);
       const ByteKeep kp = make_keep(lo, hi);
       for (int k = gl; k < g.nch; k += LANES) {
         const uint4 w = st[k];
@@ -608,14 +632,14 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
       }
       unsigned long long d[2] = {(unsigned long long)dS, (unsigned long long)dQ};
       grp_sum<LANES, 2>(d, scr);  // (the CTA variant's barriers also publish the new row)
-      if (LANES == 32) __syncwarp();
+      if (LANES <= 32) __syncwarp(grp_mask<LANES>());
       S += d[0];
       Q += d[1];
     }
   } else {
     for (int it = 0; it < I; it++) {
       int lo, hi;
-      tdsc_keep_warp(S, Q, T, rcpT, cut.k2, lo, hi);
+      tdsc_keep_warp<LANES>(S, Q, T, rcpT, cut.k2, lo, hi);
       const unsigned r = udiv_q((unsigned)(2 * S + (unsigned long long)T), 2u * (unsigned)T, rcp2T);
       lo_i[it] = lo;
       hi_i[it] = hi;
@@ -1529,7 +1553,17 @@ __global__ void __launch_bounds__(NT, MINB) k_engine_u8(const __grid_constant__ 
     const Job& J = P.jobs[sg.job];
     if (sg.kind == 0) {
       unsigned done;
-      if (J.td_mode == 0) {
+      if (J.td_mode == 3) {
+        // four rows per warp: lane octet q cleans row 4 warp + q in a quarter of the warp's stage
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = lane >> 3;
+        const int row = idx * 4 * TD_ROWS_PER_ITEM + 4 * warp + q;
+        if (row < J.rows)
+          tdsc_row_u8<8, RND>(P, J, row,
+                              reinterpret_cast<uint4*>(smem + warp * TD_WARP_STAGE + q * (TD_WARP_STAGE / 4)), scr,
+                              lane & 7);
+        const int left = J.rows - idx * 4 * TD_ROWS_PER_ITEM;
+        done = (unsigned)(left < 4 * TD_ROWS_PER_ITEM ? left : 4 * TD_ROWS_PER_ITEM);
+      } else if (J.td_mode == 0) {
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         const int row = idx * TD_ROWS_PER_ITEM + warp;
         if (row < J.rows)
@@ -1563,7 +1597,7 @@ int engine_smem_u8(const Params& p) {
   for (int j = 0; j < p.n_jobs; j++) {
     const Job& J = p.jobs[j];
     if (p.td.iterations > 0) {
-      const int td = J.td_mode == 0 ? TD_WARP_STAGE * TD_ROWS_PER_ITEM : TD_CTA_CHUNKS * 16;
+      const int td = (J.td_mode == 0 || J.td_mode == 3) ? TD_WARP_STAGE * TD_ROWS_PER_ITEM : TD_CTA_CHUNKS * 16;
       s = s > td ? s : td;
     }
     if (p.fd.iterations > 0) {

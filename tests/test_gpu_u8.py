@@ -48,6 +48,7 @@ def test_cfg1_paper_canvas(oracle, ctx):
 
 
 @pytest.mark.parametrize("C,T", [(1, 1), (1, 33), (3, 5), (7, 31), (37, 32), (64, 100), (100, 257), (130, 1000),
+                                 (37, 1250), (5, 3169), (5, 3170),
                                  (33, 4099), (5, 12500), (3, 12769), (3, 12770), (2, 25000), (1, 98273),
                                  (1, 98274), (2, 131073), (1, 372181)])
 @pytest.mark.parametrize("rep", ["mean", "median"])
