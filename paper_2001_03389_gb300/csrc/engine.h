@@ -125,6 +125,7 @@ constexpr long long TD_MAX_T = 372181;
 // each, four rows per warp in a quarter of the warp's stage (mode 3), so that
 // the per-row steps (thresholds, reductions) are shared by fewer lanes.
 constexpr int TD_QUAD_CHUNKS = TD_WARP_CHUNKS / 4;
+constexpr int TD_MBARS = NT / 32 + NT / 8 + 1;  // staging mbarriers: warps, quarter warps, the CTA
 inline int td_row_mode(long long T) {
   const long long nch = (T + 30) / 16 + 1;  // worst-case alignment of the row start
   if (nch <= TD_QUAD_CHUNKS) return 3;

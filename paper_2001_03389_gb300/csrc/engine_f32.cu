@@ -364,8 +364,11 @@ __device__ float row_median_f32(const float4* st, int nch, int head, int tail, i
 }
 
 // GN threads clean the row: t = thread in the group, h = group (its barrier is 1 + h)
+// mbar: the group's staging mbarrier; bit `pb` of mpar is the parity of its next
+// phase (tracked by every thread of the group).
 template <int GN, bool RND>
-__device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned char* smem, Red32* red, int t, int h) {
+__device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned char* smem, Red32* red, int t, int h,
+                             unsigned long long* mbar, unsigned& mpar, int pb) {
   const CutDev& cut = P.td;
   const int T = J.T;
   const float* beam_in = static_cast<const float*>(J.in);
@@ -389,13 +392,18 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
     s_cnt[1] = 0;
   }
 
-  // ---- stage the row (edge chunks through guarded loads, padding zeroed)
+  // ---- stage the row: the interior chunks (inside the row) are one TMA bulk
+  //      copy issued by the group's first thread, completing on the group's
+  //      mbarrier; the edge chunks take guarded loads, padding zeroed
+  const bool bulk = nch > 2;  // (the same in every thread of the group)
+  if (bulk && t == 0) {
+    fence_proxy_async_smem();  // earlier generic accesses of the stage come first
+    mbar_arrive_expect_tx(mbar, 16u * (unsigned)(nch - 2));
+    bulk_copy_g2s(st + 1, cb + 4, 16u * (unsigned)(nch - 2), mbar);
+  }
   for (int k = t; k < nch; k += GN) {
-    const float* a = cb + 4 * k;
-    if (k > 0 && k < nch - 1) {
-      const unsigned sdst = (unsigned)__cvta_generic_to_shared(st + k);
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sdst), "l"(a) : "memory");
-    } else {
+    if (k == 0 || k == nch - 1) {
+      const float* a = cb + 4 * k;
       const int lo = k == 0 ? head : 0, hi = k == nch - 1 ? tail : 4;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
@@ -405,7 +413,10 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
     }
     fl4[k] = 0;
   }
-  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+  if (bulk) {
+    if (!mbar_wait_bounded(mbar, (mpar >> pb) & 1u, P.spin_limit_ns)) atomicExch(P.status, 5u);
+    mpar ^= 1u << pb;
+  }
   gsync<GN>(h);
 
   // ---- sums of the staged row (padding zeros add nothing)
@@ -1065,6 +1076,14 @@ template <bool RND>
 __global__ void __launch_bounds__(NT, 2) k_engine_f32(const __grid_constant__ Params P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Red32 red[2];
+  // TDSC staging mbarriers: [0, 2) the half CTAs, 2 the CTA (one per group, so
+  // that a barrier's phases are tracked by the same threads); mpar bits: 0 this
+  // half's, 1 the CTA's
+  __shared__ __align__(8) unsigned long long s_mbar[3];
+  if (threadIdx.x < 3) mbar_init(&s_mbar[threadIdx.x], 1);
+  mbar_init_fence();
+  __syncthreads();
+  unsigned mpar = 0;
   __shared__ int s_item, s_flag;
   for (;;) {
     if (threadIdx.x == 0) s_item = (int)atomicAdd(P.counters, 1u);
@@ -1087,10 +1106,11 @@ __global__ void __launch_bounds__(NT, 2) k_engine_f32(const __grid_constant__ Pa
         // two rows per item, one per half CTA (each half synchronises on its own barrier)
         const int h = threadIdx.x / (NT / 2), t = threadIdx.x % (NT / 2);
         const int row = 2 * idx + h;
-        if (row < J.rows) tdsc_row_f32<NT / 2, RND>(P, J, row, smem + h * td32_smem_bytes(J.T), &red[h], t, h);
+        if (row < J.rows)
+          tdsc_row_f32<NT / 2, RND>(P, J, row, smem + h * td32_smem_bytes(J.T), &red[h], t, h, &s_mbar[h], mpar, 0);
         done = (unsigned)min(2, J.rows - 2 * idx);
       } else if (J.td_mode == 1) {
-        tdsc_row_f32<NT, RND>(P, J, idx, smem, &red[0], threadIdx.x, 0);
+        tdsc_row_f32<NT, RND>(P, J, idx, smem, &red[0], threadIdx.x, 0, &s_mbar[2], mpar, 1);
       } else {
         tdsc_row_f32_long(P, J, idx, &red[0]);
       }

@@ -452,8 +452,11 @@ __device__ __forceinline__ void td_stats_pass(const Rd& rd, int nch, int gl, con
 // STREAM: the row is longer than the shared-memory stage; every pass reads its
 // 16-byte chunks from global memory (L2) instead, edge chunks masked as the
 // staging would, and `st` only holds the output pass's flag words.
+// mbar: the staging group's mbarrier; bit `pb` of mpar is the parity of its
+// next phase (tracked by every thread of the group).
 template <int LANES, bool RND, bool STREAM = false>
-__device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, unsigned long long* scr, int gl) {
+__device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, unsigned long long* scr, int gl,
+                            unsigned long long* mbar, unsigned& mpar, int pb) {
   const CutDev& cut = P.td;
   const int T = J.T;
   const uint8_t* beam_in = static_cast<const uint8_t*>(J.in);
@@ -476,19 +479,39 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
     return and4(load16_guarded(a, blo, bhi), chunk_valid(g, k));
   };
 
-  // ---- pass 1: stage the row with asynchronous copies (every chunk in flight at
-  //      once, no registers held), fix up the edge chunks, then S and Q
-  if (!STREAM) {
+  // ---- pass 1: stage the row.  Warp and CTA rows: the run of chunks inside the
+  //      beam buffer is one TMA bulk copy issued by the group's first lane,
+  //      completing on the group's mbarrier.  Quarter-warp rows (at most 200
+  //      chunks) issue 16-byte asynchronous copies from every lane instead:
+  //      for them one copy's round trip costs more than it saves.  A chunk that
+  //      crosses the buffer's ends takes guarded loads.  Then the edge chunks
+  //      are fixed up, and S and Q taken.
+  if (!STREAM && LANES < 32) {
     for (int k = gl; k < g.nch; k += LANES) {
       const uint8_t* a = g.cb + 16 * k;
       if (a >= blo && a + 16 <= bhi) {
-        const unsigned sdst = (unsigned)__cvta_generic_to_shared(st + k);
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sdst), "l"(a) : "memory");
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(st + k)), "l"(a) : "memory");
       } else {
         st[k] = load16_guarded(a, blo, bhi);
       }
     }
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+    grp_sync<LANES>();
+  } else if (!STREAM) {
+    const int k0 = g.cb >= blo ? 0 : 1;
+    const int k1 = g.cb + 16 * g.nch <= bhi ? g.nch : g.nch - 1;
+    const bool bulk = k1 > k0;  // (the same in every lane of the group)
+    if (bulk && gl == 0) {
+      fence_proxy_async_smem();  // earlier generic accesses of the stage come first
+      mbar_arrive_expect_tx(mbar, 16u * (unsigned)(k1 - k0));
+      bulk_copy_g2s(st + k0, g.cb + 16 * k0, 16u * (unsigned)(k1 - k0), mbar);
+    }
+    for (int k = gl; k < g.nch; k += LANES)
+      if (k < k0 || k >= k1) st[k] = load16_guarded(g.cb + 16 * k, blo, bhi);
+    if (bulk) {
+      if (!mbar_wait_bounded(mbar, (mpar >> pb) & 1u, P.spin_limit_ns)) atomicExch(P.status, 5u);
+      mpar ^= 1u << pb;
+    }
     grp_sync<LANES>();
   }
   unsigned long long sq[2];
@@ -1531,7 +1554,8 @@ __device__ __forceinline__ int seg_of(const Params& P, int item) {
 // from global memory in every pass); out of line, as such rows are rare.
 __device__ __noinline__ void tdsc_row_u8_long(const Params& P, const Job& J, int row, uint4* st,
                                               unsigned long long* scr) {
-  tdsc_row_u8<NT, false, true>(P, J, row, st, scr, threadIdx.x);
+  unsigned no_par = 0;  // (nothing is staged)
+  tdsc_row_u8<NT, false, true>(P, J, row, st, scr, threadIdx.x, nullptr, no_par, 0);
 }
 
 // MINB = CTAs per SM the register allocation targets (the TDSC row stage is
@@ -1542,6 +1566,14 @@ __global__ void __launch_bounds__(NT, MINB) k_engine_u8(const __grid_constant__ 
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long scr[GRP_SUM_MAX * (NT / 32)];
   __shared__ int s_item, s_flag;
+  // TDSC staging mbarriers, one per staging group so that a barrier's phases
+  // are always tracked by the same threads: [0, 8) warps, [8, 40) quarter
+  // warps, 40 the CTA.  mpar bits: 0 this warp's, 1 this octet's, 2 the CTA's.
+  __shared__ __align__(8) unsigned long long s_mbar[TD_MBARS];
+  if (threadIdx.x < TD_MBARS) mbar_init(&s_mbar[threadIdx.x], 1);
+  mbar_init_fence();
+  __syncthreads();
+  unsigned mpar = 0;
   for (;;) {
     if (threadIdx.x == 0) s_item = (int)atomicAdd(P.counters, 1u);
     __syncthreads();
@@ -1560,18 +1592,19 @@ __global__ void __launch_bounds__(NT, MINB) k_engine_u8(const __grid_constant__ 
         if (row < J.rows)
           tdsc_row_u8<8, RND>(P, J, row,
                               reinterpret_cast<uint4*>(smem + warp * TD_WARP_STAGE + q * (TD_WARP_STAGE / 4)), scr,
-                              lane & 7);
+                              lane & 7, &s_mbar[8 + 4 * warp + q], mpar, 1);
         const int left = J.rows - idx * 4 * TD_ROWS_PER_ITEM;
         done = (unsigned)(left < 4 * TD_ROWS_PER_ITEM ? left : 4 * TD_ROWS_PER_ITEM);
       } else if (J.td_mode == 0) {
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         const int row = idx * TD_ROWS_PER_ITEM + warp;
         if (row < J.rows)
-          tdsc_row_u8<32, RND>(P, J, row, reinterpret_cast<uint4*>(smem + warp * TD_WARP_STAGE), scr, lane);
+          tdsc_row_u8<32, RND>(P, J, row, reinterpret_cast<uint4*>(smem + warp * TD_WARP_STAGE), scr, lane,
+                               &s_mbar[warp], mpar, 0);
         const int left = J.rows - idx * TD_ROWS_PER_ITEM;
         done = (unsigned)(left < TD_ROWS_PER_ITEM ? left : TD_ROWS_PER_ITEM);
       } else if (J.td_mode == 1) {
-        tdsc_row_u8<NT, RND>(P, J, idx, reinterpret_cast<uint4*>(smem), scr, threadIdx.x);
+        tdsc_row_u8<NT, RND>(P, J, idx, reinterpret_cast<uint4*>(smem), scr, threadIdx.x, &s_mbar[40], mpar, 2);
         done = 1;
       } else {
         tdsc_row_u8_long(P, J, idx, reinterpret_cast<uint4*>(smem), scr);
