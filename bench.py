@@ -356,7 +356,7 @@ def run_gpu(args):
 
 # per workload: the committed ncu summary of its kernel, the kernel's sources, its name
 PROFILES = {
-    2: ("engine_u8_arts12.md", ("common.cuh", "engine.h", "engine_u8.cu"),
+    2: ("engine_u8_arts12.md", ("common.cuh", "engine.h", "engine_u8_impl.cuh", "engine_u8.cu"),
         "k_engine_u8 (fused TDSC->FDSC persistent work queue)"),
     3: ("engine_f32_fp32x32.md", ("common.cuh", "engine.h", "engine_f32.cu"),
         "k_engine_f32 (fused TDSC->FDSC persistent work queue)"),
