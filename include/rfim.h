@@ -168,7 +168,9 @@ rfim_status rfim_destroy(rfim_ctx* ctx);
 /*
  * Set a tuning or test option (returns RFIM_ERR_ARG for an unknown key):
  *   "spin_limit_us"   limit of every device-side wait, microseconds (default 2e6);
- *   "schedule"        0 = auto, 1 = fused persistent (L2-resident re-read),
+ *   "schedule"        0 = auto (fused, or separate launches when every uint8
+ *                     row takes a quarter warp: rows of at most ~3,150 samples),
+ *                     1 = fused persistent (L2-resident re-read),
  *                     2 = separate launches (TDSC pass, then FDSC pass);
  *   "tile_samples"    FDSC tile width in time samples: 0 (automatic) or 1, 2, 4, 8, 16, 32
  *                     (uint8 tiles use at least 8, float32 tiles at most 8);
