@@ -57,19 +57,6 @@ __device__ __forceinline__ bool le_thr(unsigned long long lhs, unsigned long lon
   return ((u128)lhs << ne) <= q;
 }
 
-// Largest a in [0, amax] with (double)(mult * a^2) <= fl(k2 * (double)R).
-// Requires mult * amax^2 < 2^53.  a = 0 always qualifies.
-__device__ __forceinline__ unsigned max_keep(unsigned long long R, unsigned long long mult, unsigned amax,
-                                             const ExactK2& k) {
-  float est = sqrtf(k.k2f * (float)R / (float)mult);
-  long long a = (long long)est;
-  if (a > (long long)amax) a = amax;
-  if (a < 0) a = 0;
-  while (a < (long long)amax && le_thr(mult * (unsigned long long)(a + 1) * (unsigned long long)(a + 1), R, k)) a++;
-  while (a > 0 && !le_thr(mult * (unsigned long long)a * (unsigned long long)a, R, k)) a--;
-  return (unsigned)a;
-}
-
 // ---------------------------------------------------------------------------
 // SIMD-within-a-word helpers on 4 packed bytes.
 // ---------------------------------------------------------------------------
@@ -155,9 +142,6 @@ __device__ __forceinline__ uint32_t outside_fast(uint32_t x, const ByteKeep& k) 
 // 0x80 per byte -> 0xFF per byte
 __device__ __forceinline__ uint32_t widen80(uint32_t f) { return f | (f - (f >> 7)); }
 
-// 0x80 flags of a word -> 4 low bits (byte i -> bit i)
-__device__ __forceinline__ uint32_t bits4(uint32_t f) { return (((f >> 7) * 0x01020408u) >> 24) & 0xFu; }
-
 // 4 low bits -> 0x01 per selected byte
 __device__ __forceinline__ uint32_t bytes_from_bits4(uint32_t n) { return ((n & 0xFu) * 0x00204081u) & 0x01010101u; }
 
@@ -192,26 +176,6 @@ __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
-}
-
-template <typename T, int N>
-__device__ __forceinline__ void block_sum(T (&v)[N], T* scratch) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int i = 0; i < N; i++) v[i] = warp_sum(v[i]);
-  if (lane == 0) {
-#pragma unroll
-    for (int i = 0; i < N; i++) scratch[i * (NT / 32) + warp] = v[i];
-  }
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < N; i++) {
-    T s = 0;
-#pragma unroll
-    for (int w = 0; w < NT / 32; w++) s += scratch[i * (NT / 32) + w];
-    v[i] = s;
-  }
-  __syncthreads();
 }
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {

@@ -96,8 +96,6 @@ __device__ __forceinline__ FF ff_div_int(FF a, int g) {
   return r;
 }
 
-__device__ __forceinline__ double ff_d(FF a) { return (double)a.hi + (double)a.lo; }
-
 // a double as float-float (~2^-48 relative)
 __device__ __forceinline__ FF ff_from_d(double v) {
   const float hi = __double2float_rn(v);
@@ -210,54 +208,6 @@ struct Red32 {
   int flag;
 };
 
-// (a, b) summed over the CTA; every thread gets the result
-__device__ __forceinline__ void block_ff2(FF& a, FF& b, Red32* r) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  a = warp_ff(a);
-  b = warp_ff(b);
-  __syncthreads();
-  if (lane == 0) {
-    r->f[4 * warp + 0] = a.hi;
-    r->f[4 * warp + 1] = a.lo;
-    r->f[4 * warp + 2] = b.hi;
-    r->f[4 * warp + 3] = b.lo;
-  }
-  __syncthreads();
-  FF sa{0.f, 0.f}, sb{0.f, 0.f};
-#pragma unroll
-  for (int w = 0; w < NT / 32; w++) {
-    sa = ff_add(sa, FF{r->f[4 * w + 0], r->f[4 * w + 1]});
-    sb = ff_add(sb, FF{r->f[4 * w + 2], r->f[4 * w + 3]});
-  }
-  a = sa;
-  b = sb;
-}
-
-__device__ __forceinline__ double block_dsum(double v, Red32* r) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  __syncthreads();
-  if (lane == 0) r->d[warp] = v;
-  __syncthreads();
-  double s = 0.0;
-#pragma unroll
-  for (int w = 0; w < NT / 32; w++) s += r->d[w];
-  return s;
-}
-
-__device__ __forceinline__ int block_isum(int v, Red32* r) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  v = __reduce_add_sync(0xffffffffu, v);
-  __syncthreads();
-  if (lane == 0) r->i[warp] = v;
-  __syncthreads();
-  int s = 0;
-#pragma unroll
-  for (int w = 0; w < NT / 32; w++) s += r->i[w];
-  return s;
-}
-
 // ---------------------------------------------------------------------------
 // Thread groups of GN threads (a half CTA, or the whole CTA) that clean one
 // row each; h = group index, synchronised by named barrier 1 + h.
@@ -315,20 +265,6 @@ __device__ __forceinline__ int grp_isum(int v, Red32* r, int t, int h) {
 #pragma unroll
   for (int w = 0; w < GN / 32; w++) s += r->i[w];
   return s;
-}
-
-// ---------------------------------------------------------------------------
-// TDSC on one float32 row (the whole CTA)
-// ---------------------------------------------------------------------------
-// Shared memory: the row's 16-byte chunk grid (element i of the row at
-// st[head + i]), one flag nibble per chunk, the list of replaced values of the
-// current iteration.
-__device__ __forceinline__ float4 ld_f4_na(const float* p) {
-  float4 v;
-  asm volatile("ld.global.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-               : "l"(p));
-  return v;
 }
 
 __device__ __forceinline__ float f4_get(const float4& v, int i) {

@@ -83,49 +83,6 @@ __device__ __forceinline__ void or16_partial(uint8_t* dst, const uint4& v, int l
   for (int b = lo; b < hi; b++) dst[b] |= (uint8_t)(word_of(v, b >> 2) >> (8 * (b & 3)));
 }
 
-// n (<= 16) bytes of a row starting at global address a, bytes past n read as
-// 0.  Reads only inside [lo, hi).
-__device__ __forceinline__ uint4 load_seg16(const uint8_t* a, int n, const uint8_t* lo, const uint8_t* hi) {
-  const uintptr_t ia = (uintptr_t)a;
-  if (n == 16 && a >= lo && a + 16 <= hi) {
-    if ((ia & 15) == 0) return *reinterpret_cast<const uint4*>(a);
-    if ((ia & 3) == 0) {
-      const uint32_t* p = reinterpret_cast<const uint32_t*>(a);
-      return make_uint4(p[0], p[1], p[2], p[3]);
-    }
-    const int off = (int)(ia & 3);
-    const uint8_t* al = a - off;
-    if (al >= lo && al + 20 <= hi) {
-      const uint32_t* p = reinterpret_cast<const uint32_t*>(al);
-      const uint32_t w0 = p[0], w1 = p[1], w2 = p[2], w3 = p[3], w4 = p[4];
-      return make_uint4(__funnelshift_r(w0, w1, 8 * off), __funnelshift_r(w1, w2, 8 * off),
-                        __funnelshift_r(w2, w3, 8 * off), __funnelshift_r(w3, w4, 8 * off));
-    }
-  }
-  uint32_t w[4] = {0, 0, 0, 0};
-  for (int b = 0; b < n; b++) {
-    const uint8_t* p = a + b;
-    if (p >= lo && p < hi) w[b >> 2] |= (uint32_t)(*p) << (8 * (b & 3));
-  }
-  return make_uint4(w[0], w[1], w[2], w[3]);
-}
-
-// store n (<= 16) bytes of v to global address a
-__device__ __forceinline__ void store_seg16(uint8_t* a, const uint4& v, int n) {
-  const uintptr_t ia = (uintptr_t)a;
-  if (n == 16 && (ia & 15) == 0) {
-    *reinterpret_cast<uint4*>(a) = v;
-  } else if (n == 16 && (ia & 3) == 0) {
-    uint32_t* p = reinterpret_cast<uint32_t*>(a);
-    p[0] = v.x;
-    p[1] = v.y;
-    p[2] = v.z;
-    p[3] = v.w;
-  } else {
-    store16_partial(a, v, 0, n);
-  }
-}
-
 // ---------------------------------------------------------------------------
 // exact keep intervals, computed by a group of lanes in parallel
 // ---------------------------------------------------------------------------
@@ -183,21 +140,6 @@ __device__ __forceinline__ void tdsc_keep_warp(unsigned long long S, unsigned lo
   keep_from((unsigned)S, A, (unsigned)T, rcpT, lo, hi);
 }
 
-// ---------------------------------------------------------------------------
-// byte tests
-// ---------------------------------------------------------------------------
-// bit 7 of each byte set iff the byte is outside [lo, hi]; parity of hi - lo fixed
-template <bool ODD>
-__device__ __forceinline__ uint32_t outside_u(uint32_t x, const ByteKeep& k) {
-  const uint32_t d = absdiff4(x, k.m4);
-  uint32_t g = ((d & 0x7F7F7F7Fu) + k.k4) | d;
-  if (ODD) {
-    const uint32_t e = x ^ k.hi4;
-    g &= ((e & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | e;
-  }
-  return (g & 0x80808080u) | k.all;
-}
-
 // bit 7 of each byte set iff the byte is outside a non-empty [lo, hi]
 template <bool ODD>
 __device__ __forceinline__ uint32_t outside_ne(uint32_t x, const ByteKeep& k) {
@@ -239,11 +181,6 @@ __device__ __forceinline__ uint32_t sel_bytes(uint32_t x, uint32_t r4, uint32_t 
 
 __device__ __forceinline__ uint4 and4(const uint4& a, const uint4& b) {
   return make_uint4(a.x & b.x, a.y & b.y, a.z & b.z, a.w & b.w);
-}
-
-// byte flags (0x80 per byte) of a 16-byte chunk -> 16 bits, byte b -> bit b
-__device__ __forceinline__ uint32_t chunk_bits(const uint4& f) {
-  return bits4(f.x) | (bits4(f.y) << 4) | (bits4(f.z) << 8) | (bits4(f.w) << 12);
 }
 
 // ---------------------------------------------------------------------------
