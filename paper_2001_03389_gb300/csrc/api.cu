@@ -619,7 +619,7 @@ rfim_status rfim_set_option(rfim_ctx* ctx, const char* key, long long value) {
   } else if (k == "withhold_tdsc_done") {
     ctx->withhold = value ? 1 : 0;
   } else if (k == "smem_target") {
-    if (value < 16384 || value > 231424) return fail(ctx, RFIM_ERR_ARG, "smem_target out of range");
+    if (value < 16384 || value > MAX_SMEM_PER_CTA) return fail(ctx, RFIM_ERR_ARG, "smem_target out of range");
     ctx->smem_target = (int)value;
   } else if (k == "fused_lag") {
     if (value < 0 || value > 8) return fail(ctx, RFIM_ERR_ARG, "fused_lag must be in 0..8");
