@@ -105,6 +105,24 @@ def test_in_place(oracle, ctx):
     check(oracle, ctx, x, fd=fd, api="fdsc", in_place=True)
 
 
+@pytest.mark.parametrize("T", [1250, 3169, 12500])
+def test_schedules_agree_by_row_mode(oracle, ctx, T):
+    # automatic (separate launches when every row takes a quarter warp), fused
+    # and separate schedules all match the oracle
+    rng = np.random.default_rng(T)
+    x = noise_u8(rng, (3, 64, T))
+    x[:, 9, :] = np.clip(x[:, 9, :].astype(int) + 60, 0, 255)
+    td = dict(k=3.0, iterations=2, replace="median")
+    fd = dict(k=3.0, iterations=2, replace="median", bin=32)
+    try:
+        for sched in (0, 1, 2):
+            ctx.set_option("schedule", sched)
+            check(oracle, ctx, x, td=td, fd=fd)
+            check(oracle, ctx, x, td=dict(td, replace="mean"), fd=dict(fd, replace="mean"), mask_fmt="bytes")
+    finally:
+        ctx.set_option("schedule", 0)
+
+
 def test_long_rows_read_from_memory(oracle, ctx):
     # rows beyond the on-chip stage (98,273 samples): every pass reads the row
     # from memory; misaligned, in place, byte masks, fused with FDSC
