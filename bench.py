@@ -25,12 +25,15 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-CFG = 2  # the ARTS batch; --config 3 times the float32 workload instead
+ARTS = "arts_12x1536x12500_u8"  # the reported workload: the ARTS batch
+FP32 = "fp32_32x4096x8192"  # the float32 workload (--workload)
+WORKLOAD = ARTS
 METRIC = "cleaned filterbank GB/s (TDSC+FDSC) & % HBM peak; p99 chunk latency"
 UNIT = "GB/s"
 NOMINAL_HBM_GBS = 8000.0
@@ -61,16 +64,14 @@ def dist_env():
 def workload_config():
     from paper_2001_03389_gb300 import synth
 
-    spec = synth.CONFIGS[CFG]
-    return spec
+    return synth.WORKLOADS[WORKLOAD]
 
 
 def config_json(spec, n):
     es = 1 if spec["dtype"] == "u8" else 4
     mb = spec["B"] * spec["C"] * spec["T"] * es / 1e6
-    name = "arts" if CFG == 2 else "fp32"
     return {
-        "workload": f"{name}_{spec['B']}x{spec['C']}x{spec['T']}_{spec['dtype']}_bct_tdsc_then_fdsc",
+        "workload": f"{spec['name']}_bct_tdsc_then_fdsc",
         "beams": spec["B"], "channels": spec["C"], "samples": spec["T"], "dtype": spec["dtype"], "layout": "BCT",
         "tdsc": spec["tdsc"], "fdsc": spec["fdsc"], "mask": "bits",
         "global_batch": spec["B"] * n, "parallelism": f"replicas{n}" if n > 1 else "single",
@@ -89,7 +90,7 @@ class Clocks:
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"rfim_bench_clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -158,7 +159,7 @@ def cpu_baseline(spec, budget_s=15.0):
 
     tot_t, tot_b, nb = 0.0, 0, 0
     while nb < spec["B"] and tot_t < budget_s:
-        x = synth.make_beams(CFG, beams=[nb])
+        x = synth.make_beams(WORKLOAD, beams=[nb])
         t0 = time.perf_counter()
         oracle.clean(x, "bct", tdsc=spec["tdsc"], fdsc=spec["fdsc"])
         tot_t += time.perf_counter() - t0
@@ -176,7 +177,7 @@ def run_reference(args):
     spec = workload_config()
     from paper_2001_03389_gb300 import synth
 
-    x = synth.make_beams(CFG, beams=[0])
+    x = synth.make_beams(WORKLOAD, beams=[0])
     K, W = args.steps, args.warmup
     # size each step so the whole run stays within about two minutes
     t_small, b_small = oracle_time_sample(x, spec, 128)
@@ -230,11 +231,11 @@ def run_gpu(args):
         spec["B"] = args.beams  # a smaller batch of the same beams (profiling captures)
     B, C, T = spec["B"], spec["C"], spec["T"]
     if spec["dtype"] == "u8":
-        x = synth.make_beams(CFG, beams=range(B))
+        x = synth.make_beams(WORKLOAD, beams=range(B))
         xin = torch.from_numpy(x).to(dev)
     else:
         # 4.3 GB: drawn on the device (same model; the oracle timing uses the numpy beams)
-        xin = synth.torch_make_beams(CFG, B, synth.seed_of(CFG), dev)
+        xin = synth.torch_make_beams(WORKLOAD, B, synth.seed_of(WORKLOAD), dev)
         x = xin.cpu().numpy()
     nbytes = x.nbytes
     out = torch.empty_like(xin)
@@ -336,14 +337,14 @@ def run_gpu(args):
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": f"{peak_kind} copy (MEASURED_PEAKS.json hbm_gbs)",
                          "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS,
-                         "kernel": PROFILES[CFG][2],
+                         "kernel": PROFILES[WORKLOAD][2],
                          "alg_bytes_per_launch": alg, "avg_launch_ms": avg_launch_ms},
             "e2e": e2e, "e2e_matches_device": ok,
             "gpu_launches": K,
         }
         if clk:
             res["clocks"] = clk
-        if CFG == 2 and not args.no_stream and ws == 1:
+        if WORKLOAD == ARTS and not args.no_stream and ws == 1:
             res["streaming"] = run_stream_bench(rfim, synth, dev)
         if not args.no_cpu_baseline and ws == 1:
             res["cpu_baseline"] = cpu_baseline(spec)
@@ -356,9 +357,9 @@ def run_gpu(args):
 
 # per workload: the committed ncu summary of its kernel, the kernel's sources, its name
 PROFILES = {
-    2: ("engine_u8_arts12.md", ("common.cuh", "engine.h", "engine_u8_impl.cuh", "engine_u8.cu"),
+    ARTS: ("engine_u8_arts12.md", ("common.cuh", "engine.h", "engine_u8_impl.cuh", "engine_u8.cu"),
         "k_engine_u8 (fused TDSC->FDSC persistent work queue)"),
-    3: ("engine_f32_fp32x32.md", ("common.cuh", "engine.h", "engine_f32.cu"),
+    FP32: ("engine_f32_fp32x32.md", ("common.cuh", "engine.h", "engine_f32.cu"),
         "k_engine_f32 (fused TDSC->FDSC persistent work queue)"),
 }
 
@@ -379,7 +380,7 @@ def run_stream_bench(rfim, synth, dev, rates=(10, 25, 50, 100), duration_s=0.5, 
     gen = torch.Generator(device=dev)
     gen.manual_seed(seed)
     pool = torch.empty((n_beams * per_beam, C, T), dtype=torch.uint8, device=dev)
-    model = synth.cfg2_model()
+    model = synth.arts_model()
     for i in range(pool.shape[0]):
         pool[i] = synth.torch_beam_u8(gen, C, T, model, dev)
     torch.cuda.synchronize()
@@ -420,7 +421,7 @@ def run_stream_bench(rfim, synth, dev, rates=(10, 25, 50, 100), duration_s=0.5, 
 def profiled_traffic():
     """DRAM bytes per launch of the engine kernel from the committed ncu summary,
     or None when the kernel sources changed since that capture."""
-    prof = os.path.join(ROOT, "profiles", PROFILES[CFG][0])
+    prof = os.path.join(ROOT, "profiles", PROFILES[WORKLOAD][0])
     if not os.path.exists(prof):
         return None
     vals = {}
@@ -445,7 +446,7 @@ def source_hash():
 
     h = hashlib.sha256()
     cs = os.path.join(ROOT, "paper_2001_03389_gb300", "csrc")
-    for f in PROFILES[CFG][1]:
+    for f in PROFILES[WORKLOAD][1]:
         with open(os.path.join(cs, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -454,9 +455,9 @@ def source_hash():
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=None, help="timed steps (default 2000, or 300 with --config 3)")
-    ap.add_argument("--config", type=int, default=2, choices=[2, 3],
-                    help="2: the ARTS uint8 batch (the reported workload); 3: the float32 workload")
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default 2000, or 300 for the float32 workload)")
+    ap.add_argument("--workload", default=ARTS, choices=[ARTS, FP32],
+                    help=f"{ARTS}: the ARTS uint8 batch (the reported workload); {FP32}: the float32 workload")
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--beams", type=int, default=None, help="clean only the first N beams (profiling captures)")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
@@ -464,10 +465,10 @@ def main():
     ap.add_argument("--no-stream", action="store_true", help="skip the streaming-service measurement")
     ap.add_argument("--profile", action="store_true", help="warm-up and plain steps only (for ncu captures)")
     args = ap.parse_args()
-    global CFG
-    CFG = args.config
+    global WORKLOAD
+    WORKLOAD = args.workload
     if args.steps is None:
-        args.steps = 2000 if CFG == 2 else 300
+        args.steps = 2000 if WORKLOAD == ARTS else 300
     if args.impl == "reference":
         run_reference(args)
     else:

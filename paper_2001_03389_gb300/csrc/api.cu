@@ -202,14 +202,14 @@ rfim_status check_block(rfim_ctx* ctx, const rfim_block* b, const CutNorm& td, c
   return RFIM_OK;
 }
 
-// Engine limits of this build.
+// Engine limits (shapes the kernels do not take).
 rfim_status check_impl(rfim_ctx* ctx, const rfim_block* b, const CutNorm& td, const CutNorm& fd) {
   if (b->layout != RFIM_LAYOUT_BCT)
     return fail(ctx, RFIM_ERR_ARG, "BTC blocks are cleaned through a context's BCT scratch (not here)");
   if (b->dtype == RFIM_F32) {
     if (td.on && td.rep == RFIM_REPLACE_RANDOM && b->samples > TD32_MAX_T)
       return fail(ctx, RFIM_ERR_ARG, "float32 TDSC with random replacement: rows longer than %d samples are not "
-                  "available in this build", TD32_MAX_T);
+                  "supported", TD32_MAX_T);
     if (fd.on) {
       const int C = b->channels, nb = (C + fd.bin - 1) / fd.bin;
       if (fd32_smem_bytes(1, C, nb, fd.rep == RFIM_REPLACE_RANDOM) > MAX_SMEM_PER_CTA)
@@ -221,7 +221,7 @@ rfim_status check_impl(rfim_ctx* ctx, const rfim_block* b, const CutNorm& td, co
     return fail(ctx, RFIM_ERR_RANGE, "TDSC rows longer than %lld samples are not available", TD_MAX_T);
   if (td.on && td.rep == RFIM_REPLACE_RANDOM && td_random_row_mode(b->samples) < 0)
     return fail(ctx, RFIM_ERR_ARG, "uint8 TDSC with random replacement: rows longer than 78609 samples are not "
-                "available in this build");
+                "supported");
   if (fd.on) {
     // the smallest FDSC tile (8 samples x all channels) must fit one CTA's shared memory
     const int C = b->channels, nb = (C + fd.bin - 1) / fd.bin;

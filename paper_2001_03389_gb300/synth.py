@@ -20,8 +20,10 @@ Recipe (the paper's own data are not available; these stand in for them):
     samples.
   * ARTS shapes: 1536 channels, 81.92 us sampling (Sec. V-A footnote),
     12 beams per node (Sec. V-B).
-Seeds: configuration i uses SeedSequence(2001033890 + i); beam j draws from
-child j of that sequence, so any subset of beams can be regenerated alone.
+Seeds: each workload has its own SeedSequence (2001033891 for the small
+canvas, ...92 for the ARTS batch, ...93 for the float32 batch, ...94 for the
+ragged batch, ...95 for streaming chunks); beam j draws from child j of that
+sequence, so any subset of beams can be regenerated alone.
 """
 from __future__ import annotations
 
@@ -56,8 +58,8 @@ def _dispersion_delays(C: int, span: int) -> np.ndarray:
     return np.rint(d * span).astype(np.int64)
 
 
-def _beam_rng(cfg_seed: int, beam: int) -> np.random.Generator:
-    ss = np.random.SeedSequence(cfg_seed, spawn_key=(beam,))
+def _beam_rng(seed: int, beam: int) -> np.random.Generator:
+    ss = np.random.SeedSequence(seed, spawn_key=(beam,))
     return np.random.Generator(np.random.PCG64(ss))
 
 
@@ -89,9 +91,9 @@ def _rfi_offsets(rng, C: int, T: int, m: RFIModel, scale: np.ndarray | float):
     return add * scale
 
 
-def beam_u8(cfg_seed: int, beam: int, C: int, T: int, model: RFIModel, layout: str = "bct") -> np.ndarray:
+def beam_u8(seed: int, beam: int, C: int, T: int, model: RFIModel, layout: str = "bct") -> np.ndarray:
     """One uint8 beam: round(N(128,16^2) + RFI) clipped to [0,255]; (C,T) or (T,C)."""
-    rng = _beam_rng(cfg_seed, beam)
+    rng = _beam_rng(seed, beam)
     x = rng.standard_normal((C, T), dtype=np.float32)
     x *= 16.0
     x += 128.0
@@ -102,9 +104,9 @@ def beam_u8(cfg_seed: int, beam: int, C: int, T: int, model: RFIModel, layout: s
     return np.ascontiguousarray(out.T) if layout == "btc" else out
 
 
-def beam_f32(cfg_seed: int, beam: int, C: int, T: int, model: RFIModel, layout: str = "bct") -> np.ndarray:
+def beam_f32(seed: int, beam: int, C: int, T: int, model: RFIModel, layout: str = "bct") -> np.ndarray:
     """One float32 beam: g_c chi^2_2 noise plus RFI in multiples of sigma_c = 2 g_c."""
-    rng = _beam_rng(cfg_seed, beam)
+    rng = _beam_rng(seed, beam)
     g = np.exp(rng.uniform(np.log(0.5), np.log(2.0), size=C)).astype(np.float32)
     x = rng.standard_exponential((C, T), dtype=np.float32)
     x *= 2.0                       # chi^2 with 2 degrees of freedom
@@ -117,67 +119,75 @@ def beam_f32(cfg_seed: int, beam: int, C: int, T: int, model: RFIModel, layout: 
 # The paper-shaped workloads.
 # ---------------------------------------------------------------------------
 
-def cfg1_model() -> RFIModel:
+def small_canvas_model() -> RFIModel:
     # 3 persistent narrowband channels at +60, 5 broadband impulses 4 samples wide at +90,
     # one dispersed pulse at +20.
     return RFIModel(nb_count=3, nb_amp=60.0, nb_sine=False, bb_count=5, bb_width=4, bb_amp=90.0,
                     disp_amp=20.0, disp_span=300)
 
 
-def cfg2_model() -> RFIModel:
+def arts_model() -> RFIModel:
     # 2% of channels sinusoidal narrowband around +60, 1% of samples broadband +90, one pulse.
     return RFIModel(nb_frac=0.02, nb_amp=60.0, nb_sine=True, bb_frac=0.01, bb_width=1, bb_amp=90.0,
                     disp_amp=20.0, disp_span=300)
 
 
-def cfg3_model() -> RFIModel:
+def fp32_model() -> RFIModel:
     # Same mix at 5x density, amplitudes as multiples of sigma_c: 60/16 = 3.75, 90/16 = 5.625, 20/16 = 1.25.
     return RFIModel(nb_frac=0.10, nb_amp=3.75, nb_sine=True, bb_frac=0.05, bb_width=1, bb_amp=5.625,
                     disp_amp=1.25, disp_span=300)
 
 
-CONFIGS = {
-    1: dict(name="tdsc_1x64x2048_u8", dtype="u8", B=1, C=64, T=2048, model=cfg1_model,
-            tdsc=dict(k=3.0, iterations=1, replace="mean"), fdsc=None),
-    2: dict(name="arts_12x1536x12500_u8", dtype="u8", B=12, C=1536, T=12500, model=cfg2_model,
-            tdsc=dict(k=3.0, iterations=2, replace="median"),
-            fdsc=dict(k=3.0, iterations=2, replace="median", bin=32)),
-    3: dict(name="fp32_32x4096x8192", dtype="f32", B=32, C=4096, T=8192, model=cfg3_model,
-            tdsc=dict(k=2.5, iterations=3, replace="mean"),
-            fdsc=dict(k=2.5, iterations=3, replace="mean", bin=32)),
+# The workloads, named by what they are: a small uint8 canvas for TDSC, the
+# ARTS batch (12 beams of 1536 channels x 12,500 samples, Sec. V-B), and a
+# float32 batch of the same cut at larger size.
+SMALL = "tdsc_1x64x2048_u8"
+ARTS = "arts_12x1536x12500_u8"
+FP32 = "fp32_32x4096x8192"
+WORKLOADS = {
+    SMALL: dict(name=SMALL, dtype="u8", B=1, C=64, T=2048, model=small_canvas_model, seed=SEED_BASE + 1,
+                tdsc=dict(k=3.0, iterations=1, replace="mean"), fdsc=None),
+    ARTS: dict(name=ARTS, dtype="u8", B=12, C=1536, T=12500, model=arts_model, seed=SEED_BASE + 2,
+               tdsc=dict(k=3.0, iterations=2, replace="median"),
+               fdsc=dict(k=3.0, iterations=2, replace="median", bin=32)),
+    FP32: dict(name=FP32, dtype="f32", B=32, C=4096, T=8192, model=fp32_model, seed=SEED_BASE + 3,
+               tdsc=dict(k=2.5, iterations=3, replace="mean"),
+               fdsc=dict(k=2.5, iterations=3, replace="mean", bin=32)),
 }
+RAGGED_SEED = SEED_BASE + 4  # the ragged batch
+STREAM_SEED = SEED_BASE + 5  # streaming chunks
 
 
-def seed_of(cfg: int) -> int:
-    return SEED_BASE + cfg
+def seed_of(workload: str) -> int:
+    return WORKLOADS[workload]["seed"]
 
 
-def make_beams(cfg: int, beams=None, layout: str = "bct"):
-    """Generate beams of a fixed-shape configuration (1..3) as one (b, C, T) array."""
-    spec = CONFIGS[cfg]
+def make_beams(workload: str, beams=None, layout: str = "bct"):
+    """Generate beams of a fixed-shape workload as one (b, C, T) array."""
+    spec = WORKLOADS[workload]
     ids = list(range(spec["B"])) if beams is None else list(beams)
     fn = beam_u8 if spec["dtype"] == "u8" else beam_f32
     model = spec["model"]()
-    return np.stack([fn(seed_of(cfg), j, spec["C"], spec["T"], model, layout) for j in ids])
+    return np.stack([fn(spec["seed"], j, spec["C"], spec["T"], model, layout) for j in ids])
 
 
 def ragged_shapes(n: int = 200, seed: int | None = None):
     """Shapes of the ragged batch: C from {384, 768, 1536, 4096}, T ~ U[1000, 25000]."""
-    rng = np.random.Generator(np.random.PCG64(seed_of(4) if seed is None else seed))
+    rng = np.random.Generator(np.random.PCG64(RAGGED_SEED if seed is None else seed))
     Cs = rng.choice([384, 768, 1536, 4096], size=n)
     Ts = rng.integers(1000, 25001, size=n)
     return [(int(c), int(t)) for c, t in zip(Cs, Ts)]
 
 
 def ragged_beam(j: int, C: int, T: int, layout: str = "bct") -> np.ndarray:
-    """Beam j of the ragged batch, config-2 noise and RFI model."""
-    return beam_u8(seed_of(4), j, C, T, cfg2_model(), layout)
+    """Beam j of the ragged batch, ARTS noise and RFI model."""
+    return beam_u8(RAGGED_SEED, j, C, T, arts_model(), layout)
 
 
 def stream_chunk(beam: int, chunk: int, C: int = 1536, T: int = 1250) -> np.ndarray:
-    """Chunk `chunk` of streaming beam `beam` (config-2 model), shape (C, T)."""
-    rng_seed = seed_of(5) * 1_000_003 + beam
-    return beam_u8(rng_seed, chunk, C, T, cfg2_model())
+    """Chunk `chunk` of streaming beam `beam` (ARTS model), shape (C, T)."""
+    rng_seed = STREAM_SEED * 1_000_003 + beam
+    return beam_u8(rng_seed, chunk, C, T, arts_model())
 
 
 # ---------------------------------------------------------------------------
@@ -239,11 +249,11 @@ def torch_beam_f32(gen, C: int, T: int, model: RFIModel, device):
     return x.mul_(g)
 
 
-def torch_make_beams(cfg: int, beams: int, seed: int, device):
-    """A (beams, C, T) device block of a fixed-shape configuration, drawn on the device."""
+def torch_make_beams(workload: str, beams: int, seed: int, device):
+    """A (beams, C, T) device block of a fixed-shape workload, drawn on the device."""
     import torch
 
-    spec = CONFIGS[cfg]
+    spec = WORKLOADS[workload]
     gen = torch.Generator(device=device)
     gen.manual_seed(seed)
     fn = torch_beam_u8 if spec["dtype"] == "u8" else torch_beam_f32
@@ -255,14 +265,14 @@ def torch_make_beams(cfg: int, beams: int, seed: int, device):
 
 
 def torch_ragged_batch(shapes, seed: int, device, layout: str = "bct"):
-    """Beams of the given (C, T) shapes, config-2 model, as separate device tensors."""
+    """Beams of the given (C, T) shapes, ARTS model, as separate device tensors."""
     import torch
 
     gen = torch.Generator(device=device)
     gen.manual_seed(seed)
     out = []
     for C, T in shapes:
-        b = torch_beam_u8(gen, C, T, cfg2_model(), device)
+        b = torch_beam_u8(gen, C, T, arts_model(), device)
         out.append(b.t().contiguous() if layout == "btc" else b)
     return out
 

@@ -172,14 +172,14 @@ def test_f32_many_k(oracle, ctx):
         check_f32(oracle, ctx, x, td=dict(k=k, iterations=2, replace="median"), fd=dict(k=k, iterations=2, bin=5))
 
 
-def test_cfg3_full_beam(oracle, ctx):
+def test_fp32_workload_full_beam(oracle, ctx):
     # one full beam of the float32 configuration: 4096 x 8192, fused, k = 2.5, 3 iterations, mean
     from paper_2001_03389_gb300 import synth
 
-    spec = synth.CONFIGS[3]
-    x = synth.make_beams(3, beams=[0])
+    spec = synth.WORKLOADS[synth.FP32]
+    x = synth.make_beams(synth.FP32, beams=[0])
     nd = check_f32(oracle, ctx, x, td=spec["tdsc"], fd=spec["fdsc"])
-    print(f"cfg3 beam 0: {nd} allowed mask disagreements")
+    print(f"float32 workload, beam 0: {nd} allowed mask disagreements")
 
 
 def test_f32_tile_widths(oracle, ctx):

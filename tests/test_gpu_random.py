@@ -112,8 +112,8 @@ def test_random_u8_full_beam(oracle, ctx):
     # two whole beams of the ARTS batch (1536 x 12500), both methods random
     from paper_2001_03389_gb300 import synth
 
-    x = synth.make_beams(2, beams=[0, 7])
-    spec = synth.CONFIGS[2]
+    x = synth.make_beams(synth.ARTS, beams=[0, 7])
+    spec = synth.WORKLOADS[synth.ARTS]
     td = dict(spec["tdsc"], replace="random")
     fd = dict(spec["fdsc"], replace="random")
     want, wf = check_u8(oracle, ctx, x, td=td, fd=fd)

@@ -38,11 +38,11 @@ def check(oracle, ctx, x, td=None, fd=None, mask_fmt="bits", **kw):
         assert np.array_equal(gf, wf), f"byte mask differs at {np.argwhere(gf != wf)[:3].tolist()}"
 
 
-def test_cfg1_paper_canvas(oracle, ctx):
+def test_small_paper_canvas(oracle, ctx):
     from paper_2001_03389_gb300 import synth
 
-    x = synth.make_beams(1)
-    spec = synth.CONFIGS[1]
+    x = synth.make_beams(synth.SMALL)
+    spec = synth.WORKLOADS[synth.SMALL]
     check(oracle, ctx, x, td=spec["tdsc"], api="tdsc")
     check(oracle, ctx, x, td=spec["tdsc"])
 
@@ -163,24 +163,24 @@ def test_many_k_values(oracle, ctx):
         check(oracle, ctx, x, td=dict(k=k, iterations=2, replace="median"), fd=dict(k=k, iterations=2, bin=5))
 
 
-def test_cfg2_full_beam(oracle, ctx):
+def test_arts_full_beam(oracle, ctx):
     # one full ARTS-shaped beam: 1536 x 12500, TDSC then FDSC, k=3, 2 iterations, median, bit mask
     from paper_2001_03389_gb300 import synth
 
-    spec = synth.CONFIGS[2]
-    x = synth.make_beams(2, beams=[0])
+    spec = synth.WORKLOADS[synth.ARTS]
+    x = synth.make_beams(synth.ARTS, beams=[0])
     check(oracle, ctx, x, td=spec["tdsc"], fd=spec["fdsc"])
 
 
-def test_cfg2_full_size_sampled(oracle, ctx):
+def test_arts_full_size_sampled(oracle, ctx):
     # all 12 beams in the launch the benchmark times; beams 0 and 11 against the oracle
     import torch
 
     from gpu_util import unpack_bits
     from paper_2001_03389_gb300 import rfim, synth
 
-    spec = synth.CONFIGS[2]
-    x = synth.make_beams(2)
+    spec = synth.WORKLOADS[synth.ARTS]
+    x = synth.make_beams(synth.ARTS)
     B, C, T = x.shape
     dev = torch.device("cuda:0")
     xin = torch.from_numpy(x).to(dev)

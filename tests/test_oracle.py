@@ -397,15 +397,15 @@ def test_validation(oracle):
 
 
 # ---------------------------------------------------------------------------
-# the qualitative results of Sec. V-A on the paper-shaped canvas (config 1)
+# the qualitative results of Sec. V-A on the paper-shaped 1 x 64 x 2048 canvas
 # ---------------------------------------------------------------------------
 
 
-def _cfg1_truth():
-    """Recreate config 1's RFI positions from the generator's own draws."""
-    spec = synth.CONFIGS[1]
+def _small_canvas_truth():
+    """Recreate the small canvas's RFI positions from the generator's own draws."""
+    spec = synth.WORKLOADS[synth.SMALL]
     m = spec["model"]()
-    rng = synth._beam_rng(synth.seed_of(1), 0)
+    rng = synth._beam_rng(synth.seed_of(synth.SMALL), 0)
     rng.standard_normal((spec["C"], spec["T"]), dtype=np.float32)
     chans = rng.choice(spec["C"], size=m.nb_count, replace=False)
     starts = rng.choice(spec["T"] - m.bb_width + 1, size=m.bb_count, replace=False)
@@ -414,10 +414,10 @@ def _cfg1_truth():
     return chans, starts, t0 + delays
 
 
-def test_paper_accuracy_claims_cfg1(oracle):
-    x = synth.make_beams(1)
+def test_paper_accuracy_claims_small_canvas(oracle):
+    x = synth.make_beams(synth.SMALL)
     C, T = x.shape[1:]
-    chans, starts, pulse_t = _cfg1_truth()
+    chans, starts, pulse_t = _small_canvas_truth()
     bb = np.zeros(T, bool)
     for s in starts:
         bb[s:s + 4] = True

@@ -26,7 +26,7 @@ def test_noalloc_matches_rfim_clean_twice():
 
     torch.cuda.set_device(0)
     dev = torch.device("cuda:0")
-    x = torch.from_numpy(synth.make_beams(2, beams=[0, 1])[:, :, :3001].copy()).to(dev)  # 2 x 1536 x 3001
+    x = torch.from_numpy(synth.make_beams(synth.ARTS, beams=[0, 1])[:, :, :3001].copy()).to(dev)  # 2 x 1536 x 3001
     B, C, T = x.shape
     td = rfim.make_cut(3.0, 2, "median")
     fd = rfim.make_cut(3.0, 2, "median", 32)
