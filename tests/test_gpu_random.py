@@ -191,3 +191,48 @@ def test_clean_random_f32(oracle, ctx):
     nd, wf = check_f32(oracle, ctx, x, td=dict(k=2.5, iterations=2, replace="random"),
                        fd=dict(k=2.5, iterations=2, replace="random", bin=32))
     assert (wf & 1).any() and (wf & 2).any()
+
+
+def test_random_through_batch_graph_and_noalloc(oracle, ctx):
+    # the draws are keyed by the beam's index within its block: a ragged batch
+    # of one-beam blocks and one three-beam block, eager, captured, replayed and
+    # autotuned, and the allocation-free entry point, all match the oracle
+    import ctypes
+
+    import torch
+
+    from gpu_util import unpack_bits
+    from paper_2001_03389_gb300 import rfim
+
+    rng = np.random.default_rng(21)
+    td = dict(k=2.5, iterations=2, replace="random")
+    fd = dict(k=2.5, iterations=2, replace="random", bin=32)
+    xs = [rfi_u8(rng, (1, 384, 1000)), rfi_u8(rng, (3, 96, 2500)), rfi_u8(rng, (1, 768, 13001)),
+          rfi_u8(rng, (1, 64, 333))]
+    wants = [oracle.clean(x, "bct", tdsc=td, fdsc=fd) for x in xs]
+    dev = torch.device("cuda:0")
+    tdc, fdc = rfim.make_cut(**td), rfim.make_cut(**fd)
+    for flags in (0, rfim.BATCH_GRAPH, rfim.BATCH_GRAPH, rfim.BATCH_AUTOTUNE | rfim.BATCH_GRAPH):
+        ins = [torch.from_numpy(x).to(dev) for x in xs]
+        outs = [torch.full_like(x, 0x5A) for x in ins]
+        masks = [torch.full((rfim.mask_words(x.shape[1], x.shape[2], x.shape[0]),), -1, dtype=torch.int32,
+                            device=dev) for x in ins]
+        blks = [rfim.Context.block(i, o, m, "bct", "bits") for i, o, m in zip(ins, outs, masks)]
+        ctx.clean_batch(blks, tdc, fdc, flags=flags)
+        torch.cuda.synchronize()
+        for x, o, m, (want, wf) in zip(xs, outs, masks, wants):
+            B, C, T = x.shape
+            assert np.array_equal(o.cpu().numpy(), want), (flags, x.shape)
+            assert np.array_equal(unpack_bits(m.cpu().numpy(), B * C, T).reshape(x.shape), wf > 0), (flags, x.shape)
+    assert ctx.device_status() == rfim.OK
+    # allocation-free entry point, the three-beam block
+    x, (want, wf) = xs[1], wants[1]
+    xin = torch.from_numpy(x).to(dev)
+    out = torch.full_like(xin, 7)
+    mask = torch.full((rfim.mask_words(x.shape[1], x.shape[2], x.shape[0]),), -1, dtype=torch.int32, device=dev)
+    blk = rfim.Context.block(xin, out, mask, "bct", "bits")
+    assert rfim.rfim_clean_noalloc(ctypes.byref(blk), ctypes.byref(tdc), ctypes.byref(fdc), None) == rfim.OK
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), want)
+    assert np.array_equal(unpack_bits(mask.cpu().numpy(), x.shape[0] * x.shape[1], x.shape[2]).reshape(x.shape),
+                          wf > 0)
