@@ -201,9 +201,11 @@ rfim_status rfim_tdsc(rfim_ctx* ctx, const rfim_block* blk, const rfim_cut* cut,
 rfim_status rfim_fdsc(rfim_ctx* ctx, const rfim_block* blk, const rfim_cut* cut, void* stream);
 
 /*
- * TDSC (all iterations) then FDSC (all iterations) in one pass over the data:
- * a persistent kernel whose FDSC work items re-read each beam's TDSC output
- * while it is resident in L2.  Either cut may be NULL to skip that method.
+ * TDSC (all iterations) then FDSC (all iterations).  By default one persistent
+ * kernel whose FDSC work items re-read each beam's TDSC output while it is
+ * resident in L2; blocks whose rows are all short (at most ~3,150 samples)
+ * run as two launches, TDSC then FDSC, which is faster there (option
+ * "schedule").  Either cut may be NULL to skip that method.
  */
 rfim_status rfim_clean(rfim_ctx* ctx, const rfim_block* blk, const rfim_cut* tdsc, const rfim_cut* fdsc,
                        void* stream);
@@ -213,9 +215,10 @@ rfim_status rfim_clean(rfim_ctx* ctx, const rfim_block* blk, const rfim_cut* tds
 #define RFIM_BATCH_AUTOTUNE 2u /* time candidate tilings per shape on first use, cache the winner */
 
 /*
- * Clean n blocks of possibly different shapes (same dtype and layout) in ONE
- * persistent launch with a device work queue (ragged batching).  Results equal
- * n separate rfim_clean calls bit for bit.  The descriptor table is uploaded
+ * Clean n blocks of possibly different shapes (same dtype and layout) in one
+ * persistent launch with a device work queue (ragged batching; two launches,
+ * TDSC then FDSC, when every row is short, and a launch per 160 beams).
+ * Results equal n separate rfim_clean calls bit for bit.  The descriptor table is uploaded
  * with the launch; with RFIM_BATCH_GRAPH the upload and launch are captured
  * once per distinct batch (same pointers and shapes) and replayed afterwards.
  */
@@ -280,7 +283,8 @@ rfim_status rfim_device_status(rfim_ctx* ctx, void* stream);
  *     (rfim_create; 0 = a quarter of the free device memory), at most four per
  *     beam.  A chunk is admitted only when a slot is free.
  *   - A dispatcher thread launches everything waiting (up to 160 chunks) as
- *     one micro-batch on whichever of four CUDA streams is idle, so batches
+ *     one micro-batch (TDSC and FDSC as two launches for short chunks) on
+ *     whichever of four CUDA streams is idle, so batches
  *     overlap on the device; completion is signalled from the stream.
  *   - Per beam the service keeps the count of chunks and the latency of the
  *     last one.  Statistics of earlier chunks never enter a decision.
