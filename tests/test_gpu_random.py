@@ -236,3 +236,18 @@ def test_random_through_batch_graph_and_noalloc(oracle, ctx):
     assert np.array_equal(out.cpu().numpy(), want)
     assert np.array_equal(unpack_bits(mask.cpu().numpy(), x.shape[0] * x.shape[1], x.shape[2]).reshape(x.shape),
                           wf > 0)
+
+
+def test_random_f32_btc(oracle, ctx):
+    # float32 BTC blocks go through the BCT scratch: the draws keep the beam,
+    # channel and sample indices of the block
+    rng = np.random.default_rng(31)
+    x = np.ascontiguousarray(chi2_f32(rng, (2, 96, 300)).transpose(0, 2, 1))  # (B, T, C)
+    td = dict(k=2.5, iterations=2, replace="random")
+    fd = dict(k=2.5, iterations=2, replace="random", bin=32)
+    want, wf, margin = oracle.clean_f32_margin(x, "btc", tdsc=td, fdsc=fd)
+    got, gf = run_gpu(ctx, x, layout="btc", tdsc=td, fdsc=fd)
+    dis = gf != (wf > 0)
+    assert not (dis & ~(margin <= MARGIN)).any()
+    if not dis.any():
+        assert np.array_equal(got.view(np.uint32), want.view(np.uint32))

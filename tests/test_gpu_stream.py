@@ -201,3 +201,42 @@ def test_stream_replay_schedule(lib):
         ctx.stream_close()
     finally:
         ctx.close()
+
+
+def test_stream_random_replacement_matches_oracle(lib, oracle):
+    # random replacement through the service: each chunk is a block of one
+    # beam (index 0 for the draws), alone or inside a micro-batch
+    import torch
+
+    from gpu_util import unpack_bits
+
+    rfim = lib
+    C, T = 64, 1250
+    td = dict(k=2.5, iterations=2, replace="random")
+    fd = dict(k=2.5, iterations=2, replace="random", bin=32)
+    ctx = rfim.Context(0)
+    try:
+        ctx.stream_open(4, C, T, rfim.U8, rfim.make_cut(**td), rfim.make_cut(**fd))
+        pool = chunks_u8(12, C, T, seed=23)
+        results, tickets = {}, []
+        for i in range(12):
+            tk = None
+            while tk is None:
+                tk = ctx.stream_push(i % 4, pool[i], time.monotonic())
+                if tk is None:  # no slot: finish the oldest
+                    j, tj = tickets.pop(0)
+                    results[j] = result(rfim, ctx, tj, C, T, rfim.U8)
+                    ctx.stream_release(tj)
+            tickets.append((i, tk))
+        for i, tk in tickets:
+            results[i] = result(rfim, ctx, tk, C, T, rfim.U8)
+            ctx.stream_release(tk)
+        assert sorted(results) == list(range(12))
+        for i, (out, mask) in results.items():
+            want, wf = oracle.clean(pool[i].cpu().numpy()[None], "bct", tdsc=td, fdsc=fd)
+            assert np.array_equal(out.reshape(1, C, T), want), i
+            assert np.array_equal(unpack_bits(mask, C, T)[None], wf > 0), i
+        torch.cuda.synchronize()
+    finally:
+        ctx.stream_close()
+        ctx.close()
