@@ -88,11 +88,11 @@ int64_t orc_draw(int method, int it, int64_t beam, int64_t line, int64_t index, 
 #define ORC_ATTEMPTS 32
 
 void orc_tdsc_row_u8(uint8_t* x, uint8_t* f, int64_t n, double k, int iters, int replace) {
-  orc_tdsc_row_u8x(x, f, n, k, iters, replace, 0, 0);
+  orc_tdsc_row_u8x(x, f, n, k, iters, replace, 0, 0, 0);
 }
 
 void orc_tdsc_row_u8x(uint8_t* x, uint8_t* f, int64_t n, double k, int iters, int replace, int64_t beam,
-                      int64_t line) {
+                      int64_t line, int it0) {
   const double k2 = k * k;
   uint8_t* fl = (uint8_t*)malloc((size_t)n);
   for (int it = 0; it < iters; it++) {
@@ -120,7 +120,7 @@ void orc_tdsc_row_u8x(uint8_t* x, uint8_t* f, int64_t n, double k, int iters, in
         continue;
       }
       for (int a = 0; a < ORC_ATTEMPTS; a++) {
-        const int64_t u = orc_draw(1, it, beam, line, t, a, n);
+        const int64_t u = orc_draw(1, it0 + it, beam, line, t, a, n);
         if (!fl[u]) { /* unflagged samples are not changed in this iteration */
           x[t] = x[u];
           break;
@@ -158,11 +158,11 @@ static int64_t fdsc_lcm(int64_t n, int64_t bin) {
 }
 
 void orc_fdsc_col_u8(uint8_t* x, uint8_t* f, int64_t n, double k, int iters, int replace, int64_t bin) {
-  orc_fdsc_col_u8x(x, f, n, k, iters, replace, bin, 0, 0);
+  orc_fdsc_col_u8x(x, f, n, k, iters, replace, bin, 0, 0, 0);
 }
 
 void orc_fdsc_col_u8x(uint8_t* x, uint8_t* f, int64_t n, double k, int iters, int replace, int64_t bin,
-                      int64_t beam, int64_t line) {
+                      int64_t beam, int64_t line, int it0) {
   const double k2 = k * k;
   const int64_t nb = (n + bin - 1) / bin;
   const int64_t L = fdsc_lcm(n, bin);
@@ -199,7 +199,7 @@ void orc_fdsc_col_u8x(uint8_t* x, uint8_t* f, int64_t n, double k, int iters, in
       }
       const int64_t G = ((g + 1) * bin < n ? bin : n - g * bin);
       for (int a = 0; a < ORC_ATTEMPTS; a++) {
-        const int64_t u = c0 + orc_draw(2, it, beam, line, c, a, G);
+        const int64_t u = c0 + orc_draw(2, it0 + it, beam, line, c, a, G);
         if (!fl[u]) {
           x[c] = x[u];
           break;
@@ -230,11 +230,11 @@ void orc_tdsc_row_f32(float* x, uint8_t* f, int64_t n, double k, int iters, int 
 }
 
 void orc_tdsc_row_f32m(float* x, uint8_t* f, double* margin, int64_t n, double k, int iters, int replace) {
-  orc_tdsc_row_f32x(x, f, margin, n, k, iters, replace, 0, 0);
+  orc_tdsc_row_f32x(x, f, margin, n, k, iters, replace, 0, 0, 0);
 }
 
 void orc_tdsc_row_f32x(float* x, uint8_t* f, double* margin, int64_t n, double k, int iters, int replace,
-                       int64_t beam, int64_t line) {
+                       int64_t beam, int64_t line, int it0) {
   uint8_t* fl = (uint8_t*)malloc((size_t)n);
   for (int it = 0; it < iters; it++) {
     double s = 0.0;
@@ -260,7 +260,7 @@ void orc_tdsc_row_f32x(float* x, uint8_t* f, double* margin, int64_t n, double k
         continue;
       }
       for (int a = 0; a < ORC_ATTEMPTS; a++) {
-        const int64_t u = orc_draw(1, it, beam, line, t, a, n);
+        const int64_t u = orc_draw(1, it0 + it, beam, line, t, a, n);
         if (!fl[u]) {
           x[t] = x[u];
           break;
@@ -277,11 +277,11 @@ void orc_fdsc_col_f32(float* x, uint8_t* f, int64_t n, double k, int iters, int 
 
 void orc_fdsc_col_f32m(float* x, uint8_t* f, double* margin, int64_t n, double k, int iters, int replace,
                        int64_t bin) {
-  orc_fdsc_col_f32x(x, f, margin, n, k, iters, replace, bin, 0, 0);
+  orc_fdsc_col_f32x(x, f, margin, n, k, iters, replace, bin, 0, 0, 0);
 }
 
 void orc_fdsc_col_f32x(float* x, uint8_t* f, double* margin, int64_t n, double k, int iters, int replace,
-                       int64_t bin, int64_t beam, int64_t line) {
+                       int64_t bin, int64_t beam, int64_t line, int it0) {
   const int64_t nb = (n + bin - 1) / bin;
   double* m = (double*)malloc((size_t)nb * sizeof(double));
   double* d = (double*)malloc((size_t)n * sizeof(double));
@@ -321,7 +321,7 @@ void orc_fdsc_col_f32x(float* x, uint8_t* f, double* margin, int64_t n, double k
       }
       const int64_t G = ((g + 1) * bin < n ? bin : n - g * bin);
       for (int a = 0; a < ORC_ATTEMPTS; a++) {
-        const int64_t u = c0 + orc_draw(2, it, beam, line, c, a, G);
+        const int64_t u = c0 + orc_draw(2, it0 + it, beam, line, c, a, G);
         if (!fl[u]) {
           x[c] = x[u];
           break;
@@ -372,8 +372,10 @@ static int64_t at(int64_t b, int64_t c, int64_t t, int64_t C, int64_t T, int lay
   return layout == ORC_LAYOUT_BCT ? (b * C + c) * T + t : (b * T + t) * C + c;
 }
 
-int orc_clean_u8(const uint8_t* in, uint8_t* out, uint8_t* flags, int64_t B, int64_t C, int64_t T,
-                 int layout, const orc_cut* tdsc, const orc_cut* fdsc) {
+/* it0: index of the cuts' first iteration, which keys the random draws (the
+ * interleaved order runs round r as single iterations with it0 = r) */
+static int clean_u8_from(const uint8_t* in, uint8_t* out, uint8_t* flags, int64_t B, int64_t C, int64_t T,
+                         int layout, const orc_cut* tdsc, const orc_cut* fdsc, int it0) {
   int rc = check_block(B, C, T, layout, tdsc, fdsc);
   if (rc) return rc;
   rc = range_u8(C, T, tdsc, fdsc);
@@ -390,7 +392,7 @@ int orc_clean_u8(const uint8_t* in, uint8_t* out, uint8_t* flags, int64_t B, int
           v[t] = out[at(b, c, t, C, T, layout)];
           fl[t] = 0;
         }
-        orc_tdsc_row_u8x(v, fl, T, tdsc->k, tdsc->iterations, tdsc->replace, b, c);
+        orc_tdsc_row_u8x(v, fl, T, tdsc->k, tdsc->iterations, tdsc->replace, b, c, it0);
         for (int64_t t = 0; t < T; t++) {
           out[at(b, c, t, C, T, layout)] = v[t];
           if (flags) flags[at(b, c, t, C, T, layout)] |= fl[t];
@@ -404,7 +406,7 @@ int orc_clean_u8(const uint8_t* in, uint8_t* out, uint8_t* flags, int64_t B, int
           v[c] = out[at(b, c, t, C, T, layout)];
           fl[c] = 0;
         }
-        orc_fdsc_col_u8x(v, fl, C, fdsc->k, fdsc->iterations, fdsc->replace, fdsc->bin, b, t);
+        orc_fdsc_col_u8x(v, fl, C, fdsc->k, fdsc->iterations, fdsc->replace, fdsc->bin, b, t, it0);
         for (int64_t c = 0; c < C; c++) {
           out[at(b, c, t, C, T, layout)] = v[c];
           if (flags) flags[at(b, c, t, C, T, layout)] |= fl[c];
@@ -416,13 +418,26 @@ int orc_clean_u8(const uint8_t* in, uint8_t* out, uint8_t* flags, int64_t B, int
   return ORC_OK;
 }
 
+int orc_clean_u8(const uint8_t* in, uint8_t* out, uint8_t* flags, int64_t B, int64_t C, int64_t T,
+                 int layout, const orc_cut* tdsc, const orc_cut* fdsc) {
+  return clean_u8_from(in, out, flags, B, C, T, layout, tdsc, fdsc, 0);
+}
+
+static int clean_f32_from(const float* in, float* out, uint8_t* flags, double* margin, int64_t B, int64_t C,
+                          int64_t T, int layout, const orc_cut* tdsc, const orc_cut* fdsc, int it0);
+
 int orc_clean_f32(const float* in, float* out, uint8_t* flags, int64_t B, int64_t C, int64_t T,
                   int layout, const orc_cut* tdsc, const orc_cut* fdsc) {
-  return orc_clean_f32m(in, out, flags, NULL, B, C, T, layout, tdsc, fdsc);
+  return clean_f32_from(in, out, flags, NULL, B, C, T, layout, tdsc, fdsc, 0);
 }
 
 int orc_clean_f32m(const float* in, float* out, uint8_t* flags, double* margin, int64_t B, int64_t C, int64_t T,
                    int layout, const orc_cut* tdsc, const orc_cut* fdsc) {
+  return clean_f32_from(in, out, flags, margin, B, C, T, layout, tdsc, fdsc, 0);
+}
+
+static int clean_f32_from(const float* in, float* out, uint8_t* flags, double* margin, int64_t B, int64_t C,
+                          int64_t T, int layout, const orc_cut* tdsc, const orc_cut* fdsc, int it0) {
   int rc = check_block(B, C, T, layout, tdsc, fdsc);
   if (rc) return rc;
   const int64_t N = B * C * T;
@@ -442,7 +457,7 @@ int orc_clean_f32m(const float* in, float* out, uint8_t* flags, double* margin, 
           fl[t] = 0;
           if (mg) mg[t] = INFINITY;
         }
-        orc_tdsc_row_f32x(v, fl, mg, T, tdsc->k, tdsc->iterations, tdsc->replace, b, c);
+        orc_tdsc_row_f32x(v, fl, mg, T, tdsc->k, tdsc->iterations, tdsc->replace, b, c, it0);
         for (int64_t t = 0; t < T; t++) {
           out[at(b, c, t, C, T, layout)] = v[t];
           if (flags) flags[at(b, c, t, C, T, layout)] |= fl[t];
@@ -458,7 +473,7 @@ int orc_clean_f32m(const float* in, float* out, uint8_t* flags, double* margin, 
           fl[c] = 0;
           if (mg) mg[c] = INFINITY;
         }
-        orc_fdsc_col_f32x(v, fl, mg, C, fdsc->k, fdsc->iterations, fdsc->replace, fdsc->bin, b, t);
+        orc_fdsc_col_f32x(v, fl, mg, C, fdsc->k, fdsc->iterations, fdsc->replace, fdsc->bin, b, t, it0);
         for (int64_t c = 0; c < C; c++) {
           out[at(b, c, t, C, T, layout)] = v[c];
           if (flags) flags[at(b, c, t, C, T, layout)] |= fl[c];
@@ -476,7 +491,9 @@ int orc_clean_f32m(const float* in, float* out, uint8_t* flags, double* margin, 
 /* ------------------------------------------------------------------ */
 /* Interleaved order: round i runs TDSC iteration i on every row, then  */
 /* FDSC iteration i on every column (each a single-iteration cut on the  */
-/* current values); flags are OR-ed over rounds.  With one iteration of  */
+/* current values, random draws keyed by iteration i); flags are OR-ed   */
+/* over rounds.  With unequal iteration counts the method with more     */
+/* iterations runs alone in the last rounds.  With one iteration of     */
 /* each method this is the blocked order.                                */
 /* ------------------------------------------------------------------ */
 static int clean_interleaved(const void* in, void* out, uint8_t* flags, int64_t B, int64_t C, int64_t T,
@@ -501,8 +518,9 @@ static int clean_interleaved(const void* in, void* out, uint8_t* flags, int64_t 
       f1 = *fdsc;
       f1.iterations = 1;
     }
-    rc = is_f32 ? orc_clean_f32((const float*)out, (float*)out, fr, B, C, T, layout, &t1, &f1)
-                : orc_clean_u8((const uint8_t*)out, (uint8_t*)out, fr, B, C, T, layout, &t1, &f1);
+    /* round r is iteration r of each method: its random draws are keyed by r */
+    rc = is_f32 ? clean_f32_from((const float*)out, (float*)out, fr, NULL, B, C, T, layout, &t1, &f1, r)
+                : clean_u8_from((const uint8_t*)out, (uint8_t*)out, fr, B, C, T, layout, &t1, &f1, r);
     if (flags)
       for (int64_t i = 0; i < N; i++) flags[i] |= fr[i];
   }

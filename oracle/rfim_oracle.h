@@ -88,19 +88,22 @@ void orc_fdsc_col_f32(float* x, uint8_t* f, int64_t n, double k, int iters, int 
  * FDSC (where the position is within the bin). */
 uint64_t orc_mix64(uint64_t z);
 int64_t orc_draw(int method, int it, int64_t beam, int64_t line, int64_t index, int attempt, int64_t n);
-/* the row/column cuts with the beam and line that key the random draws */
+/* the row/column cuts with the beam and line that key the random draws, and
+ * it0, the index of their first iteration (iteration i draws with it0 + i) */
 void orc_tdsc_row_u8x(uint8_t* x, uint8_t* f, int64_t n, double k, int iters, int replace, int64_t beam,
-                      int64_t line);
+                      int64_t line, int it0);
 void orc_fdsc_col_u8x(uint8_t* x, uint8_t* f, int64_t n, double k, int iters, int replace, int64_t bin,
-                      int64_t beam, int64_t line);
+                      int64_t beam, int64_t line, int it0);
 void orc_tdsc_row_f32x(float* x, uint8_t* f, double* margin, int64_t n, double k, int iters, int replace,
-                       int64_t beam, int64_t line);
+                       int64_t beam, int64_t line, int it0);
 void orc_fdsc_col_f32x(float* x, uint8_t* f, double* margin, int64_t n, double k, int iters, int replace,
-                       int64_t bin, int64_t beam, int64_t line);
+                       int64_t bin, int64_t beam, int64_t line, int it0);
 
 /* The combined cleaner in interleaved order: round i applies TDSC iteration i
  * to every row, then FDSC iteration i to every column (single-iteration cuts
- * on the current values), for max(iterations) rounds; flags OR over rounds. */
+ * on the current values, random draws keyed by iteration i), for
+ * max(iterations) rounds -- the method with more iterations runs alone in the
+ * last rounds; flags OR over rounds. */
 int orc_clean_u8_interleaved(const uint8_t* in, uint8_t* out, uint8_t* flags,
                              int64_t B, int64_t C, int64_t T, int layout,
                              const orc_cut* tdsc, const orc_cut* fdsc);

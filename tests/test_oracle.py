@@ -29,35 +29,81 @@ def _frac_k2(k):
     return Fraction(k) ** 2  # k is a binary double; its square is an exact rational
 
 
-def rational_tdsc(row, k, iterations, replace):
-    """TDSC on exact rationals: mu = mean, sigma^2 = population variance."""
-    x = [Fraction(int(v)) for v in row]
+M64 = (1 << 64) - 1
+
+
+def py_mix64(z):
+    """SplitMix64 output function (Steele, Lea, Flood 2014), restated from the
+    published definition: add the golden-ratio increment, then two
+    xor-shift-multiply rounds and a final xor-shift."""
+    z = (z + 0x9E3779B97F4A7C15) & M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M64
+    return z ^ (z >> 31)
+
+
+def py_draw(method, it, beam, line, index, attempt, n):
+    """Position in [0, n) of a random-replacement attempt (the library's
+    documented key: method 1 = TDSC, 2 = FDSC; it = the iteration)."""
+    h = py_mix64(py_mix64(py_mix64(py_mix64(beam) ^ line) ^ index) ^ (method << 8 | it << 16 | attempt << 24))
+    return ((h >> 32) * n) >> 32
+
+
+def _random_pick(x, hit, method, it, beam, line, index, lo, n):
+    """Value taken by flagged sample `index`: the first of 32 draws over
+    positions lo .. lo + n - 1 that lands on an unflagged sample (unflagged
+    values do not change within an iteration), else its own value."""
+    for a in range(32):
+        u = lo + py_draw(method, it, beam, line, index, a, n)
+        if not hit[u]:
+            return x[u]
+    return x[index]
+
+
+def _round_f32(q):
+    """(float) of the double nearest to the rational q: the float32 replacement
+    value is the float32 rounding of the double mean."""
+    return Fraction(float(np.float32(float(q))))
+
+
+def rational_tdsc(row, k, iterations, replace, beam=0, line=0, it0=0, f32=False):
+    """TDSC on exact rationals: mu = mean, sigma^2 = population variance.
+    Returns (values, flags, ties) where ties counts exact |x - mu| = k sigma
+    decisions (decided by rounding in a floating-point evaluation)."""
+    x = [Fraction(float(v)) if f32 else Fraction(int(v)) for v in row]
     n = len(x)
     flags = [0] * n
+    ties = 0
     k2 = _frac_k2(k)
-    for _ in range(iterations):
+    for i in range(iterations):
         mu = sum(x) / n
         var = sum((v - mu) ** 2 for v in x) / n
         if replace == "mean":
-            r = Fraction(math.floor(mu + Fraction(1, 2)))  # round half up
+            r = _round_f32(mu) if f32 else Fraction(math.floor(mu + Fraction(1, 2)))  # round half up
         else:
             r = sorted(x)[(n - 1) // 2]
         hit = [(v - mu) ** 2 > k2 * var for v in x]
-        for i, h in enumerate(hit):
+        ties += sum(1 for v in x if var > 0 and (v - mu) ** 2 == k2 * var)
+        new = list(x)
+        for t, h in enumerate(hit):
             if h:
-                x[i] = r
-                flags[i] = 1
-    return [int(v) for v in x], flags
+                new[t] = _random_pick(x, hit, 1, it0 + i, beam, line, t, 0, n) if replace == "random" else r
+                flags[t] = 1
+        x = new
+    vals = [float(v) for v in x] if f32 else [int(v) for v in x]
+    return vals, flags, ties
 
 
-def rational_fdsc(col, k, iterations, replace, bin):
-    """FDSC on exact rationals: bin means, corrected values d, mu', sigma'."""
-    x = [Fraction(int(v)) for v in col]
+def rational_fdsc(col, k, iterations, replace, bin, beam=0, line=0, it0=0, f32=False):
+    """FDSC on exact rationals: bin means, corrected values d, mu', sigma'.
+    Returns (values, flags, ties) as rational_tdsc."""
+    x = [Fraction(float(v)) if f32 else Fraction(int(v)) for v in col]
     n = len(x)
     flags = [0] * n
+    ties = 0
     k2 = _frac_k2(k)
     bins = [list(range(s, min(s + bin, n))) for s in range(0, n, bin)]
-    for _ in range(iterations):
+    for i in range(iterations):
         m = {}
         rep = {}
         for b in bins:
@@ -65,19 +111,68 @@ def rational_fdsc(col, k, iterations, replace, bin):
             for c in b:
                 m[c] = mb
             if replace == "mean":
-                rep[tuple(b)] = Fraction(math.floor(mb + Fraction(1, 2)))
+                rep[b[0]] = _round_f32(mb) if f32 else Fraction(math.floor(mb + Fraction(1, 2)))
             else:
-                rep[tuple(b)] = sorted(x[c] for c in b)[(len(b) - 1) // 2]
+                rep[b[0]] = sorted(x[c] for c in b)[(len(b) - 1) // 2]
         d = [x[c] - m[c] for c in range(n)]
         mu = sum(d) / n
         var = sum((v - mu) ** 2 for v in d) / n
         hit = [(d[c] - mu) ** 2 > k2 * var for c in range(n)]
+        ties += sum(1 for c in range(n) if var > 0 and (d[c] - mu) ** 2 == k2 * var)
+        new = list(x)
         for b in bins:
             for c in b:
                 if hit[c]:
-                    x[c] = rep[tuple(b)]
+                    if replace == "random":
+                        new[c] = _random_pick(x, hit, 2, it0 + i, beam, line, c, b[0], len(b))
+                    else:
+                        new[c] = rep[b[0]]
                     flags[c] = 1
-    return [int(v) for v in x], flags
+        x = new
+    vals = [float(v) for v in x] if f32 else [int(v) for v in x]
+    return vals, flags, ties
+
+
+def rational_clean(x, tdsc=None, fdsc=None, order="blocked"):
+    """A (B, C, T) block cleaned on exact rationals, per the order readings:
+    blocked = every TDSC iteration on each row, then every FDSC iteration on
+    each column; interleaved = round r runs TDSC iteration r on every row, then
+    FDSC iteration r on every column (random draws keyed by r), the method with
+    more iterations running alone in the last rounds.  Flags: bit 0 TDSC,
+    bit 1 FDSC.  Returns (out, flags, ties)."""
+    f32 = x.dtype == np.float32
+    out = x.astype(np.float64 if f32 else np.int64).copy()
+    flags = np.zeros(x.shape, np.uint8)
+    B, C, T = x.shape
+    it_t = tdsc["iterations"] if tdsc else 0
+    it_f = fdsc["iterations"] if fdsc else 0
+    if order == "blocked":
+        passes = [("t", 0, it_t)] if it_t else []
+        passes += [("f", 0, it_f)] if it_f else []
+    else:
+        passes = []
+        for r in range(max(it_t, it_f)):
+            if r < it_t:
+                passes.append(("t", r, 1))
+            if r < it_f:
+                passes.append(("f", r, 1))
+    ties = 0
+    for kind, it0, n_it in passes:
+        for b in range(B):
+            if kind == "t":
+                for c in range(C):
+                    v, f, tz = rational_tdsc(out[b, c], tdsc["k"], n_it, tdsc["replace"], b, c, it0, f32)
+                    out[b, c] = v
+                    flags[b, c] |= np.array(f, np.uint8)
+                    ties += tz
+            else:
+                for t in range(T):
+                    v, f, tz = rational_fdsc(out[b, :, t], fdsc["k"], n_it, fdsc["replace"], fdsc["bin"], b, t, it0,
+                                             f32)
+                    out[b, :, t] = v
+                    flags[b, :, t] |= np.array(f, np.uint8) << 1
+                    ties += tz
+    return out.astype(x.dtype), flags, ties
 
 
 # ---------------------------------------------------------------------------
@@ -131,7 +226,7 @@ def test_tdsc_u8_bruteforce_vs_rational(oracle):
         it = int(rng.integers(1, 4))
         rep = "mean" if trial % 3 else "median"
         out, fl = oracle.tdsc_row(row, k, it, rep)
-        r_out, r_fl = rational_tdsc(row, k, it, rep)
+        r_out, r_fl, _ = rational_tdsc(row, k, it, rep)
         assert out.tolist() == r_out, (row, k, it, rep)
         assert fl.tolist() == r_fl, (row, k, it, rep)
 
@@ -149,7 +244,7 @@ def test_fdsc_u8_bruteforce_vs_rational(oracle):
         it = int(rng.integers(1, 4))
         rep = "mean" if trial % 3 else "median"
         out, fl = oracle.fdsc_col(col, k, it, rep, bin)
-        r_out, r_fl = rational_fdsc(col, k, it, rep, bin)
+        r_out, r_fl, _ = rational_fdsc(col, k, it, rep, bin)
         assert out.tolist() == r_out, (col, k, it, rep, bin)
         assert (fl > 0).astype(int).tolist() == r_fl, (col, k, it, rep, bin)
 
@@ -162,7 +257,7 @@ def test_fdsc_u8_larger_columns_vs_rational(oracle):
         col[rng.integers(0, n, 3)] = 250
         for k in (2.0, 3.0):
             out, fl = oracle.fdsc_col(col, k, 2, "mean", bin)
-            r_out, r_fl = rational_fdsc(col, k, 2, "mean", bin)
+            r_out, r_fl, _ = rational_fdsc(col, k, 2, "mean", bin)
             assert out.tolist() == r_out
             assert (fl > 0).astype(int).tolist() == r_fl
 
@@ -572,3 +667,147 @@ def test_random_replacement_statistics_and_edge_cases(oracle):
     o32, f32 = oracle.clean(xf, "bct", tdsc=dict(k=3.0, iterations=2, replace="random"),
                             fdsc=dict(k=3.0, iterations=2, replace="random", bin=2))
     assert np.array_equal(f8, f32) and np.array_equal(o8.astype(np.float32), o32)
+
+
+# ---------------------------------------------------------------------------
+# float32 FDSC over several bins, random draws keyed by the iteration, and the
+# interleaved order, each against the exact-rational restatements above
+# ---------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("case", read_golden("fdsc_f32_handworked.txt"), ids=lambda c: str(c["params"]))
+def test_fdsc_f32_handworked(oracle, case):
+    p = case["params"]
+    col = np.array(case["in"], dtype=np.float32)
+    out, fl = oracle.fdsc_col(col, float(p["k"]), int(p["iterations"]), p["replace"], int(p["bin"]))
+    assert out.tolist() == [float(v) for v in case["out"]]
+    assert (fl > 0).astype(int).tolist() == [int(v) for v in case["flag"]]
+
+
+def test_py_draw_restates_splitmix64(oracle):
+    # the test's own SplitMix64 gives the published first outputs of seed 0,
+    # and the oracle's draws equal the test's draws
+    assert py_mix64(0) == 0xE220A8397B1DCDAF
+    assert py_mix64(0x9E3779B97F4A7C15) == 0x6E789E6AA1B965F4
+    rng = np.random.default_rng(5)
+    for _ in range(300):
+        m, it, b, line, idx, a = (int(rng.integers(1, 3)), int(rng.integers(0, 16)), int(rng.integers(0, 200)),
+                                  int(rng.integers(0, 30000)), int(rng.integers(0, 30000)), int(rng.integers(0, 32)))
+        n = int(rng.integers(1, 5000))
+        assert oracle.draw(m, it, b, line, idx, a, n) == py_draw(m, it, b, line, idx, a, n)
+
+
+def _dyadic_f32(rng, n):
+    # small integers over small powers of two: sums and means of up to 16
+    # values stay exact in double, so only exact ties are decided by rounding
+    return (rng.integers(0, 40, n) / rng.choice([1, 2, 4, 8], n)).astype(np.float32)
+
+
+@pytest.mark.parametrize("replace", ["mean", "median", "random"])
+def test_fdsc_f32_bruteforce_vs_rational(oracle, replace):
+    # several bins, a partial last bin, 1-3 iterations (Sec. IV FDSC, Fig. 3)
+    rng = np.random.default_rng(61)
+    run = 0
+    for trial in range(400):
+        n = int(rng.integers(2, 17))
+        bin = int(rng.integers(1, n + 1))
+        col = _dyadic_f32(rng, n)
+        col[rng.integers(0, n)] = float(rng.choice([60.0, 100.5, 0.0]))
+        k = float(rng.choice([0.75, 1.0, 1.5, 2.0, 2.5]))
+        it = int(rng.integers(1, 4))
+        r_out, r_fl, ties = rational_fdsc(col, k, it, replace, bin, f32=True)
+        if ties:
+            continue  # an exact tie: the double evaluation may go either way
+        run += 1
+        x = col[None, :, None]
+        out, fl = oracle.clean(x, "bct", fdsc=dict(k=k, iterations=it, replace=replace, bin=bin))
+        assert out[0, :, 0].tolist() == r_out, (col, k, it, bin)
+        assert (fl[0, :, 0] > 0).astype(int).tolist() == r_fl, (col, k, it, bin)
+    assert run > 300
+
+
+@pytest.mark.parametrize("replace", ["mean", "median", "random"])
+def test_tdsc_f32_bruteforce_vs_rational(oracle, replace):
+    rng = np.random.default_rng(62)
+    run = 0
+    for trial in range(400):
+        n = int(rng.integers(2, 17))
+        row = _dyadic_f32(rng, n)
+        row[rng.integers(0, n)] = float(rng.choice([60.0, 100.5, 0.0]))
+        k = float(rng.choice([0.75, 1.0, 1.5, 2.0, 2.5]))
+        it = int(rng.integers(1, 4))
+        r_out, r_fl, ties = rational_tdsc(row, k, it, replace, f32=True)
+        if ties:
+            continue
+        run += 1
+        out, fl = oracle.clean(row[None, None, :], "bct", tdsc=dict(k=k, iterations=it, replace=replace))
+        assert out[0, 0].tolist() == r_out, (row, k, it)
+        assert fl[0, 0].astype(int).tolist() == r_fl, (row, k, it)
+    assert run > 300
+
+
+def test_random_u8_bruteforce_vs_rational(oracle):
+    # random replacement over several iterations: iteration i draws with it = i
+    rng = np.random.default_rng(63)
+    for trial in range(300):
+        B, C, T = 2, int(rng.integers(2, 9)), int(rng.integers(2, 13))
+        x = rng.integers(0, 256, (B, C, T)).astype(np.uint8)
+        x[rng.random(x.shape) < 0.1] = 250
+        k = float(rng.choice([0.75, 1.0, 1.5, 2.0]))
+        td = dict(k=k, iterations=int(rng.integers(1, 4)), replace="random")
+        fd = dict(k=k, iterations=int(rng.integers(1, 4)), replace="random", bin=int(rng.integers(1, C + 1)))
+        want, wf, _ = rational_clean(x, td, fd)
+        got, gf = oracle.clean(x, "bct", tdsc=td, fdsc=fd)
+        assert np.array_equal(got, want) and np.array_equal(gf, wf), (x, td, fd)
+
+
+@pytest.mark.parametrize("replace", ["mean", "median", "random"])
+def test_interleaved_vs_rational(oracle, replace):
+    # Interleaved order with equal and unequal iteration counts: round r is
+    # iteration r of each method (random draws keyed by r); the method with
+    # more iterations runs alone in the last rounds.
+    rng = np.random.default_rng(64)
+    for trial in range(150):
+        B, C, T = int(rng.integers(1, 3)), int(rng.integers(2, 7)), int(rng.integers(2, 9))
+        x = rng.integers(0, 256, (B, C, T)).astype(np.uint8)
+        x[rng.random(x.shape) < 0.1] = 250
+        k = float(rng.choice([0.75, 1.0, 1.5, 2.0]))
+        td = dict(k=k, iterations=int(rng.integers(1, 4)), replace=replace)
+        fd = dict(k=k, iterations=int(rng.integers(1, 4)), replace=replace, bin=int(rng.integers(1, C + 1)))
+        want, wf, _ = rational_clean(x, td, fd, order="interleaved")
+        got, gf = oracle.clean(x, "bct", tdsc=td, fdsc=fd, order="interleaved")
+        assert np.array_equal(got, want) and np.array_equal(gf, wf), (x, td, fd)
+
+
+def test_interleaved_f32_vs_rational(oracle):
+    rng = np.random.default_rng(65)
+    run = 0
+    for trial in range(120):
+        C, T = int(rng.integers(2, 6)), int(rng.integers(2, 8))
+        x = _dyadic_f32(rng, C * T).reshape(1, C, T)
+        k = float(rng.choice([0.75, 1.0, 1.5]))
+        rep = ["mean", "median", "random"][trial % 3]
+        td = dict(k=k, iterations=int(rng.integers(1, 4)), replace=rep)
+        fd = dict(k=k, iterations=int(rng.integers(1, 4)), replace=rep, bin=int(rng.integers(1, C + 1)))
+        want, wf, ties = rational_clean(x, td, fd, order="interleaved")
+        if ties:
+            continue
+        run += 1
+        got, gf = oracle.clean(x, "bct", tdsc=td, fdsc=fd, order="interleaved")
+        assert np.array_equal(got, want) and np.array_equal(gf, wf), (x, td, fd)
+    assert run > 60
+
+
+@pytest.mark.parametrize("case", read_golden("interleaved_u8_handworked.txt"), ids=lambda c: str(c["params"]))
+def test_interleaved_handworked(oracle, case):
+    p = case["params"]
+    C, T = int(p["C"]), int(p["T"])
+    x = np.array(case["in"], dtype=np.uint8).reshape(1, C, T)
+    td = dict(k=float(p["tdsc_k"]), iterations=int(p["tdsc_it"]), replace="mean")
+    fd = dict(k=float(p["fdsc_k"]), iterations=int(p["fdsc_it"]), replace="mean", bin=int(p["bin"]))
+    out, fl = oracle.clean(x, "bct", tdsc=td, fdsc=fd, order="interleaved")
+    assert out.reshape(-1).tolist() == [int(v) for v in case["out"]]
+    assert fl.reshape(-1).tolist() == [int(v) for v in case["flag"]]
+    # the blocked order differs on this block (TDSC's second iteration runs before FDSC)
+    _, fb = oracle.clean(x, "bct", tdsc=td, fdsc=fd)
+    assert fb.reshape(-1).tolist() != [int(v) for v in case["flag"]]
