@@ -111,8 +111,9 @@ typedef enum { RFIM_LAYOUT_BCT = 0, RFIM_LAYOUT_BTC = 1 } rfim_layout;
  * channel, index = time sample), 2 = FDSC (line = time sample, index =
  * channel), beam = the beam's index within its block, it = the iteration; the
  * first draw that hits an unflagged sample wins, and after 32 misses the
- * sample keeps its value.  TDSC rows with RANDOM hold at most 78,609 samples
- * (uint8) or 52,000 (float32).
+ * sample keeps its value.  In the interleaved order ("order" option) round r
+ * is iteration r of each method and draws with it = r.  TDSC rows with RANDOM
+ * hold at most 78,609 samples (uint8) or 52,000 (float32).
  */
 typedef enum { RFIM_REPLACE_MEAN = 0, RFIM_REPLACE_MEDIAN = 1, RFIM_REPLACE_RANDOM = 2 } rfim_replace;
 
@@ -128,7 +129,7 @@ typedef enum { RFIM_REPLACE_MEAN = 0, RFIM_REPLACE_MEDIAN = 1, RFIM_REPLACE_RAND
  */
 typedef enum { RFIM_MASK_NONE = 0, RFIM_MASK_BITS = 1, RFIM_MASK_BYTES = 2 } rfim_mask_fmt;
 
-/* One sigma cut.  k > 0 (accepted range [1e-3, 1e6]), iterations 1..16,
+/* One sigma cut.  k: any finite k > 0, iterations 1..16,
  * fdsc_bin: FDSC channels per bin, 1..channels (0 means 32, capped at channels);
  * ignored by TDSC. */
 typedef struct {
@@ -254,17 +255,31 @@ rfim_status rfim_clean_host(rfim_ctx* ctx, const rfim_block* host_blk, const rfi
  *   - Every call on a device shares the array and clears it on its stream
  *     first.  Calls whose work overlaps on the GPU (different streams without
  *     ordering) race on it and must not be issued; order them on one stream.
- *   - Device-side wait timeouts are not reported (there is no context to read
- *     them through); the fused schedule cannot wait forever in normal use.
+ *   - A device-side wait that gives up (after 2 s) leaves its output
+ *     incomplete and sets a status word in the same array; the call itself
+ *     has already returned, so read the word with rfim_noalloc_status.
  *   - Calls no cudaMalloc, cudaFree or other allocating routine.
  */
 #define RFIM_NOALLOC_MAX_BEAMS 160
 rfim_status rfim_clean_noalloc(const rfim_block* blk, const rfim_cut* tdsc, const rfim_cut* fdsc, void* stream);
 
 /*
+ * Status of the latest rfim_clean_noalloc call on the CURRENT device (each
+ * call clears the word on its stream first): synchronises `stream` (the one
+ * that call used), reads the shared array's status word and clears it.
+ * RFIM_OK, or RFIM_ERR_TIMEOUT if a device-side wait of that call gave up.
+ * Allocates nothing either (the word is copied to a host variable); like the
+ * calls it reports on, it must not overlap other rfim_clean_noalloc work on
+ * the device.
+ */
+rfim_status rfim_noalloc_status(void* stream);
+
+/*
  * Synchronise `stream` and return the device status word of the context's
  * kernels since the last check: RFIM_OK, or RFIM_ERR_TIMEOUT if a device-side
  * wait gave up (the affected output is then incomplete).  Clears the word.
+ * Batches of the streaming service that timed out since the last check (their
+ * chunks complete with RFIM_ERR_TIMEOUT) are reported here too, and cleared.
  */
 rfim_status rfim_device_status(rfim_ctx* ctx, void* stream);
 
@@ -286,8 +301,13 @@ rfim_status rfim_device_status(rfim_ctx* ctx, void* stream);
  *     one micro-batch (TDSC and FDSC as two launches for short chunks) on
  *     whichever of four CUDA streams is idle, so batches
  *     overlap on the device; completion is signalled from the stream.
- *   - Per beam the service keeps the count of chunks and the latency of the
- *     last one.  Statistics of earlier chunks never enter a decision.
+ *   - Per-beam state on the device: each beam keeps the slot of its latest
+ *     completed chunk (cleaned data, mask and the per-channel statistics of
+ *     its input, see rfim_stream_beam_state) until a newer chunk of the beam
+ *     completes; at most half of the slots are held this way.  Statistics of
+ *     earlier chunks never enter a decision (each chunk is its own batch).
+ *   - The options "spin_limit_us" and "withhold_tdsc_done" in force at open
+ *     apply to the service's launches.
  * Returns RFIM_ERR_STATE if the service is already open, RFIM_ERR_OOM if not
  * even one slot fits.
  */
@@ -313,13 +333,35 @@ rfim_status rfim_stream_push(rfim_ctx* ctx, int beam, const void* chunk, double 
  * ceil(chunk_samples / 32) words per channel) point to context-owned device
  * memory valid until rfim_stream_release.  wait_us: how long to wait for
  * completion (0 = do not wait).  Returns RFIM_ERR_BUSY if not done in time,
- * RFIM_ERR_ARG for an unknown ticket.
+ * RFIM_ERR_ARG for an unknown ticket, and for a chunk whose batch failed the
+ * reason (RFIM_ERR_TIMEOUT: a device-side wait of its launch gave up, so its
+ * output is incomplete; the ticket must still be released).
  */
 rfim_status rfim_stream_poll(rfim_ctx* ctx, unsigned long long ticket, void** out_dev, void** mask_dev,
                              int wait_us);
 
 /* Return a completed ticket's slot to the pool (RFIM_ERR_BUSY while it is in flight). */
 rfim_status rfim_stream_release(rfim_ctx* ctx, unsigned long long ticket);
+
+/*
+ * The per-beam state the service keeps on the device: beam `beam`'s latest
+ * completed chunk (the newest by push order among those cleaned so far).
+ *   chunk_index (nullable): that chunk's index among the beam's pushes (0, 1, ...).
+ *   stats (nullable, host memory of 2 * channels doubles): for each channel c,
+ *     stats[2c] = sum over the chunk's samples of the INPUT value and
+ *     stats[2c + 1] = the sum of their squares, as the first TDSC iteration
+ *     found them (exact for uint8; float-float sums rounded to double for
+ *     float32); zeros when the service runs no TDSC.  Copied synchronously.
+ *   out_dev / mask_dev (nullable): that chunk's cleaned data and bit mask in
+ *     device memory, valid until the beam's next chunk completes.
+ * The statistics are records for the caller (mean S/T, variance Q/T - mean^2
+ * of each channel in the previous chunk); the cleaning never reads them.
+ * Returns RFIM_ERR_BUSY while the beam has no completed chunk (or no state
+ * slot was free for it), RFIM_ERR_ARG for a bad beam, RFIM_ERR_STATE if the
+ * service is not open.
+ */
+rfim_status rfim_stream_beam_state(rfim_ctx* ctx, int beam, unsigned long long* chunk_index, double* stats,
+                                   const void** out_dev, const void** mask_dev);
 
 /*
  * Replay an arrival schedule through the open service: chunk i (of beam

@@ -134,8 +134,7 @@ struct CutNorm {
 rfim_status check_cut(rfim_ctx* ctx, const rfim_cut* c, int C, bool fdsc, CutNorm& out) {
   out = CutNorm();
   if (!c) return RFIM_OK;
-  if (!std::isfinite(c->k) || !(c->k >= 1e-3) || !(c->k <= 1e6))
-    return fail(ctx, RFIM_ERR_ARG, "k must be finite and in [1e-3, 1e6], got %g", c->k);
+  if (!std::isfinite(c->k) || !(c->k > 0.0)) return fail(ctx, RFIM_ERR_ARG, "k must be finite and > 0, got %g", c->k);
   if (c->iterations < 1 || c->iterations > 16)
     return fail(ctx, RFIM_ERR_ARG, "iterations must be in 1..16, got %d", c->iterations);
   if (c->replace != RFIM_REPLACE_MEAN && c->replace != RFIM_REPLACE_MEDIAN && c->replace != RFIM_REPLACE_RANDOM)
@@ -313,14 +312,28 @@ void add_block_jobs(rfim_ctx* ctx, Plan& pl, const rfim_block* b) {
   }
 }
 
-CutDev cut_dev(const CutNorm& c) {
+// The k the kernels use: clamped to [K_MIN_U8 (uint8 only), K_MAX], which
+// changes no decision.
+//  - Above: |x - mu| <= sigma sqrt(n - 1) for every sample of n values, so no
+//    cut with k > sqrt(n - 1) flags anything; n < 2^31 gives sqrt(n) < 46341,
+//    and k = 1e6 flags nothing too.  (The clamp keeps k^2 and the float-float
+//    split of k finite.)
+//  - Below, uint8: the threshold fl(k2 R) has R < 2^53 (validated), so for
+//    k <= 1e-9 it is below 1 and, the left side being an integer, every such
+//    k flags exactly the samples with a nonzero left side.
+// float32 takes k unclamped below: there the threshold is k sigma itself.
+constexpr double K_MAX = 1e6, K_MIN_U8 = 1e-9;
+
+CutDev cut_dev(const CutNorm& c, rfim_dtype dt) {
   CutDev d;
   memset(&d, 0, sizeof d);
   if (c.on) {
-    d.k2 = make_k2(c.k);
-    d.k = c.k;
-    d.k_hi = (float)c.k;
-    d.k_lo = (float)(c.k - (double)d.k_hi);
+    double k = std::min(c.k, K_MAX);
+    if (dt == RFIM_U8) k = std::max(k, K_MIN_U8);
+    d.k2 = make_k2(k);
+    d.k = k;
+    d.k_hi = (float)k;
+    d.k_lo = (float)(k - (double)d.k_hi);
     d.iterations = c.it;
     d.replace = c.rep;
     d.bin = c.bin;
@@ -396,8 +409,8 @@ void fill_params(rfim_ctx* ctx, const Plan& pl, int j0, int j1, int mode, Params
   memset(&p, 0, sizeof p);
   p.n_jobs = j1 - j0;
   for (int j = j0; j < j1; j++) p.jobs[j - j0] = pl.jobs[j];
-  p.td = cut_dev(pl.td);
-  p.fd = cut_dev(pl.fd);
+  p.td = cut_dev(pl.td, pl.dtype);
+  p.fd = cut_dev(pl.fd, pl.dtype);
   if (mode == 1 || mode == 3) p.td.iterations = 0;
   if (mode == 0 || mode == 5) p.fd.iterations = 0;
   if (mode == 5) {
@@ -473,11 +486,13 @@ rfim_status run_plan(rfim_ctx* ctx, const Plan& pl, cudaStream_t st) {
         if (r < pl.td.it) {
           fill_params(ctx, pl, j0, j1, r == 0 ? 0 : 5, p, next_counters(ctx));
           p.td.iterations = 1;
+          p.td.it0 = r;  // round r is iteration r: its random draws are keyed by r
           if ((s = launch_one(ctx, p, pl.max_T, st)) != RFIM_OK) return s;
         }
         if (r < pl.fd.it) {
           fill_params(ctx, pl, j0, j1, 3, p, next_counters(ctx));
           p.fd.iterations = 1;
+          p.fd.it0 = r;
           if ((s = launch_one(ctx, p, pl.max_T, st)) != RFIM_OK) return s;
         }
       }
@@ -819,6 +834,11 @@ rfim_status rfim_device_status(rfim_ctx* ctx, void* stream) {
     // counters of a launch that timed out are left mid-way; the ring resets them per launch
     return fail(ctx, RFIM_ERR_TIMEOUT, "a device-side wait gave up (status %u)", st);
   }
+  // the streaming service's batches report through their own status words
+  if (ctx->stream) {
+    const unsigned long long n = stream_service_take_timeouts(ctx->stream);
+    if (n) return fail(ctx, RFIM_ERR_TIMEOUT, "%llu streaming batch(es) had a device-side wait give up", n);
+  }
   return RFIM_OK;
 }
 
@@ -893,8 +913,14 @@ rfim_status ctx_validate(rfim_ctx* ctx, const rfim_block* b, const rfim_cut* tds
   return check_impl(ctx, b, td, fd);
 }
 
+void ctx_wait_options(rfim_ctx* ctx, unsigned long long& spin_limit_ns, int& withhold_job) {
+  spin_limit_ns = (unsigned long long)ctx->spin_limit_us * 1000ull;
+  withhold_job = ctx->withhold ? 0 : -1;
+}
+
 rfim_status launch_blocks_fixed(const rfim_block* blocks, int n, const rfim_cut* tdsc, const rfim_cut* fdsc,
-                                unsigned* counters, unsigned* status, cudaStream_t st) {
+                                unsigned* counters, unsigned* status, cudaStream_t st, double* const* stats,
+                                unsigned long long spin_limit_ns, int withhold_job) {
   if (!tdsc && !fdsc) return RFIM_ERR_ARG;
   if (!blocks || n < 1) return RFIM_ERR_ARG;
   CutNorm td, fd;
@@ -919,6 +945,7 @@ rfim_status launch_blocks_fixed(const rfim_block* blocks, int n, const rfim_cut*
     for (int j = 0; j < blocks[i].beams; j++) {
       p.jobs[j0 + j] = make_job(&blocks[i], j, fd, 0, 113 * 1024);
       random_row_mode(p.jobs[j0 + j], &blocks[i], td);
+      if (stats && stats[i]) p.jobs[j0 + j].stats = stats[i] + 2 * (size_t)j * blocks[i].channels;
     }
   const rfim_block* b = &blocks[0];
   const bool both = td.on && fd.on;
@@ -929,16 +956,16 @@ rfim_status launch_blocks_fixed(const rfim_block* blocks, int n, const rfim_cut*
   const int modes[2] = {separate ? 0 : (both ? 2 : (td.on ? 0 : 1)), separate ? 3 : -1};
   for (const int mode : modes) {
     if (mode < 0) break;
-    p.td = cut_dev(td);
-    p.fd = cut_dev(fd);
+    p.td = cut_dev(td, b->dtype);
+    p.fd = cut_dev(fd, b->dtype);
     if (mode == 1 || mode == 3) p.td.iterations = 0;
     if (mode == 0) p.fd.iterations = 0;
     p.mask_kind = (int)b->mask_fmt;
     p.fd_reads_out = (mode == 2 || mode == 3) ? 1 : 0;
     p.wait_tdsc = mode == 2 ? 1 : 0;
     p.mask_or = (mode == 2 || mode == 3) ? 1 : 0;
-    p.withhold_job = -1;
-    p.spin_limit_ns = 2000000000ull;
+    p.withhold_job = mode == 2 ? withhold_job : -1;
+    p.spin_limit_ns = spin_limit_ns;
     p.counters = counters;
     p.status = status;
     p.dtype = b->dtype == RFIM_F32 ? 1 : 0;

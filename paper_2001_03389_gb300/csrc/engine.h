@@ -23,6 +23,7 @@ struct CutDev {
   int iterations;  // 0 = method disabled
   int replace;     // ReplaceKind
   int bin;         // FDSC channels per bin
+  int it0;         // index of the first iteration (keys the random draws; round r of the interleaved order)
 };
 
 // One beam: C x T samples, BCT (time fastest) or BTC (channel fastest).
@@ -48,6 +49,8 @@ struct Job {
                     //          2 = one row per item, read from global memory in every pass (no stage)
   int td_items;     // number of TDSC work items
   int beam;         // index of the beam within its block (keys the random-replacement draws)
+  double* stats;    // or null: per row, the sum and the sum of squares of the input row ([2 * row], [2 * row + 1]),
+                    // written by the first TDSC iteration (the streaming service's per-beam state)
 };
 
 // A run of consecutive queue items: `count` items of one kind for one job.

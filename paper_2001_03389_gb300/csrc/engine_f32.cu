@@ -371,6 +371,10 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
   grp_ff2<GN>(S, Q, red, t, h);
   // S, Q: running sums of the current values, the same in every thread of the
   // group (the merges above add in the same order everywhere)
+  if (J.stats && t == 0) {  // statistics of the input row, for the caller's records
+    J.stats[2 * (size_t)row] = (double)S.hi + (double)S.lo;
+    J.stats[2 * (size_t)row + 1] = (double)Q.hi + (double)Q.lo;
+  }
   const double rT = 1.0 / (double)T;
   const FF kff{cut.k_hi, cut.k_lo};
   const int I = cut.iterations;
@@ -437,7 +441,7 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
           if (!((nib >> i) & 1u)) continue;
           const int tt = 4 * k + i - head;
           for (int a = 0; a < DRAW_ATTEMPTS; a++) {
-            const unsigned u = draw_pos(key, tt, 1, it, a, (unsigned)T);
+            const unsigned u = draw_pos(key, tt, 1, cut.it0 + it, a, (unsigned)T);
             const unsigned pu = (unsigned)head + u;
             if (!((fl4[pu >> 2] >> (4 + (pu & 3))) & 1u)) {
               f4_set(v, i, sf[u]);
@@ -582,6 +586,10 @@ __device__ __noinline__ void tdsc_row_f32_long(const Params& P, const Job& J, in
       ff_acc_sq(Q, y);
     }
     grp_ff2<NT>(S, Q, red, t, 0);  // (the same in every thread)
+    if (it == 0 && J.stats && t == 0) {  // statistics of the input row, for the caller's records
+      J.stats[2 * (size_t)row] = (double)S.hi + (double)S.lo;
+      J.stats[2 * (size_t)row + 1] = (double)Q.hi + (double)Q.lo;
+    }
     FF mu = ff_div_int(S, T);
     const FF mq = ff_div_int(Q, T);
     FF var = ff_add(mq, ff_neg(ff_mul(mu, mu)));
@@ -905,7 +913,7 @@ __device__ void fdsc_item_f32(const Params& P, const Job& J, int item, unsigned 
           for (int j = 0; j < n; j++) {
             if (!(L.fcur[c0 + j] & tb)) continue;
             for (int a = 0; a < DRAW_ATTEMPTS; a++) {
-              const int uu = (int)draw_pos(key, c0 + j, 2, it, a, (unsigned)n);
+              const int uu = (int)draw_pos(key, c0 + j, 2, cut.it0 + it, a, (unsigned)n);
               if (!(L.fcur[c0 + uu] & tb)) {
                 L.tile[(c0 + j) * Ws + t] = L.tile[(c0 + uu) * Ws + t];
                 break;

@@ -478,6 +478,10 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
   if (LANES <= 32) __syncwarp(grp_mask<LANES>());
   grp_sum_row<LANES, 2>(sq, scr);  // (the CTA variant's barriers also publish the staged row)
   unsigned long long S = sq[0], Q = sq[1];
+  if (J.stats && gl == 0) {  // statistics of the input row, for the caller's records (exact in double)
+    J.stats[2 * (size_t)row] = (double)S;
+    J.stats[2 * (size_t)row + 1] = (double)Q;
+  }
 
   // single: every flagged sample ends at one value (the median, or the mean of a
   // one-iteration cut), so one keep interval (the intersection) decides everything
@@ -579,7 +583,7 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
           const uint32_t old = (word_of(w, b >> 2) >> (8 * (b & 3))) & 0xFFu;
           uint32_t nv = old;
           for (int a = 0; a < DRAW_ATTEMPTS; a++) {
-            const unsigned u = draw_pos(key, t, 1, it, a, (unsigned)T);
+            const unsigned u = draw_pos(key, t, 1, cut.it0 + it, a, (unsigned)T);
             const unsigned pu = (unsigned)g.head + u;
             if (!((fcur[pu >> 4] >> (pu & 15)) & 1u)) {
               nv = sb[u];
@@ -1248,7 +1252,7 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
             const unsigned x = bv.byte(i);
             unsigned y = x;
             for (int a = 0; a < DRAW_ATTEMPTS; a++) {
-              const unsigned u = draw_pos(key, c0 + (int)i, 2, it, a, gsz);
+              const unsigned u = draw_pos(key, c0 + (int)i, 2, cut.it0 + it, a, gsz);
               if (!(L.fcur[c0 + u] & tb)) {
                 y = bv.byte(u);
                 break;

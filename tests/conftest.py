@@ -13,6 +13,18 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "slow: longer CPU test")
 
 
+# float32 parity: decisions checked and mask disagreements (each within 1e-9
+# relative of its threshold, or the test fails), summed over the session
+F32_TALLY = {"checks": 0, "decisions": 0, "disagreements": 0}
+
+
+def pytest_terminal_summary(terminalreporter):
+    if F32_TALLY["checks"]:
+        terminalreporter.write_line(
+            f"float32 parity: {F32_TALLY['disagreements']} mask disagreements (all within 1e-9 relative of the "
+            f"threshold) in {F32_TALLY['decisions']} samples over {F32_TALLY['checks']} checks")
+
+
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 

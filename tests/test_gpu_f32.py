@@ -3,14 +3,21 @@
 Tolerance (float32): a mask disagreement is allowed only where the oracle's
 decision lies within 1e-9 relative of its threshold, |(|x - mu| - k sigma)| <=
 1e-9 k sigma (the oracle reports that distance per sample); such
-disagreements are counted.  Samples neither side flags must be bit-identical
-to the input; samples both sides replace must agree within 1e-6 relative.
-Samples in a row or column after a counted disagreement are not compared
-value by value (the replacement changes later statistics of that row or column).
+disagreements are counted (tests/conftest.py prints the tally).  Samples
+neither side flags must be bit-identical to the input; samples both sides
+replace must agree within 1e-6 relative.
+
+A disagreement changes the later statistics of its own row (TDSC) or column
+(FDSC) only, so the value checks leave out just that row or column.  A fused
+clean (TDSC then FDSC) is checked method by method: the library's TDSC output
+against the oracle's TDSC on the input (rows), the library's FDSC of that
+output against the oracle's FDSC of the same output (columns), and the fused
+launch against the two separate launches, bit for bit.
 """
 import numpy as np
 import pytest
 
+from conftest import F32_TALLY
 from gpu_util import run_gpu
 
 pytestmark = pytest.mark.gpu
@@ -33,30 +40,34 @@ def ctx():
     c.close()
 
 
-def check_f32(oracle, ctx, x, td=None, fd=None, mask_fmt="bits", **kw):
-    """Returns the number of (allowed) mask disagreements."""
-    want, wf, margin = oracle.clean_f32_margin(x, "bct", tdsc=td, fdsc=fd)
-    got, gf = run_gpu(ctx, x, tdsc=td, fdsc=fd, mask_fmt=mask_fmt, **kw)
-    wflag = wf > 0
+def _gpu_flags(got, gf, x, mask_fmt):
     if mask_fmt == "bits":
-        gflag = gf
-        dis = gflag != wflag
-    elif mask_fmt == "bytes":
-        gflag = gf > 0
-        dis = gf != wf
-    else:
-        gflag = got != x  # no mask: changed samples (a replaced value can equal the original)
+        return gf
+    if mask_fmt == "bytes":
+        return gf > 0
+    return got != x  # no mask: changed samples (a replaced value can equal the original)
+
+
+def compare_f32(x, want, wf, margin, got, gflag, line_axes, mask_fmt="bits", byte_flags=None):
+    """One method's output against the oracle's on the same input.  line_axes:
+    the axes that index a line of that method (a disagreement excludes its
+    line from the value checks).  Returns the number of mask disagreements."""
+    wflag = wf > 0
+    if mask_fmt is None:
         dis = np.zeros_like(wflag)
+    elif byte_flags is not None:
+        dis = byte_flags != wf
+    else:
+        dis = gflag != wflag
     nd = int(dis.sum())
+    ok = np.ones_like(wflag)
     if nd:
         bad = dis & ~(margin <= MARGIN)
         assert not bad.any(), (f"{int(bad.sum())} mask disagreements farther than {MARGIN} from the threshold, "
                                f"first at {np.argwhere(bad)[:3].tolist()}, margins {margin[bad][:3]}")
-    # rows and columns touched by a disagreement are excluded from the value checks
-    ok = np.ones_like(wflag)
-    for b, c, t in np.argwhere(dis):
-        ok[b, c, :] = False
-        ok[b, :, t] = False
+        for idx in np.argwhere(dis):
+            sel = tuple(int(idx[a]) if a in line_axes else slice(None) for a in range(3))
+            ok[sel] = False
     keep = ok & ~wflag & ~gflag if mask_fmt is not None else ok & ~wflag
     assert np.array_equal(got[keep].view(np.uint32), x[keep].view(np.uint32)), "unflagged samples changed"
     both = ok & wflag & (gflag if mask_fmt is not None else True)
@@ -64,7 +75,38 @@ def check_f32(oracle, ctx, x, td=None, fd=None, mask_fmt="bits", **kw):
         err = np.abs(got[both].astype(np.float64) - want[both].astype(np.float64))
         tol = REL * np.maximum(np.abs(want[both].astype(np.float64)), 1e-30)
         assert np.all(err <= tol), f"replaced values differ: max rel {np.max(err / tol) * REL:.3g}"
+    F32_TALLY["checks"] += 1
+    F32_TALLY["decisions"] += int(x.size)
+    F32_TALLY["disagreements"] += nd
     return nd
+
+
+def check_f32(oracle, ctx, x, td=None, fd=None, mask_fmt="bits", layout="bct", **kw):
+    """Clean x on the GPU with the given cuts and check it against the oracle.
+    Returns the number of (allowed) mask disagreements."""
+    rows = (0, 1) if layout == "bct" else (0, 2)  # (beam, channel) indexes a TDSC row
+    cols = (0, 2) if layout == "bct" else (0, 1)  # (beam, time) indexes an FDSC column
+    api = kw.pop("api", "clean" if td and fd else ("tdsc" if td else "fdsc"))
+    if td and fd and api == "clean":
+        # the two methods one at a time, each on its own input
+        got_t, bt = run_gpu(ctx, x, layout=layout, tdsc=td, mask_fmt="bytes", api="tdsc")
+        want_t, wft, mt = oracle.clean_f32_margin(x, layout, tdsc=td)
+        nd = compare_f32(x, want_t, wft, mt, got_t, bt > 0, rows, "bytes", byte_flags=bt)
+        got_f, bf = run_gpu(ctx, got_t, layout=layout, fdsc=fd, mask_fmt="bytes", api="fdsc")
+        want_f, wff, mf = oracle.clean_f32_margin(got_t, layout, fdsc=fd)
+        nd += compare_f32(got_t, want_f, wff, mf, got_f, bf > 0, cols, "bytes", byte_flags=bf)
+        # the fused launch equals the two launches
+        got, gf = run_gpu(ctx, x, layout=layout, tdsc=td, fdsc=fd, mask_fmt=mask_fmt, **kw)
+        assert np.array_equal(got.view(np.uint32), got_f.view(np.uint32)), "fused clean differs from TDSC then FDSC"
+        if mask_fmt == "bits":
+            assert np.array_equal(gf, (bt | bf) > 0)
+        elif mask_fmt == "bytes":
+            assert np.array_equal(gf, bt | bf)
+        return nd
+    want, wf, margin = oracle.clean_f32_margin(x, layout, tdsc=td, fdsc=fd)
+    got, gf = run_gpu(ctx, x, layout=layout, tdsc=td, fdsc=fd, mask_fmt=mask_fmt, api=api, **kw)
+    return compare_f32(x, want, wf, margin, got, _gpu_flags(got, gf, x, mask_fmt), rows if td else cols, mask_fmt,
+                       byte_flags=gf if mask_fmt == "bytes" else None)
 
 
 def chi2_block(rng, B, C, T, gain=True):
@@ -172,6 +214,16 @@ def test_f32_many_k(oracle, ctx):
         check_f32(oracle, ctx, x, td=dict(k=k, iterations=2, replace="median"), fd=dict(k=k, iterations=2, bin=5))
 
 
+@pytest.mark.parametrize("k", [1e-300, 1e-40, 1e-12, 1e-3, 5e5, 2e6, 1e39, 1e300])
+def test_f32_extreme_k(oracle, ctx, k):
+    rng = np.random.default_rng(int(abs(np.log10(k))) + 5)
+    x = chi2_block(rng, 2, 40, 300)
+    x[0, 3, :] = 1.5  # constant row
+    for rep in ("mean", "median"):
+        check_f32(oracle, ctx, x, td=dict(k=k, iterations=2, replace=rep), fd=dict(k=k, iterations=2, replace=rep,
+                                                                                  bin=16))
+
+
 def test_fp32_workload_full_beam(oracle, ctx):
     # one full beam of the float32 configuration: 4096 x 8192, fused, k = 2.5, 3 iterations, mean
     from paper_2001_03389_gb300 import synth
@@ -180,6 +232,43 @@ def test_fp32_workload_full_beam(oracle, ctx):
     x = synth.make_beams(synth.FP32, beams=[0])
     nd = check_f32(oracle, ctx, x, td=spec["tdsc"], fd=spec["fdsc"])
     print(f"float32 workload, beam 0: {nd} allowed mask disagreements")
+
+
+def test_fp32_workload_full_launch_sampled(oracle, ctx):
+    # The float32 configuration at full size, in the launch the benchmark times:
+    # 32 beams x 4096 channels x 8192 samples drawn on the device, one fused
+    # rfim_clean (k = 2.5, 3 iterations, mean).  Beams 0 and 31 of that launch
+    # equal TDSC then FDSC launched on the beam alone, bit for bit, and those
+    # two launches match the oracle within the float32 tolerance.
+    import torch
+
+    from gpu_util import unpack_bits
+    from paper_2001_03389_gb300 import rfim, synth
+
+    spec = synth.WORKLOADS[synth.FP32]
+    dev = torch.device("cuda:0")
+    xin = synth.torch_make_beams(synth.FP32, spec["B"], synth.seed_of(synth.FP32), dev)
+    B, C, T = xin.shape
+    out = torch.empty_like(xin)
+    mask = torch.zeros(rfim.mask_words(C, T, B), dtype=torch.int32, device=dev)
+    ctx.clean(ctx.block(xin, out, mask, "bct", "bits"), spec["tdsc"], spec["fdsc"])
+    torch.cuda.synchronize()
+    assert ctx.device_status() == rfim.OK
+    nd = 0
+    for b in (0, B - 1):
+        x = xin[b:b + 1].cpu().numpy()
+        got = out[b:b + 1].cpu().numpy()
+        gm = unpack_bits(mask.view(B, -1)[b].cpu().numpy(), C, T)[None]
+        got_t, bt = run_gpu(ctx, x, tdsc=spec["tdsc"], mask_fmt="bytes", api="tdsc")
+        got_f, bf = run_gpu(ctx, got_t, fdsc=spec["fdsc"], mask_fmt="bytes", api="fdsc")
+        assert np.array_equal(got.view(np.uint32), got_f.view(np.uint32)), b
+        assert np.array_equal(gm, (bt | bf) > 0), b
+        want_t, wft, mt = oracle.clean_f32_margin(x, "bct", tdsc=spec["tdsc"])
+        nd += compare_f32(x, want_t, wft, mt, got_t, bt > 0, (0, 1), "bytes", byte_flags=bt)
+        want_f, wff, mf = oracle.clean_f32_margin(got_t, "bct", fdsc=spec["fdsc"])
+        nd += compare_f32(got_t, want_f, wff, mf, got_f, bf > 0, (0, 2), "bytes", byte_flags=bf)
+    print(f"float32 workload, beams 0 and {B - 1} of the full launch: {nd} allowed mask disagreements")
+    assert nd <= 4
 
 
 def test_f32_tile_widths(oracle, ctx):
@@ -222,18 +311,8 @@ def test_f32_btc_layout(oracle, ctx, C, T):
     x = np.ascontiguousarray(xb.transpose(0, 2, 1))
     td = dict(k=2.5, iterations=3, replace="mean")
     fd = dict(k=2.5, iterations=3, replace="median", bin=min(32, C))
-    want, wf, margin = oracle.clean_f32_margin(x, "btc", tdsc=td, fdsc=fd)
     for kw in (dict(), dict(in_place=True), dict(mask_fmt="bytes")):
-        mf = kw.pop("mask_fmt", "bits")
-        got, gf = run_gpu(ctx, x, layout="btc", tdsc=td, fdsc=fd, mask_fmt=mf, **kw)
-        gflag = gf if mf == "bits" else gf > 0
-        dis = gflag != (wf > 0)
-        assert not (dis & ~(margin <= MARGIN)).any()
-        if not dis.any():
-            keep = ~(wf > 0)
-            assert np.array_equal(got[keep].view(np.uint32), x[keep].view(np.uint32))
-            both = wf > 0
-            assert np.all(np.abs(got[both].astype(np.float64) - want[both]) <= REL * np.abs(want[both]) + 1e-30)
+        check_f32(oracle, ctx, x, td=td, fd=fd, layout="btc", **kw)
 
 
 def test_f32_interleaved_order(oracle, ctx):

@@ -163,6 +163,18 @@ def test_many_k_values(oracle, ctx):
         check(oracle, ctx, x, td=dict(k=k, iterations=2, replace="median"), fd=dict(k=k, iterations=2, bin=5))
 
 
+@pytest.mark.parametrize("k", [1e-300, 1e-12, 1e-9, 3e-9, 1e-6, 1e-3, 0.05, 5e5, 1e6, 2e6, 1e20, 1e300])
+def test_extreme_k(oracle, ctx, k):
+    # any finite k > 0 is a valid cut (Sec. IV's n sigma); tiny k flags every
+    # sample off the mean, huge k flags nothing
+    rng = np.random.default_rng(int(abs(np.log10(k))) + 3)
+    x = noise_u8(rng, (2, 40, 700))
+    x[0, 5, :] = 77  # a constant row: sigma = 0 flags nothing for any k
+    for rep in ("mean", "median", "random"):
+        check(oracle, ctx, x, td=dict(k=k, iterations=2, replace=rep), fd=dict(k=k, iterations=2, replace=rep, bin=16),
+              mask_fmt="bytes")
+
+
 def test_arts_full_beam(oracle, ctx):
     # one full ARTS-shaped beam: 1536 x 12500, TDSC then FDSC, k=3, 2 iterations, median, bit mask
     from paper_2001_03389_gb300 import synth
@@ -228,9 +240,10 @@ def test_validation_errors(ctx):
     x = torch.zeros((1, 8, 64), dtype=torch.uint8, device="cuda:0")
     out = torch.zeros_like(x)
     blk = ctx.block(x, out)
-    with pytest.raises(rfim.RfimError) as e:
-        ctx.tdsc(blk, rfim.make_cut(0.0))
-    assert e.value.status == rfim.ERR_ARG
+    for bad_k in (0.0, -1.0, float("inf"), float("nan")):
+        with pytest.raises(rfim.RfimError) as e:
+            ctx.tdsc(blk, rfim.make_cut(bad_k))
+        assert e.value.status == rfim.ERR_ARG
     with pytest.raises(rfim.RfimError) as e:
         ctx.fdsc(blk, rfim.make_cut(3.0, bin=9))
     assert e.value.status == rfim.ERR_ARG
