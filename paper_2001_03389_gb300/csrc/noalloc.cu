@@ -34,21 +34,51 @@ unsigned* g_scratch[NOALLOC_MAX_DEVICES];
 
 using namespace rfim;
 
-extern "C" rfim_status rfim_clean_noalloc(const rfim_block* blk, const rfim_cut* tdsc, const rfim_cut* fdsc,
-                                          void* stream) {
+namespace rfim {
+namespace {
+// The scratch array's device address on the current device (looked up once per device).
+rfim_status noalloc_scratch(unsigned** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return RFIM_ERR_CUDA;
   if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return RFIM_ERR_ARG;
-  unsigned* scratch = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch[dev]) {
-      void* p = nullptr;
-      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess || !p) return RFIM_ERR_CUDA;
-      g_scratch[dev] = static_cast<unsigned*>(p);
-    }
-    scratch = g_scratch[dev];
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_scratch[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return RFIM_ERR_CUDA;
+    g_scratch[dev] = static_cast<unsigned*>(p);
   }
+  *out = g_scratch[dev];
+  return RFIM_OK;
+}
+}  // namespace
+}  // namespace rfim
+
+extern "C" rfim_status rfim_clean_noalloc(const rfim_block* blk, const rfim_cut* tdsc, const rfim_cut* fdsc,
+                                          void* stream) {
+  unsigned* scratch = nullptr;
+  const rfim_status s = noalloc_scratch(&scratch);
+  if (s != RFIM_OK) return s;
   return noalloc_clean(blk, tdsc, fdsc, scratch, scratch + 1 + MAX_JOBS, (cudaStream_t)stream);
+}
+
+// The status word is the last of the shared array: read it after `stream`'s
+// work, then clear it, with plain synchronous copies to and from a host
+// variable (no allocation).
+extern "C" rfim_status rfim_noalloc_status(void* stream) {
+  unsigned* scratch = nullptr;
+  rfim_status s = noalloc_scratch(&scratch);
+  if (s != RFIM_OK) return s;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return RFIM_ERR_CUDA;
+  }
+  unsigned word = 0;
+  const unsigned zero = 0;
+  if (cudaMemcpy(&word, scratch + 1 + MAX_JOBS, sizeof word, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      (word && cudaMemcpy(scratch + 1 + MAX_JOBS, &zero, sizeof zero, cudaMemcpyHostToDevice) != cudaSuccess)) {
+    (void)cudaGetLastError();
+    return RFIM_ERR_CUDA;
+  }
+  return word ? RFIM_ERR_TIMEOUT : RFIM_OK;
 }

@@ -52,10 +52,19 @@ rfim_status tuner_apply(Tuner* t, rfim_ctx* ctx, const rfim_block* blocks, int n
 // mask format), default tuning; `counters` holds 1 + 160 words, `status` one.
 rfim_status noalloc_clean(const rfim_block* b, const rfim_cut* tdsc, const rfim_cut* fdsc, unsigned* counters,
                           unsigned* status, cudaStream_t st);
+// stats (nullable): per block, a device array of 2 doubles per (beam, channel)
+// row that the first TDSC iteration fills with the input row's sum and sum of
+// squares; spin_limit_ns bounds every device-side wait; withhold_job (-1 =
+// none) is the test hook of rfim_set_option("withhold_tdsc_done").
 rfim_status launch_blocks_fixed(const rfim_block* blocks, int n, const rfim_cut* tdsc, const rfim_cut* fdsc,
-                                unsigned* counters, unsigned* status, cudaStream_t st);
+                                unsigned* counters, unsigned* status, cudaStream_t st, double* const* stats = nullptr,
+                                unsigned long long spin_limit_ns = 2000000000ull, int withhold_job = -1);
+// the context's spin limit (ns) and withhold test hook (-1 = off), as the next launch would use them
+void ctx_wait_options(rfim_ctx* ctx, unsigned long long& spin_limit_ns, int& withhold_job);
 
 // streaming service (stream.cu)
 void stream_service_destroy(StreamService* s);
+// batches of the service whose device-side wait gave up since the last call (clears the count)
+unsigned long long stream_service_take_timeouts(StreamService* s);
 
 }  // namespace rfim

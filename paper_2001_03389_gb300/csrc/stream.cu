@@ -7,6 +7,16 @@
 // batches overlap on the device, and a host function enqueued behind each
 // batch marks its chunks done.  Device-pointer chunks are read in place (the
 // kernels clean them into the slot), host chunks are copied into the slot.
+//
+// Per-beam state on the device: every slot also holds its chunk's per-channel
+// input statistics (sum and sum of squares, written by the first TDSC pass),
+// and each beam keeps the slot of its latest completed chunk -- cleaned data,
+// mask and statistics -- resident until a newer chunk of the beam completes.
+// The statistics are records for the caller; no decision reads them.
+//
+// Each stream's launches report their device status word (a bounded wait
+// that gave up) through pinned host memory; a batch that timed out completes
+// its chunks with RFIM_ERR_TIMEOUT.
 #include <cuda_runtime.h>
 #include <time.h>
 
@@ -44,6 +54,8 @@ struct Ticket {
   int slot;
   int beam;
   int state;
+  rfim_status status;      // result once done: RFIM_OK, or why the chunk's batch failed
+  unsigned long long seq;  // index of the chunk among its beam's pushes
   const void* src;  // device chunk read in place, or the slot itself (host chunks)
   double arrival;
   double done;
@@ -63,8 +75,16 @@ struct StreamService {
   int n_slots = 0;
   unsigned char* d_slots = nullptr;
   unsigned char* d_masks = nullptr;
+  double* d_stats = nullptr;  // per slot: 2 doubles per channel (input sum, sum of squares)
   unsigned* d_ctr = nullptr;  // N_STREAMS counter blocks + status words
+  unsigned* h_status = nullptr;  // pinned: each stream's status word after its last batch
+  unsigned long long spin_limit_ns = 2000000000ull;
+  int withhold = -1;
   std::vector<int> free_slots;
+  std::vector<int> slot_refs;  // holders of a slot: its ticket until released, its beam's state
+  std::vector<int> beam_slot;  // slot of each beam's latest completed chunk (-1: none yet)
+  std::vector<unsigned long long> beam_seq;  // that chunk's index among the beam's pushes
+  int state_slots = 0;                       // slots held as beam states
   std::unordered_map<unsigned long long, Ticket> tickets;
   unsigned long long next_ticket = 1;
   std::deque<unsigned long long> waiting;
@@ -83,6 +103,7 @@ struct StreamService {
   double bytes_done = 0.0, first_arrival = 0.0, last_done = 0.0;
   std::vector<unsigned long long> beam_chunks;
   std::vector<double> beam_last_latency;
+  unsigned long long timeouts = 0;  // batches whose device-side wait gave up, not yet reported
   // threads
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -94,20 +115,41 @@ struct StreamService {
 
 namespace {
 
+// one holder of slot i fewer; a slot nobody holds returns to the pool (under s->mu)
+void slot_unref(StreamService* s, int i) {
+  if (--s->slot_refs[i] == 0) s->free_slots.push_back(i);
+}
+
 // Host function behind a batch: its chunks are done (runs on a CUDA thread,
-// makes no CUDA call).
+// makes no CUDA call; the stream's status word was copied to h_status first).
 void CUDART_CB batch_done(void* arg) {
   auto* b = static_cast<StreamService::Batch*>(arg);
   StreamService* s = b->svc;
   const double t = now_mono();
+  const rfim_status st = s->h_status[b->lane] ? RFIM_ERR_TIMEOUT : RFIM_OK;
   {
     std::lock_guard<std::mutex> g(s->mu);
+    if (st != RFIM_OK) {
+      s->fault = st;
+      s->timeouts++;
+    }
     for (unsigned long long id : b->ids) {
       auto it = s->tickets.find(id);
       if (it == s->tickets.end()) continue;
       Ticket& k = it->second;
       k.state = T_DONE;
+      k.status = st;
       k.done = t;
+      const int old = s->beam_slot[k.beam];
+      // the beam's newest result: its slot becomes the beam's state (a beam
+      // without one takes a slot only while states hold under half of them)
+      if (st == RFIM_OK && (old < 0 ? 2 * s->state_slots < s->n_slots : k.seq > s->beam_seq[k.beam])) {
+        if (old < 0) s->state_slots++;
+        s->beam_slot[k.beam] = k.slot;
+        s->beam_seq[k.beam] = k.seq;
+        s->slot_refs[k.slot]++;
+        if (old >= 0) slot_unref(s, old);
+      }
       const double l = t - k.arrival;
       s->lat.push_back(l);
       if (s->lat.size() == 1 || k.arrival < s->first_arrival) s->first_arrival = k.arrival;
@@ -125,7 +167,9 @@ void CUDART_CB batch_done(void* arg) {
 void dispatch_loop(StreamService* s) {
   cudaSetDevice(s->device);
   std::vector<rfim_block> blocks;
+  std::vector<double*> stats;
   blocks.reserve(MAX_BATCH);
+  stats.reserve(MAX_BATCH);
   std::unique_lock<std::mutex> lk(s->mu);
   for (;;) {
     int lane = -1;
@@ -146,6 +190,7 @@ void dispatch_loop(StreamService* s) {
     StreamService::Batch& b = s->batches[lane];
     b.ids.clear();
     blocks.clear();
+    stats.clear();
     while (!s->waiting.empty() && (int)b.ids.size() < MAX_BATCH) {
       const unsigned long long id = s->waiting.front();
       s->waiting.pop_front();
@@ -163,14 +208,20 @@ void dispatch_loop(StreamService* s) {
       blk.layout = RFIM_LAYOUT_BCT;
       blk.mask_fmt = RFIM_MASK_BITS;
       blocks.push_back(blk);
+      stats.push_back(s->d_stats + (size_t)k.slot * 2 * s->C);
     }
     s->busy[lane] = true;
     lk.unlock();
     unsigned* ctr = s->d_ctr + (size_t)lane * CTR_WORDS;
     rfim_status st = launch_blocks_fixed(blocks.data(), (int)blocks.size(), s->has_td ? &s->td : nullptr,
-                                         s->has_fd ? &s->fd : nullptr, ctr, ctr + 1 + MAX_JOBS, s->streams[lane]);
+                                         s->has_fd ? &s->fd : nullptr, ctr, ctr + 1 + MAX_JOBS, s->streams[lane],
+                                         stats.data(), s->spin_limit_ns, s->withhold);
     cudaError_t e = cudaSuccess;
-    if (st == RFIM_OK) e = cudaLaunchHostFunc(s->streams[lane], batch_done, &b);
+    // the batch's status word (cleared by the launch) to the host, then the completion
+    if (st == RFIM_OK)
+      e = cudaMemcpyAsync(s->h_status + lane, ctr + 1 + MAX_JOBS, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                          s->streams[lane]);
+    if (st == RFIM_OK && e == cudaSuccess) e = cudaLaunchHostFunc(s->streams[lane], batch_done, &b);
     if (e != cudaSuccess) (void)cudaGetLastError();
     lk.lock();
     if (st != RFIM_OK || e != cudaSuccess) {
@@ -180,6 +231,7 @@ void dispatch_loop(StreamService* s) {
         auto it = s->tickets.find(id);
         if (it != s->tickets.end()) {
           it->second.state = T_DONE;
+          it->second.status = s->fault;
           it->second.done = now_mono();
         }
       }
@@ -207,7 +259,9 @@ void svc_free(StreamService* s) {
   if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
   cudaFree(s->d_slots);
   cudaFree(s->d_masks);
+  cudaFree(s->d_stats);
   cudaFree(s->d_ctr);
+  cudaFreeHost(s->h_status);
   delete s;
 }
 
@@ -228,6 +282,14 @@ rfim_status svc_push(StreamService* s, int beam, const void* chunk, bool on_devi
 }  // namespace
 
 void stream_service_destroy(StreamService* s) { svc_free(s); }
+
+// Batches whose device-side wait gave up since the last call (then cleared).
+unsigned long long stream_service_take_timeouts(StreamService* s) {
+  std::lock_guard<std::mutex> g(s->mu);
+  const unsigned long long n = s->timeouts;
+  s->timeouts = 0;
+  return n;
+}
 
 }  // namespace rfim
 
@@ -306,15 +368,22 @@ rfim_status rfim_stream_open(rfim_ctx* ctx, int n_beams, int channels, int chunk
   }
   if (cudaMalloc(&s->d_slots, s->chunk_bytes * s->n_slots) != cudaSuccess ||
       cudaMalloc(&s->d_masks, s->mask_bytes * s->n_slots) != cudaSuccess ||
-      cudaMalloc(&s->d_ctr, sizeof(unsigned) * CTR_WORDS * N_STREAMS) != cudaSuccess) {
+      cudaMalloc(&s->d_stats, sizeof(double) * 2 * channels * s->n_slots) != cudaSuccess ||
+      cudaMalloc(&s->d_ctr, sizeof(unsigned) * CTR_WORDS * N_STREAMS) != cudaSuccess ||
+      cudaMallocHost(&s->h_status, sizeof(unsigned) * N_STREAMS) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(s->d_slots);
     cudaFree(s->d_masks);
+    cudaFree(s->d_stats);
+    cudaFree(s->d_ctr);
     delete s;
     ctx_set_error(ctx, "streaming slot allocation failed");
     return RFIM_ERR_OOM;
   }
   cudaMemset(s->d_ctr, 0, sizeof(unsigned) * CTR_WORDS * N_STREAMS);
+  cudaMemset(s->d_stats, 0, sizeof(double) * 2 * channels * s->n_slots);
+  memset(s->h_status, 0, sizeof(unsigned) * N_STREAMS);
+  ctx_wait_options(ctx, s->spin_limit_ns, s->withhold);
   for (int i = 0; i < N_STREAMS; i++) {
     cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking);
     s->batches[i].svc = s;
@@ -323,6 +392,9 @@ rfim_status rfim_stream_open(rfim_ctx* ctx, int n_beams, int channels, int chunk
   cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
   s->free_slots.reserve(s->n_slots);
   for (int i = s->n_slots - 1; i >= 0; i--) s->free_slots.push_back(i);
+  s->slot_refs.assign(s->n_slots, 0);
+  s->beam_slot.assign(n_beams, -1);
+  s->beam_seq.assign(n_beams, 0);
   s->beam_chunks.assign(n_beams, 0);
   s->beam_last_latency.assign(n_beams, 0.0);
   s->dispatcher = std::thread(dispatch_loop, s);
@@ -351,6 +423,7 @@ rfim_status svc_push(StreamService* s, int beam, const void* chunk, bool on_devi
     if (s->free_slots.empty()) return RFIM_ERR_BUSY;
     slot = s->free_slots.back();
     s->free_slots.pop_back();
+    s->slot_refs[slot] = 1;  // held by its ticket
   }
   const void* src = chunk;
   if (!on_device) {
@@ -366,7 +439,7 @@ rfim_status svc_push(StreamService* s, int beam, const void* chunk, bool on_devi
     if (e != cudaSuccess) {
       (void)cudaGetLastError();  // reported by the status: not left for the caller's next call
       std::lock_guard<std::mutex> g(s->mu);
-      s->free_slots.push_back(slot);
+      slot_unref(s, slot);
       return RFIM_ERR_CUDA;
     }
     src = dst;
@@ -380,6 +453,8 @@ rfim_status svc_push(StreamService* s, int beam, const void* chunk, bool on_devi
     k.slot = slot;
     k.beam = beam;
     k.state = T_WAITING;
+    k.status = RFIM_OK;
+    k.seq = s->beam_chunks[beam];
     k.src = src;
     k.arrival = arrival_time_s;
     k.done = 0.0;
@@ -414,7 +489,7 @@ rfim_status rfim_stream_poll(rfim_ctx* ctx, unsigned long long ticket, void** ou
     if (it == s->tickets.end()) return RFIM_ERR_ARG;
   }
   if (it->second.state != T_DONE) return RFIM_ERR_BUSY;
-  if (s->fault != RFIM_OK) return s->fault;
+  if (it->second.status != RFIM_OK) return it->second.status;
   if (out_dev) *out_dev = s->d_slots + (size_t)it->second.slot * s->chunk_bytes;
   if (mask_dev) *mask_dev = s->d_masks + (size_t)it->second.slot * s->mask_bytes;
   return RFIM_OK;
@@ -428,9 +503,44 @@ rfim_status rfim_stream_release(rfim_ctx* ctx, unsigned long long ticket) {
   auto it = s->tickets.find(ticket);
   if (it == s->tickets.end()) return RFIM_ERR_ARG;
   if (it->second.state != T_DONE) return RFIM_ERR_BUSY;
-  s->free_slots.push_back(it->second.slot);
+  slot_unref(s, it->second.slot);
   s->tickets.erase(it);
   return RFIM_OK;
+}
+
+rfim_status rfim_stream_beam_state(rfim_ctx* ctx, int beam, unsigned long long* chunk_index, double* stats,
+                                   const void** out_dev, const void** mask_dev) {
+  StreamService* s = svc_of(ctx);
+  if (!ctx) return RFIM_ERR_ARG;
+  if (!s) return RFIM_ERR_STATE;
+  if (beam < 0 || beam >= s->n_beams) return RFIM_ERR_ARG;
+  int slot;
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    slot = s->beam_slot[beam];
+    if (slot < 0) return RFIM_ERR_BUSY;
+    if (chunk_index) *chunk_index = s->beam_seq[beam];
+    if (out_dev) *out_dev = s->d_slots + (size_t)slot * s->chunk_bytes;
+    if (mask_dev) *mask_dev = s->d_masks + (size_t)slot * s->mask_bytes;
+    s->slot_refs[slot]++;  // held while its statistics are copied out
+  }
+  rfim_status st = RFIM_OK;
+  if (stats) {
+    cudaError_t e;
+    {
+      std::lock_guard<std::mutex> g(s->copy_mu);
+      e = cudaMemcpyAsync(stats, s->d_stats + (size_t)slot * 2 * s->C, sizeof(double) * 2 * s->C,
+                          cudaMemcpyDeviceToHost, s->copy_stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s->copy_stream);
+    }
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      st = RFIM_ERR_CUDA;
+    }
+  }
+  std::lock_guard<std::mutex> g(s->mu);
+  slot_unref(s, slot);
+  return st;
 }
 
 rfim_status rfim_stream_replay(rfim_ctx* ctx, int n, const int* beams, const void* const* chunks,

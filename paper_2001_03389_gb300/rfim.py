@@ -59,10 +59,13 @@ _SIGS = {
     "rfim_clean_host": ([_vp, _blkp, _cutp, _cutp], ctypes.c_int),
     "rfim_device_status": ([_vp, _vp], ctypes.c_int),
     "rfim_clean_noalloc": ([_blkp, _cutp, _cutp, _vp], ctypes.c_int),
+    "rfim_noalloc_status": ([_vp], ctypes.c_int),
     "rfim_stream_open": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _cutp, _cutp], ctypes.c_int),
     "rfim_stream_push": ([_vp, ctypes.c_int, _vp, ctypes.c_double, ctypes.POINTER(ctypes.c_ulonglong)], ctypes.c_int),
     "rfim_stream_poll": ([_vp, ctypes.c_ulonglong, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int], ctypes.c_int),
     "rfim_stream_release": ([_vp, ctypes.c_ulonglong], ctypes.c_int),
+    "rfim_stream_beam_state": ([_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(_vp), ctypes.POINTER(_vp)], ctypes.c_int),
     "rfim_stream_replay": ([_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_vp),
                             ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "rfim_stream_stats": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -216,6 +219,22 @@ class Context:
 
     def stream_release(self, ticket):
         self._check(rfim_stream_release(self.h, ticket), "rfim_stream_release")
+
+    def stream_beam_state(self, beam, channels):
+        """(chunk index, stats (channels x 2: input sum, sum of squares), out_ptr,
+        mask_ptr) of the beam's latest completed chunk, or None before its first."""
+        import numpy as np
+
+        idx = ctypes.c_ulonglong()
+        stats = np.zeros((channels, 2), dtype=np.float64)
+        o, m = _vp(), _vp()
+        st = rfim_stream_beam_state(self.h, int(beam), ctypes.byref(idx),
+                                    stats.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(o),
+                                    ctypes.byref(m))
+        if st == ERR_BUSY:
+            return None
+        self._check(st, "rfim_stream_beam_state")
+        return idx.value, stats, o.value, m.value
 
     def stream_replay(self, beams, chunk_ptrs, arrivals):
         import numpy as np

@@ -240,3 +240,79 @@ def test_stream_random_replacement_matches_oracle(lib, oracle):
     finally:
         ctx.stream_close()
         ctx.close()
+
+
+def test_stream_per_beam_device_state(lib):
+    # Each beam keeps its latest completed chunk on the device: the cleaned
+    # data, mask and per-channel sums of the chunk's input.  The sums are the
+    # plain totals of the input (checked against numpy); they never enter a
+    # decision (the results above equal rfim_clean of the chunk alone).
+    from gpu_util import device_bytes
+
+    rfim = lib
+    C, T = 128, 1250
+    ctx = rfim.Context(0)
+    try:
+        ctx.stream_open(3, C, T, rfim.U8, rfim.make_cut(**TD), rfim.make_cut(**FD))
+        pool = chunks_u8(9, C, T, seed=31)
+        assert ctx.stream_beam_state(0, C) is None  # nothing completed yet
+        last = {}
+        for i in range(9):
+            b = i % 3
+            tk = ctx.stream_push(b, pool[i], time.monotonic())
+            assert tk is not None
+            out, mask = result(rfim, ctx, tk, C, T, rfim.U8)
+            ctx.stream_release(tk)
+            last[b] = (i // 3, pool[i].cpu().numpy().astype(np.int64), out, mask)
+        for b, (idx, x, out, mask) in last.items():
+            got = ctx.stream_beam_state(b, C)
+            assert got is not None
+            gi, stats, op, mp = got
+            assert gi == idx
+            assert np.array_equal(stats[:, 0], x.sum(axis=1).astype(np.float64))
+            assert np.array_equal(stats[:, 1], (x * x).sum(axis=1).astype(np.float64))
+            # the retained slot still holds that chunk's cleaned data and mask
+            assert np.array_equal(device_bytes(op, C * T).cpu().numpy(), out)
+            W = (T + 31) // 32
+            assert np.array_equal(device_bytes(mp, C * W * 4).cpu().numpy().view(np.int32), mask)
+        assert ctx.device_status() == rfim.OK
+        ctx.stream_close()
+    finally:
+        ctx.close()
+
+
+def test_stream_batch_timeout_is_reported(lib):
+    # A device-side wait that gives up inside a streaming batch: the test hook
+    # withholds the TDSC completion of the batch's first beam, so its FDSC
+    # items wait out a short spin limit.  The chunks of that batch complete
+    # with RFIM_ERR_TIMEOUT, rfim_device_status reports it once, and the
+    # context and the service stay usable.
+    rfim = lib
+    C, T = 64, 4000  # rows longer than ~3,150 samples: one fused launch per batch
+    ctx = rfim.Context(0)
+    try:
+        ctx.set_option("withhold_tdsc_done", 1)
+        ctx.set_option("spin_limit_us", 20000)
+        ctx.stream_open(2, C, T, rfim.U8, rfim.make_cut(**TD), rfim.make_cut(**FD))
+        pool = chunks_u8(2, C, T, seed=41)
+        tk = ctx.stream_push(0, pool[0], time.monotonic())
+        with pytest.raises(rfim.RfimError) as e:
+            ctx.stream_poll(tk, wait_us=5_000_000)
+        assert e.value.status == rfim.ERR_TIMEOUT
+        ctx.stream_release(tk)
+        assert ctx.device_status() == rfim.ERR_TIMEOUT
+        assert ctx.device_status() == rfim.OK  # reported once
+        ctx.stream_close()
+        # a new service without the hook cleans normally
+        ctx.set_option("withhold_tdsc_done", 0)
+        ctx.set_option("spin_limit_us", 2000000)
+        ctx.stream_open(2, C, T, rfim.U8, rfim.make_cut(**TD), rfim.make_cut(**FD))
+        tk = ctx.stream_push(1, pool[1], time.monotonic())
+        out, _ = result(rfim, ctx, tk, C, T, rfim.U8)
+        ctx.stream_release(tk)
+        ref, _ = reference(rfim, ctx, pool[1])
+        assert np.array_equal(out, ref)
+        assert ctx.device_status() == rfim.OK
+        ctx.stream_close()
+    finally:
+        ctx.close()
