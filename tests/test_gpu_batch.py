@@ -140,3 +140,41 @@ def test_batch_graph_interleaved(ctx, oracle):
         assert ctx.device_status() == rfim.OK
     finally:
         ctx.set_option("order", 0)
+
+
+def test_ragged_batch_full_size(ctx, oracle):
+    # The ragged configuration at full size: 200 beams, C from {384, 768, 1536,
+    # 4096}, T uniform in [1000, 25000] (4.16 GB), drawn on the device.
+    # One graph-captured, autotuned rfim_clean_batch equals 200 separate
+    # rfim_clean calls bit for bit (a replay too), and three beams -- the first,
+    # the longest, and the shortest 4096-channel one -- equal the oracle.
+    import torch
+
+    from gpu_util import unpack_bits
+    from paper_2001_03389_gb300 import rfim, synth
+
+    shapes = synth.ragged_shapes(200)
+    beams = synth.torch_ragged_batch(shapes, seed=synth.RAGGED_SEED, device="cuda:0")
+    assert sum(c * t for c, t in shapes) > 4e9
+    td, fd = rfim.make_cut(**CUTS["tdsc"]), rfim.make_cut(**CUTS["fdsc"])
+    ref_o, ref_m, ref_b = _blocks(rfim, beams)
+    for b in ref_b:
+        ctx.clean(b, td, fd)
+    torch.cuda.synchronize()
+    for _ in range(2):  # capture (after tuning), then replay
+        o, m, b = _blocks(rfim, beams)
+        ctx.clean_batch(b, td, fd, flags=rfim.BATCH_GRAPH | rfim.BATCH_AUTOTUNE)
+        torch.cuda.synchronize()
+        for i in range(len(beams)):
+            assert torch.equal(o[i], ref_o[i]), (i, shapes[i])
+            assert torch.equal(m[i], ref_m[i]), (i, shapes[i])
+        del o, m, b
+    assert ctx.device_status() == rfim.OK
+    longest = max(range(200), key=lambda i: shapes[i][1])
+    wide = min((i for i in range(200) if shapes[i][0] == 4096), key=lambda i: shapes[i][1])
+    for i in (0, longest, wide):
+        C, T = shapes[i]
+        x = beams[i].cpu().numpy()[None]
+        want, wf = oracle.clean(x, "bct", tdsc=CUTS["tdsc"], fdsc=CUTS["fdsc"])
+        assert np.array_equal(ref_o[i].cpu().numpy()[None], want), shapes[i]
+        assert np.array_equal(unpack_bits(ref_m[i].cpu().numpy(), C, T)[None], wf > 0), shapes[i]
