@@ -102,13 +102,9 @@ rfim_status cuda_fail(rfim_ctx* ctx, cudaError_t e, const char* what) {
 }
 
 ExactK2 make_k2(double k) {
-  const double k2 = k * k;
-  int e = 0;
-  const double f = std::frexp(k2, &e);  // k2 = f * 2^e, f in [0.5, 1)
   ExactK2 r;
-  r.M = (unsigned long long)std::ldexp(f, 53);
-  r.E = e - 53;
-  r.k2f = (float)k2;
+  r.k2 = k * k;  // fl(k * k): one IEEE rounding
+  r.k2f = (float)r.k2;
   return r;
 }
 

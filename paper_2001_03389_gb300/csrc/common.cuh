@@ -3,58 +3,30 @@
 // Exact uint8 decisions.  The library decides a uint8 flag as
 //     (double)lhs > fl(k2 * (double)R)
 // with lhs, R exact integers below 2^53 and k2 = fl(k*k) a double (TDSC:
-// lhs = (T x - S)^2, R = T Q - S^2; FDSC: lhs = C D^2, R = sum D^2).  On GB300
-// an FP64 warp instruction occupies the SM's FP64 pipe for ~20 cycles even
-// with one active lane, so the product is evaluated in 128-bit integers:
-// k2 = M * 2^E with an integer 53-bit M, the exact product M * R is rounded to
-// 53 significant bits (round to nearest, ties to even -- the IEEE rounding of
-// the double product) and compared with lhs scaled by 2^-E.
+// lhs = (T x - S)^2, R = T Q - S^2; FDSC: lhs = C D^2, R = sum D^2).  The right
+// side is evaluated as written, one IEEE double multiply per row or column and
+// iteration, and turned into the integer floor(fl(k2 R)): for integers lhs,
+// lhs > fl(k2 R) iff lhs > floor(fl(k2 R)), so every per-candidate test is a
+// 64-bit integer comparison.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
 
 namespace rfim {
 
-typedef unsigned __int128 u128;
-
 constexpr int NT = 256;  // threads per CTA in every kernel of the engine
 
-// k2 = fl(k*k) = M * 2^E exactly, M in [2^52, 2^53).  Built on the host.
+// The squared threshold of a cut.  Built on the host.
 struct ExactK2 {
-  unsigned long long M;
-  int E;
+  double k2;  // fl(k * k)
   float k2f;  // k2 rounded to float, for first guesses only
 };
 
-__device__ __forceinline__ int bitlen128(u128 x) {
-  const unsigned long long hi = (unsigned long long)(x >> 64);
-  const unsigned long long lo = (unsigned long long)x;
-  if (hi) return 128 - __clzll((long long)hi);
-  if (lo) return 64 - __clzll((long long)lo);
-  return 0;
-}
-
-// (double)lhs <= fl(k2 * (double)R), for integers lhs, R < 2^53.
-__device__ __forceinline__ bool le_thr(unsigned long long lhs, unsigned long long R, const ExactK2& k) {
-  if (R == 0) return lhs == 0;
-  u128 q = (u128)k.M * R;
-  int s = bitlen128(q) - 53;
-  if (s > 0) {
-    const u128 rem = q & (((u128)1 << s) - 1);
-    const u128 half = (u128)1 << (s - 1);
-    q >>= s;
-    if (rem > half || (rem == half && (q & 1))) q += 1;
-  } else {
-    s = 0;
-  }
-  const int e = s + k.E;  // threshold = q * 2^e
-  if (e >= 0) {
-    if (e >= 60) return true;  // q >= 1 so the threshold is >= 2^60 > lhs
-    return (u128)lhs <= (q << e);
-  }
-  const int ne = -e;
-  if (ne >= 75) return lhs == 0;  // lhs * 2^ne would exceed every q < 2^54
-  return ((u128)lhs << ne) <= q;
+// floor(fl(k2 * R)) for an integer R < 2^53, saturated at 2^62 (beyond every
+// left side, which stays below 2^53).
+__device__ __forceinline__ unsigned long long thr_floor(unsigned long long R, const ExactK2& k) {
+  const double t = __dmul_rn(k.k2, __ull2double_rn(R));
+  return t < 4.0e18 ? __double2ull_rz(t) : (1ull << 62);
 }
 
 // ---------------------------------------------------------------------------

@@ -87,19 +87,19 @@ __device__ __forceinline__ void or16_partial(uint8_t* dst, const uint4& v, int l
 // exact keep intervals, computed by a group of lanes in parallel
 // ---------------------------------------------------------------------------
 
-// A = max{a in [0, amax] : (double)(mult a^2) <= fl(k2 R)}.  The W lanes of an
-// aligned group (W = 8 or 32) each test one candidate around a float estimate;
-// the passing candidates form a prefix.  All lanes of the group return A.
+// A = max{a in [0, amax] : mult a^2 <= F}, F = floor(fl(k2 R)) (thr_floor): the
+// largest |d x - S| a kept sample may have.  The W lanes of an aligned group
+// (W = 8 or 32) each test one candidate around a float estimate; the passing
+// candidates form a prefix.  All lanes of the group return A.
 template <int W>
-__device__ __forceinline__ unsigned max_keep_grp(unsigned long long R, unsigned long long mult, unsigned amax,
-                                                 const ExactK2& k) {
+__device__ __forceinline__ unsigned max_keep_grp(unsigned long long F, unsigned long long mult, unsigned amax) {
   const int lane = threadIdx.x & 31;
   const int gl = lane & (W - 1);
   const int gshift = lane & ~(W - 1);
   const unsigned full = (W == 32) ? 0xffffffffu : ((1u << W) - 1u);
   const unsigned gmask = full << gshift;
-  const float est = sqrtf(k.k2f * (float)R / (float)mult);
-  long long e = (long long)est;
+  const float est = sqrtf((float)F / (float)mult);
+  long long e = est < 4.0e9f ? (long long)est : (long long)amax;
   if (e > (long long)amax) e = amax;  // A never exceeds amax
   long long base = e - (W / 2 - 1);
   for (int round = 0; round < 1024; round++) {
@@ -107,7 +107,7 @@ __device__ __forceinline__ unsigned max_keep_grp(unsigned long long R, unsigned 
     bool ok;
     if (a < 0) ok = true;
     else if (a > (long long)amax) ok = false;
-    else ok = le_thr(mult * (unsigned long long)a * (unsigned long long)a, R, k);
+    else ok = mult * (unsigned long long)a * (unsigned long long)a <= F;
     const unsigned b = (__ballot_sync(gmask, ok) >> gshift) & full;
     if (b == full) {
       if (base + (W - 1) >= (long long)amax) return amax;
@@ -136,7 +136,7 @@ __device__ __forceinline__ void tdsc_keep_warp(unsigned long long S, unsigned lo
                                                const ExactK2& k2, int& lo, int& hi) {
   const unsigned long long Tl = (unsigned long long)T;
   const unsigned long long R = Tl * Q - S * S;
-  const unsigned A = max_keep_grp<(LANES < 32 ? LANES : 32)>(R, 1ull, 255u * (unsigned)T, k2);
+  const unsigned A = max_keep_grp<(LANES < 32 ? LANES : 32)>(thr_floor(R, k2), 1ull, 255u * (unsigned)T);
   keep_from((unsigned)S, A, (unsigned)T, rcpT, lo, hi);
 }
 
@@ -393,6 +393,45 @@ __device__ __forceinline__ void td_stats_pass(const Rd& rd, int nch, int gl, con
   }
 }
 
+// One statistics pass over a staged row of at most 32 chunks per lane (single-
+// replacement mode): sums of the samples OUTSIDE [lo, hi] and their count, and
+// with PROBE the SAD sums of the median probes.  Outliers are rare, so a sweep
+// takes the probes and a cheap superset test of each chunk; each lane then sums
+// its own chunks that hold an outlier, exactly.  Padding bytes of the edge
+// chunks are 0; the caller corrects the count for them.
+template <int LANES, bool ODD, bool PROBE, typename Rd>
+__device__ __forceinline__ void td_outlier_pass(const Rd& rd, int nch, int gl, const ByteKeep& kp,
+                                                const uint32_t (&p4)[4], unsigned (&f32)[4], unsigned& s_out,
+                                                unsigned long long& q_out, unsigned& n_out) {
+  uint32_t slow = 0;
+  for (int k = gl, r = 0; k < nch; k += LANES, r++) {
+    const uint4 w = rd(k);
+    if (PROBE) {
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        f32[i] = sad4(w.x, p4[i], f32[i]);
+        f32[i] = sad4(w.y, p4[i], f32[i]);
+        f32[i] = sad4(w.z, p4[i], f32[i]);
+        f32[i] = sad4(w.w, p4[i], f32[i]);
+      }
+    }
+    const uint32_t t = outside_fast(w.x, kp) | outside_fast(w.y, kp) | outside_fast(w.z, kp) | outside_fast(w.w, kp);
+    if (t & 0x80808080u) slow |= 1u << r;
+  }
+  while (slow) {
+    const int r = __ffs(slow) - 1;
+    slow &= slow - 1;
+    const uint4 w = rd(gl + r * LANES);
+    const uint32_t f0 = outside_ne<ODD>(w.x, kp), f1 = outside_ne<ODD>(w.y, kp);
+    const uint32_t f2 = outside_ne<ODD>(w.z, kp), f3 = outside_ne<ODD>(w.w, kp);
+    const uint32_t o0 = w.x & wide8(f0), o1 = w.y & wide8(f1), o2 = w.z & wide8(f2), o3 = w.w & wide8(f3);
+    s_out += dp4a_u(o0, 0x01010101u, 0u) + dp4a_u(o1, 0x01010101u, 0u) + dp4a_u(o2, 0x01010101u, 0u) +
+             dp4a_u(o3, 0x01010101u, 0u);
+    q_out += dp4a_u(o0, o0, 0u) + dp4a_u(o1, o1, 0u) + dp4a_u(o2, o2, 0u) + dp4a_u(o3, o3, 0u);
+    n_out += (__popc(f0) + __popc(f1)) + (__popc(f2) + __popc(f3));
+  }
+}
+
 // STREAM: the row is longer than the shared-memory stage; every pass reads its
 // 16-byte chunks from global memory (L2) instead, edge chunks masked as the
 // staging would, and `st` only holds the output pass's flag words.
@@ -500,7 +539,9 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
 
   if (single) {
     // Every replaced value is the median m, so after iteration i a sample holds
-    // x if x lies in every keep interval so far, else m: S_{i+1} = s_in + n_out m.
+    // x if x lies in every keep interval so far, else m: S_{i+1} = s_in + n_out m,
+    // with s_in = S0 - (sum of the samples outside), S0 the sum of the input row.
+    const unsigned long long S0 = S, Q0 = Q;
     MedSearch ms;
     med_init(ms, S, Q, T);
     for (int it = 0; it < I; it++) {
@@ -524,7 +565,7 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
         s_in = 0;
         q_in = 0;
         n_out = (gl == 0) ? (unsigned)T : 0u;
-      } else {
+      } else if (STREAM) {
         if (kp.odd) {
           if (probe) td_stats_pass<LANES, true, true>(rd, g.nch, gl, kp, p4, f32, s_in, q_in, n_out);
           else td_stats_pass<LANES, true, false>(rd, g.nch, gl, kp, p4, f32, s_in, q_in, n_out);
@@ -532,9 +573,26 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
           if (probe) td_stats_pass<LANES, false, true>(rd, g.nch, gl, kp, p4, f32, s_in, q_in, n_out);
           else td_stats_pass<LANES, false, false>(rd, g.nch, gl, kp, p4, f32, s_in, q_in, n_out);
         }
+      } else {
+        // staged rows (at most 32 chunks per lane): sums of the outliers, subtracted below
+        unsigned s_out = 0;
+        unsigned long long q_out = 0;
+        if (kp.odd) {
+          if (probe) td_outlier_pass<LANES, true, true>(rd, g.nch, gl, kp, p4, f32, s_out, q_out, n_out);
+          else td_outlier_pass<LANES, true, false>(rd, g.nch, gl, kp, p4, f32, s_out, q_out, n_out);
+        } else {
+          if (probe) td_outlier_pass<LANES, false, true>(rd, g.nch, gl, kp, p4, f32, s_out, q_out, n_out);
+          else td_outlier_pass<LANES, false, false>(rd, g.nch, gl, kp, p4, f32, s_out, q_out, n_out);
+        }
+        s_in = s_out;  // (kept sums taken from the totals after the reduction)
+        q_in = q_out;
       }
       unsigned long long red[7] = {s_in, q_in, n_out, f32[0], f32[1], f32[2], f32[3]};
       grp_sum_row<LANES, 7>(red, scr);
+      if (!STREAM && !kp.all) {
+        red[0] = S0 - red[0];
+        red[1] = Q0 - red[1];
+      }
       if (!kp.all && klo > 0) red[2] -= npad;  // the zero padding bytes were counted as flagged
       if (probe) {
         unsigned long long f[4] = {red[3], red[4], red[5], red[6]};
@@ -711,6 +769,59 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
       }
     return fb;
   };
+  if (!STREAM && !random && same_align) {
+    // A chunk whose bytes all lie inside every keep interval is neither changed
+    // nor flagged.  The first sweep stores such chunks as they are (most of a
+    // row); each lane then takes the exact path on its own remaining chunks.
+    // The row's mask words are zeroed first (unless this pass ORs into an
+    // earlier round's flags) and the exact path ORs its bits in with
+    // reductions, so no flag word waits on another chunk.  (Rows here have
+    // at most 32 chunks per lane: warp rows 800 / 32, quarter-warp rows
+    // 200 / 8, CTA rows 6144 / 256.)
+    int ilo = klo, ihi = khi;  // the intersection of the iterations' keep intervals
+    if (!single)
+      for (int j = 0; j < I; j++) {
+        ilo = lo_i[j] > ilo ? lo_i[j] : ilo;
+        ihi = hi_i[j] < ihi ? hi_i[j] : ihi;
+      }
+    const ByteKeep ki = make_keep(ilo, ihi);
+    uint32_t slow = 0;  // bit r: chunk gl + r * LANES takes the exact path
+    for (int k = gl, r = 0; k < g.nch; k += LANES, r++) {
+      const uint4 w = st[k];
+      const uint32_t t = outside_fast(w.x, ki) | outside_fast(w.y, ki) | outside_fast(w.z, ki) | outside_fast(w.w, ki);
+      if (k == 0 || k == g.nch - 1 || (t & 0x80808080u)) {
+        slow |= 1u << r;
+        continue;
+      }
+      *reinterpret_cast<uint4*>(ob + 16 * k) = w;
+      if (mrowb && !P.td_mask_or) {
+        if (mb_align) *reinterpret_cast<uint4*>(mbb + 16 * k) = make_uint4(0u, 0u, 0u, 0u);
+        else store16_partial(mbb + 16 * k, make_uint4(0u, 0u, 0u, 0u), 0, 16);
+      }
+    }
+    if (mrow && !P.td_mask_or)
+      for (int wi = gl; wi < W32; wi += LANES) mrow[wi] = 0u;
+    grp_sync<LANES>();  // (orders the zeroed words before the reductions)
+    while (slow) {
+      const int r = __ffs(slow) - 1;
+      slow &= slow - 1;
+      const int k = gl + r * LANES;
+      uint32_t fb = final_chunk(k);
+      if (!mrow) continue;
+      if (k == 0 || k == g.nch - 1) {  // bits of padding bytes are not samples
+        const int clo = k == 0 ? g.head : 0, chi = k == g.nch - 1 ? g.tail : 16;
+        fb &= (chi >= 16 ? 0xFFFFu : ((1u << chi) - 1u)) & ~((1u << clo) - 1u);
+      }
+      if (!fb) continue;
+      // chunk byte b is row sample 16 k - head + b
+      const int s0 = 16 * k - g.head;
+      const unsigned long long v = s0 < 0 ? (unsigned long long)(fb >> (-s0)) : (unsigned long long)fb << (s0 & 31);
+      const int w0 = s0 < 0 ? 0 : s0 >> 5;
+      if ((uint32_t)v) atomicOr(mrow + w0, (uint32_t)v);
+      if ((uint32_t)(v >> 32)) atomicOr(mrow + w0 + 1, (uint32_t)(v >> 32));
+    }
+    return;
+  }
   for (int base = 0; base < g.nch; base += 2 * LANES) {
     const int ka = base + gl, kb = base + LANES + gl;
     uint32_t fa = 0, fbb = 0;
@@ -939,21 +1050,26 @@ __device__ unsigned bin_median(const BinView& bv, bool words, int lo, int hi) {
   return (unsigned)lo;
 }
 
-// Lower median of the 32 bytes held in w, searched in [lo, hi] (SAD counting).
+// f(p) = sum over the 32 bytes held in w of |x - p| (p <= 255)
+__device__ __forceinline__ unsigned sad32(const uint32_t (&w)[8], unsigned p) {
+  const uint32_t p4 = splat4(p);
+  unsigned a = 0, b = 0;
+#pragma unroll
+  for (int i = 0; i < 8; i += 2) {
+    a = sad4(w[i], p4, a);
+    b = sad4(w[i + 1], p4, b);
+  }
+  return a + b;
+}
+
+// Lower median m = min{p : #(x <= p) >= 16} of the 32 bytes held in w, known to
+// lie in [lo, hi]: bisection, with #(x <= p) = (32 + f(p+1) - f(p)) / 2 for
+// p <= 254, so #(x <= p) >= 16 iff f(p+1) >= f(p).  (Walking from the bin mean
+// instead took more steps: in a bin holding an outlier the mean is off.)
 __device__ __forceinline__ unsigned median32_regs(const uint32_t (&w)[8], int lo, int hi) {
   while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    const uint32_t pa = splat4((uint32_t)mid), pb = splat4((uint32_t)(mid + 1));
-    unsigned fa = 0, fb = 0, fa1 = 0, fb1 = 0;
-#pragma unroll
-    for (int i = 0; i < 8; i += 2) {
-      fa = sad4(w[i], pa, fa);
-      fb = sad4(w[i], pb, fb);
-      fa1 = sad4(w[i + 1], pa, fa1);
-      fb1 = sad4(w[i + 1], pb, fb1);
-    }
-    // #(x <= mid) = (32 + f(mid+1) - f(mid)) / 2 >= 16
-    if ((int)(fb + fb1) - (int)(fa + fa1) >= 0) hi = mid;
+    const int mid = (lo + hi) >> 1;  // mid < hi <= 255
+    if (sad32(w, (unsigned)mid + 1) >= sad32(w, (unsigned)mid)) hi = mid;
     else lo = mid + 1;
   }
   return (unsigned)lo;
@@ -1157,10 +1273,21 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
     __syncwarp();
 
     for (int it = 0; it < cut.iterations; it++) {
+      if (it > 0) {
+        // sum of D^2 per column from the bin sums as the last iteration left them
+        unsigned long long v = 0;
+        if (own)
+          for (int gi = sl; gi < NB; gi += LPC)
+            v += fd_contrib(gi == NB - 1 ? ml : mf, gi == NB - 1 ? (unsigned)Gl : (unsigned)G, L.Sg[tcol * NBP + gi],
+                            L.Qg[tcol * NBP + gi]);
+        for (int o = 1; o < LPC; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (own && sl == 0) L.V[tcol] = v;
+        __syncwarp();
+      }
       // per-column keep half-widths (8-lane candidate groups)
-      const unsigned long long Vt = own ? L.V[tcol] : 0ull;
-      const unsigned Af = max_keep_grp<8>(Vt, multF, own ? 255u * (unsigned)G : 0u, cut.k2);
-      const unsigned Al = (Gl == G) ? Af : max_keep_grp<8>(Vt, multL, own ? 255u * (unsigned)Gl : 0u, cut.k2);
+      const unsigned long long Ft = thr_floor(own ? L.V[tcol] : 0ull, cut.k2);
+      const unsigned Af = max_keep_grp<8>(Ft, multF, own ? 255u * (unsigned)G : 0u);
+      const unsigned Al = (Gl == G) ? Af : max_keep_grp<8>(Ft, multL, own ? 255u * (unsigned)Gl : 0u);
       if (own && sl == 0) {
         L.A[2 * tcol] = Af;
         L.A[2 * tcol + 1] = Al;
@@ -1220,7 +1347,6 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
         const bool lastbin = gi == NB - 1;
         const unsigned gsz = lastbin ? (unsigned)Gl : (unsigned)G;
         const unsigned bit = 1u << (t0 + t - t_item);
-        const unsigned long long mm = lastbin ? ml : mf;
         if (rnd) {
           // Random replacement: the bin's flags of this iteration go to fcur
           // first, so each draw tests the flag of the value it would copy
@@ -1269,7 +1395,6 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
           if (s_new != s_old || q_new != q_old) {
             L.Sg[t * NBP + gi] = s_new;
             L.Qg[t * NBP + gi] = q_new;
-            atomicAdd(&L.V[t], fd_contrib(mm, gsz, s_new, q_new) - fd_contrib(mm, gsz, s_old, q_old));
           }
           continue;
         }
@@ -1299,32 +1424,32 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
           }
           const ByteKeep kp = make_keep(lo, hi);
           const uint32_t r4 = splat4(r);
-          // sums of the replaced originals; the new sums follow from them
-          unsigned s_rep = 0, q_rep = 0, n_rep = 0;
+          uint32_t fbm = 0;  // flagged channels of the bin: bit j = channel 32 gi + j
 #pragma unroll
           for (int i = 0; i < 8; i++) {
             const uint32_t f = outside_exact(w[i], kp);
-            if (f) {
-              const uint32_t wm = (f >> 7) * 0xFFu;
-              const uint32_t xo = w[i] & wm;
-              s_rep = dp4a_u(xo, 0x01010101u, s_rep);
-              q_rep = dp4a_u(xo, xo, q_rep);
-              n_rep += __popc(f);
-              w[i] ^= (w[i] ^ r4) & wm;
-              uint32_t ff = f;
-              while (ff) {
-                const int byte = (__ffs(ff) - 1) >> 3;
-                ff &= ff - 1;
-                atomicOr(&L.fmask[gi * 32 + 4 * i + byte], bit);
-              }
-            }
+            w[i] = sel8(w[i], r4, wide8(f));
+            fbm |= (((f >> 7) * 0x01020408u) >> 24) << (4 * i);
           }
-          const unsigned s_new = s_old - s_rep + n_rep * r, q_new = q_old - q_rep + n_rep * r * r;
-          if (s_new != s_old || q_new != q_old) {  // some value changed (equal sums imply x == r)
+          if (fbm) {  // (the flag pass lists bins by a superset test: some have nothing to replace)
             store_bin32(L.tile, t, gi, pitch, w);
-            L.Sg[t * NBP + gi] = s_new;
-            L.Qg[t * NBP + gi] = q_new;
-            atomicAdd(&L.V[t], fd_contrib(mm, 32u, s_new, q_new) - fd_contrib(mm, 32u, s_old, q_old));
+            if (it + 1 < cut.iterations) {  // later iterations start from the new bin sums
+              unsigned s0 = 0, q0 = 0, s1 = 0, q1 = 0;
+#pragma unroll
+              for (int i = 0; i < 8; i += 2) {
+                s0 = dp4a_u(w[i], 0x01010101u, s0);
+                q0 = dp4a_u(w[i], w[i], q0);
+                s1 = dp4a_u(w[i + 1], 0x01010101u, s1);
+                q1 = dp4a_u(w[i + 1], w[i + 1], q1);
+              }
+              L.Sg[t * NBP + gi] = s0 + s1;
+              L.Qg[t * NBP + gi] = q0 + q1;
+            }
+            while (fbm) {
+              const int j = __ffs(fbm) - 1;
+              fbm &= fbm - 1;
+              atomicOr(&L.fmask[gi * 32 + j], bit);
+            }
           }
           continue;
         }
@@ -1396,7 +1521,6 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
         if (s_new != s_old || q_new != q_old) {
           L.Sg[t * NBP + gi] = s_new;
           L.Qg[t * NBP + gi] = q_new;
-          atomicAdd(&L.V[t], fd_contrib(mm, gsz, s_new, q_new) - fd_contrib(mm, gsz, s_old, q_old));
         }
       }
       __syncwarp();
@@ -1441,7 +1565,10 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
       const unsigned f = L.fmask[c] & valid;
       unsigned* wp = mb + (size_t)c * W32;
       if (P.mask_or) {
-        if (f) *wp = __ldcg(wp) | f;
+        // the word holds this beam's TDSC flags (published before this item
+        // started) and only this item writes its FDSC bits: a reduction that
+        // returns nothing, so the item does not wait for the word
+        if (f) atomicOr(wp, f);
       } else {
         *wp = f;
       }
