@@ -29,10 +29,8 @@ def test_profiles_exist_and_parse(bench):
         assert re.fullmatch(r"traffic: dram_bytes_per_launch=\d+ source_hash=[0-9a-f]{16}\n?", lines[0]), lines[0]
         for f in srcs:
             assert os.path.exists(os.path.join(ROOT, "paper_2001_03389_gb300", "csrc", f)), f
-        bench.WORKLOAD = w
-        t = bench.profiled_traffic()  # a float when the sources match the capture, else None
+        t = bench.profiled_traffic(w)  # a float when the sources match the capture, else None
         assert t is None or t > 0
-    bench.WORKLOAD = bench.ARTS
 
 
 def test_workloads_and_algorithmic_bytes(bench):
@@ -46,3 +44,6 @@ def test_workloads_and_algorithmic_bytes(bench):
     cfg = bench.config_json(arts, 1)
     assert cfg["workload"] == "arts_12x1536x12500_u8_bct_tdsc_then_fdsc"
     assert cfg["parallelism"] == "single" and bench.config_json(arts, 4)["global_batch"] == 48
+    f32 = synth.WORKLOADS[bench.FP32]
+    assert (f32["B"], f32["C"], f32["T"], f32["dtype"]) == (32, 4096, 8192, "f32")
+    assert (bench.F32_MARGIN, bench.F32_REL) == (1e-9, 1e-6)  # the float32 parity bar
