@@ -52,6 +52,7 @@ struct rfim_ctx {
   int smem_target = 113 * 1024;
   int fused_lag = 1;
   int order = 0;  // 0 = blocked (all TDSC iterations, then FDSC), 1 = interleaved rounds
+  int f32_records = 0;  // float32 fused launches: TDSC records its cuts and FDSC replays them
   long long stage_group_bytes = 32ll << 20;  // rfim_clean_host: bytes per staged group
   int stage_streams = 3;                     // rfim_clean_host: streams in the staging ring
   // graphs for rfim_clean_batch (each with its own counter blocks)
@@ -70,6 +71,11 @@ struct rfim_ctx {
   StreamService* stream = nullptr;
   // autotuner
   Tuner* tuner = nullptr;
+  // float32 fused launches: per-row TDSC cuts that FDSC items replay (grow-only;
+  // outgrown buffers stay allocated until destroy, as captured graphs hold them)
+  float* prog = nullptr;
+  size_t prog_cap = 0;
+  std::vector<float*> prog_retired;
   std::mutex mu;
 };
 
@@ -232,6 +238,7 @@ struct Plan {
   int mask_kind = 0;
   int max_T = 1;
   rfim_dtype dtype = RFIM_U8;
+  bool prog = false;  // the jobs carry TDSC cut records (float32; used by fused launches only)
 };
 
 int pick_ws_opt(int tile_samples, int C, int nb, int pitch, int budget, bool rnd) {
@@ -419,8 +426,11 @@ void fill_params(rfim_ctx* ctx, const Plan& pl, int j0, int j1, int mode, Params
     }
     p.td_mask_or = 1;
   }
+  if (!(pl.prog && mode == 2))
+    for (int j = 0; j < p.n_jobs; j++) p.jobs[j].prog = nullptr;
   p.mask_kind = pl.mask_kind;
-  p.fd_reads_out = (mode == 2 || mode == 3) ? 1 : 0;
+  // fused float32 with cut records: FDSC reads the input and replays TDSC's cuts
+  p.fd_reads_out = (mode == 2 && !(pl.prog && p.n_jobs > 0)) || mode == 3 ? 1 : 0;
   p.wait_tdsc = mode == 2 ? 1 : 0;
   p.mask_or = (mode == 2 || mode == 3) ? 1 : 0;
   p.withhold_job = (ctx->withhold && mode == 2) ? 0 : -1;
@@ -542,6 +552,45 @@ rfim_status make_plan(rfim_ctx* ctx, const rfim_block* blocks, int n, const rfim
     }
   }
   for (int i = 0; i < n; i++) add_block_jobs(ctx, pl, &blocks[i]);
+  // float32 with both methods, non-random TDSC and a bit mask: record TDSC's
+  // cuts per row (the fused launch then writes each value once, from FDSC)
+  bool records = ctx->f32_records && pl.dtype == RFIM_F32 && pl.td.on && pl.fd.on &&
+                 pl.td.rep != RFIM_REPLACE_RANDOM && pl.mask_kind == RFIM_MASK_BITS;
+  // the FDSC tile then also holds one mask word per channel: the widest sub-slab that still fits
+  auto records_ws = [&](const Job& J) {
+    const bool rnd = pl.fd.rep == RFIM_REPLACE_RANDOM;
+    const int budget = std::min(MAX_SMEM_PER_CTA, std::max(ctx->smem_target, fd32_smem_bytes(1, J.C, J.nb, rnd, true)));
+    for (int cand : {8, 4, 2, 1})
+      if ((ctx->tile_samples == 0 || cand <= ctx->tile_samples) && fd32_smem_bytes(cand, J.C, J.nb, rnd, true) <= budget)
+        return cand;
+    return 0;
+  };
+  for (const Job& J : pl.jobs)
+    if (records && records_ws(J) == 0) records = false;
+  if (records) {
+    for (Job& J : pl.jobs) {
+      J.ws = records_ws(J);
+      J.fd_items = (J.T + J.ws - 1) / J.ws;
+    }
+    size_t rows = 0;
+    for (const Job& J : pl.jobs) rows += (size_t)J.C;
+    const size_t bytes = rows * (size_t)pl.td.it * PROG_FLOATS * sizeof(float);
+    if (bytes > ctx->prog_cap) {
+      float* p = nullptr;
+      const size_t cap = std::max(bytes, 2 * ctx->prog_cap);
+      cudaError_t e = cudaMalloc(&p, cap);
+      if (e != cudaSuccess) return fail(ctx, RFIM_ERR_OOM, "TDSC cut records: %s", cudaGetErrorString(e));
+      if (ctx->prog) ctx->prog_retired.push_back(ctx->prog);
+      ctx->prog = p;
+      ctx->prog_cap = cap;
+    }
+    size_t off = 0;
+    for (Job& J : pl.jobs) {
+      J.prog = ctx->prog + off;
+      off += (size_t)J.C * pl.td.it * PROG_FLOATS;
+    }
+    pl.prog = true;
+  }
   return RFIM_OK;
 }
 
@@ -594,6 +643,8 @@ rfim_status rfim_destroy(rfim_ctx* ctx) {
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   cudaFree(ctx->btc_buf);
   cudaFree(ctx->btc_mask);
+  cudaFree(ctx->prog);
+  for (float* p : ctx->prog_retired) cudaFree(p);
   if (ctx->stager) stager_destroy(ctx->stager);
   if (ctx->tuner) tuner_destroy(ctx->tuner);
   cudaFree(ctx->d_counters);
@@ -621,6 +672,9 @@ rfim_status rfim_set_option(rfim_ctx* ctx, const char* key, long long value) {
   } else if (k == "stage_streams") {
     if (value < 1 || value > 4) return fail(ctx, RFIM_ERR_ARG, "stage_streams must be 1..4");
     ctx->stage_streams = (int)value;
+  } else if (k == "f32_records") {
+    if (value != 0 && value != 1) return fail(ctx, RFIM_ERR_ARG, "f32_records must be 0 or 1");
+    ctx->f32_records = (int)value;
   } else if (k == "order") {
     if (value != 0 && value != 1) return fail(ctx, RFIM_ERR_ARG, "order must be 0 (blocked) or 1 (interleaved)");
     ctx->order = (int)value;
@@ -753,8 +807,8 @@ rfim_status rfim_clean_batch(rfim_ctx* ctx, const rfim_block* blocks, int n, con
   unsigned char* kp = key.data() + sizeof(Job) * pl.jobs.size();
   memcpy(kp, &pl.td, sizeof(CutNorm));
   memcpy(kp + 64, &pl.fd, sizeof(CutNorm));
-  int opts[9] = {pl.mask_kind, ctx->schedule, ctx->ctas_per_sm, ctx->fused_lag, ctx->withhold, (int)ctx->spin_limit_us,
-                 ctx->tile_samples, ctx->smem_target, ctx->order};
+  int opts[10] = {pl.mask_kind, ctx->schedule, ctx->ctas_per_sm, ctx->fused_lag, ctx->withhold,
+                  (int)ctx->spin_limit_us, ctx->tile_samples, ctx->smem_target, ctx->order, ctx->f32_records};
   memcpy(kp + 128, opts, sizeof opts);
   auto it = ctx->graphs.find(key);
   if (it == ctx->graphs.end()) {

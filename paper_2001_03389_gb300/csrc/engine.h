@@ -51,7 +51,14 @@ struct Job {
   int beam;         // index of the beam within its block (keys the random-replacement draws)
   double* stats;    // or null: per row, the sum and the sum of squares of the input row ([2 * row], [2 * row + 1]),
                     // written by the first TDSC iteration (the streaming service's per-beam state)
+  float* prog;      // or null (float32, fused launches with a bit mask, option "f32_records"): per row and
+                    // TDSC iteration, the iteration's cut and replacement value (PROG_FLOATS floats); TDSC
+                    // rows record these and their mask bits instead of writing the row, and FDSC items load
+                    // the input and replay the cuts on the samples whose TDSC bit is set
 };
+// per row and iteration: {mu_f, lo_f, hi_f, r} (the float32 decision and the
+// replacement), then {mu_lo, thr_hi, thr_lo, 0} (read only inside the band)
+constexpr int PROG_FLOATS = 8;
 
 // A run of consecutive queue items: `count` items of one kind for one job.
 struct Seg {
@@ -156,11 +163,12 @@ __host__ __device__ inline int td32_smem_bytes(int T) {
   const int nch = (T + 6) / 4 + 1;
   return 16 * nch + align16i(nch) + 4 * TD32_LIST;
 }
-// rnd: random replacement adds one flag word per channel
-__host__ __device__ inline int fd32_smem_bytes(int ws, int C, int nb, bool rnd = false) {
+// rnd: random replacement adds one flag word per channel; prog: one word per
+// channel holds the TDSC mask word of the sub-slab (replay of TDSC's cut records)
+__host__ __device__ inline int fd32_smem_bytes(int ws, int C, int nb, bool rnd = false, bool prog = false) {
   const int U = ws * nb;
   return align16i(ws * C * 4) + align16i(C * 4) + align16i(U * 8) * 2 + align16i(U * 4) + align16i(ws * 8) +
-         align16i(ws * 4) * 2 + (rnd ? align16i(C * 4) : 0);
+         align16i(ws * 4) * 2 + (rnd ? align16i(C * 4) : 0) + (prog ? align16i(C * 4) : 0);
 }
 int engine_smem_f32(const Params& p);
 void* engine_kernel_f32(const Params& p);

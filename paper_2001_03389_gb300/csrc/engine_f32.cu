@@ -189,6 +189,42 @@ __device__ __forceinline__ Cut32 make_cut32(FF mu, FF thr) {
   return c;
 }
 
+// One TDSC iteration of a row as FDSC items replay it: the cut and the value
+// that replaces the samples it flags.
+__device__ __forceinline__ void store_prog(float* e, const Cut32& c, float r) {
+  reinterpret_cast<float4*>(e)[0] = make_float4(c.mu_f, c.lo_f, c.hi_f, r);
+  reinterpret_cast<float4*>(e)[1] = make_float4(c.mu_lo, c.thr_hi, c.thr_lo, 0.f);
+}
+
+// The value TDSC left in a sample of the input value y that one of its
+// iterations flagged: the row's iterations replayed in order, y <- r_i where
+// cut i flags y.  f: the first records' fast fields, loaded ahead.
+__device__ __forceinline__ float replay_tdsc(float y, const float4* pe, const float4 (&f)[3], int I) {
+#pragma unroll
+  for (int i = 0; i < 3; i++) {
+    if (i < I) {
+      const float a = fabsf(__fsub_rn(y, f[i].x));
+      bool fl = a > f[i].z;
+      if (!fl && a > f[i].y) {
+        const float4 sl = __ldcg(pe + 2 * i + 1);
+        fl = flag64(y, f[i].x, sl.x, sl.y, sl.z);
+      }
+      if (fl) y = f[i].w;
+    }
+  }
+  for (int i = 3; i < I; i++) {
+    const float4 q = __ldcg(pe + 2 * i);
+    const float a = fabsf(__fsub_rn(y, q.x));
+    bool fl = a > q.z;
+    if (!fl && a > q.y) {
+      const float4 sl = __ldcg(pe + 2 * i + 1);
+      fl = flag64(y, q.x, sl.x, sl.y, sl.z);
+    }
+    if (fl) y = q.w;
+  }
+  return y;
+}
+
 // Total order of floats as unsigned keys (-0 before +0).
 __device__ __forceinline__ unsigned fkey(float f) {
   const unsigned b = __float_as_uint(f);
@@ -412,6 +448,7 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
     }
     const Cut32 c = make_cut32(mu, ff_mul(kff, ff_sqrt(var)));
     const float r = cut.replace == REP_MEDIAN ? row_median_f32<GN>(st, nch, head, tail, T, red, t, h) : c.mu_f;
+    if (J.prog && t == 0) store_prog(J.prog + ((size_t)row * I + it) * PROG_FLOATS, c, r);
 
     // decide and replace; the replaced values go to a list for the statistics
     // update (its length counter was zeroed before the last barrier)
@@ -508,10 +545,10 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
   }
   gsync<GN>(h);
 
-  // ---- write the row and its mask
+  // ---- write the row (unless FDSC replays the recorded cuts) and its mask
   const bool same_align = (((uintptr_t)rout) & 15) == (((uintptr_t)rin) & 15);
   float* ob = rout - head;
-  for (int k = t; k < nch; k += GN) {
+  for (int k = t; k < (J.prog ? 0 : nch); k += GN) {
     const float4 v = st[k];
     const int lo = k == 0 ? head : 0, hi = k == nch - 1 ? tail : 4;
     if (same_align && lo == 0 && hi == 4) {
@@ -632,6 +669,7 @@ __device__ __noinline__ void tdsc_row_f32_long(const Params& P, const Job& J, in
     if (t == 0) {
       s_cut[it] = c;
       s_rep[it] = r;
+      if (J.prog) store_prog(J.prog + ((size_t)row * I + it) * PROG_FLOATS, c, r);
     }
     gsync<NT>(0);
   }
@@ -645,7 +683,7 @@ __device__ __noinline__ void tdsc_row_f32_long(const Params& P, const Job& J, in
     bool fl = false;
     if (i < T) {
       const float y = cur(i, I, fl);  // (read before the write: out may be in)
-      rout[i] = y;
+      if (!J.prog) rout[i] = y;
       if (mb) mb[i] = P.td_mask_or ? (unsigned char)(mb[i] | (fl ? 1u : 0u)) : (unsigned char)(fl ? 1u : 0u);
     }
     const unsigned bits = __ballot_sync(0xffffffffu, fl);
@@ -666,6 +704,7 @@ __device__ __noinline__ void tdsc_row_f32_long(const Params& P, const Job& J, in
 struct Fd32Layout {
   float* tile;    // C x ws
   unsigned* fm;   // C: FDSC flag bits of the item (bit = t - t_item)
+  unsigned* tm;   // C: the TDSC mask word of the sub-slab (replay of TDSC's cut records)
   float2* um;     // units: bin mean as float-float
   float2* uv;     // units: sum of squared deviations as float-float
   float* uq;      // units: sum of squares (cancellation check)
@@ -675,7 +714,7 @@ struct Fd32Layout {
   unsigned* fcur; // C (random replacement only): flags of the iteration in progress (bit = t - t0)
 };
 
-__device__ __forceinline__ Fd32Layout fd32_layout(unsigned char* smem, int ws, int C, int nb) {
+__device__ __forceinline__ Fd32Layout fd32_layout(unsigned char* smem, int ws, int C, int nb, bool rnd) {
   const int U = ws * nb;
   Fd32Layout L;
   unsigned char* p = smem;
@@ -696,6 +735,8 @@ __device__ __forceinline__ Fd32Layout fd32_layout(unsigned char* smem, int ws, i
   L.thr_hi = reinterpret_cast<float*>(p);
   p += align16i(ws * 4);
   L.fcur = reinterpret_cast<unsigned*>(p);
+  p += rnd ? align16i(C * 4) : 0;
+  L.tm = reinterpret_cast<unsigned*>(p);
   return L;
 }
 
@@ -721,13 +762,13 @@ __device__ void fdsc_item_f32(const Params& P, const Job& J, int item, unsigned 
   const int t_end = min(t_item + Ws, T);
   const float* src = static_cast<const float*>(P.fd_reads_out ? J.out : J.in);
   float* dst = static_cast<float*>(J.out);
-  const Fd32Layout L = fd32_layout(smem, Ws, C, NB);
+  const bool rnd = RND && cut.replace == REP_RANDOM;
+  const Fd32Layout L = fd32_layout(smem, Ws, C, NB, rnd);
   const FF kff{cut.k_hi, cut.k_lo};
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool vec = ((((uintptr_t)src) | ((uintptr_t)dst)) & 15) == 0 && (T & 3) == 0;
   const double rC = 1.0 / (double)C;
 
-  const bool rnd = RND && cut.replace == REP_RANDOM;
   for (int c = threadIdx.x; c < C; c += NT) L.fm[c] = 0;
   if (rnd)
     for (int c = threadIdx.x; c < C; c += NT) L.fcur[c] = 0;  // each unit clears its own bits after use
@@ -736,6 +777,8 @@ __device__ void fdsc_item_f32(const Params& P, const Job& J, int item, unsigned 
     const int w = min(Ws, t_end - t0);
     // ---- load the sub-slab: thread per channel; 16-byte asynchronous copies
     //      (all in flight at once, L1 bypassed) where rows allow them
+    const int W32 = (T + 31) >> 5;
+    const unsigned* mw = J.prog ? static_cast<const unsigned*>(J.mask) + (t0 >> 5) : nullptr;
     if (vec && w == Ws && Ws >= 4) {
       for (int c = threadIdx.x; c < C; c += NT) {
         const float* a = src + (size_t)c * T + t0;
@@ -744,6 +787,10 @@ __device__ void fdsc_item_f32(const Params& P, const Job& J, int item, unsigned 
           const unsigned sdst = (unsigned)__cvta_generic_to_shared(d + j);
           asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sdst), "l"(a + j) : "memory");
         }
+        if (mw) {  // with the tile: the TDSC mask word of this channel's sub-slab
+          const unsigned sdst = (unsigned)__cvta_generic_to_shared(L.tm + c);
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sdst), "l"(mw + (size_t)c * W32) : "memory");
+        }
       }
       asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
     } else {
@@ -751,6 +798,44 @@ __device__ void fdsc_item_f32(const Params& P, const Job& J, int item, unsigned 
         const float* a = src + (size_t)c * T + t0;
         float* d = L.tile + c * Ws;
         for (int j = 0; j < w; j++) d[j] = a[j];
+        if (mw) L.tm[c] = __ldcg(mw + (size_t)c * W32);
+      }
+    }
+    if (J.prog) {
+      // The tile holds the input.  A sample whose TDSC bit is set takes the
+      // value TDSC gave it (replay_tdsc).  The TDSC rows of this beam are
+      // published (the item waited for them); bits [t0 & 31, +w) of each word
+      // are this item's own, so no FDSC bit is there yet.  Two channels of a
+      // thread at a time load their records together.
+      __syncthreads();  // (the tile and the mask words are complete)
+      const int I = P.td.iterations, sh = t0 & 31;
+      const unsigned wm = w >= 32 ? 0xFFFFFFFFu : (1u << w) - 1u;
+      const float4* prog4 = reinterpret_cast<const float4*>(J.prog);
+      for (int cA = threadIdx.x; cA < C; cA += 2 * NT) {
+        const int cB = cA + NT;
+        unsigned bA = (L.tm[cA] >> sh) & wm;
+        unsigned bB = cB < C ? (L.tm[cB] >> sh) & wm : 0u;
+        if (!(bA | bB)) continue;
+        const float4* pA = prog4 + (size_t)cA * I * 2;
+        const float4* pB = prog4 + (size_t)(bB ? cB : cA) * I * 2;
+        float4 fA[3], fB[3];
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+          fA[i] = (bA && i < I) ? __ldcg(pA + 2 * i) : make_float4(0.f, 0.f, 0.f, 0.f);
+          fB[i] = (bB && i < I) ? __ldcg(pB + 2 * i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        float* dA = L.tile + cA * Ws;
+        while (bA) {
+          const int j = __ffs(bA) - 1;
+          bA &= bA - 1;
+          dA[j] = replay_tdsc(dA[j], pA, fA, I);
+        }
+        float* dB = L.tile + (size_t)(bB ? cB : cA) * Ws;
+        while (bB) {
+          const int j = __ffs(bB) - 1;
+          bB &= bB - 1;
+          dB[j] = replay_tdsc(dB[j], pB, fB, I);
+        }
       }
     }
     __syncthreads();
@@ -1079,7 +1164,7 @@ int engine_smem_f32(const Params& p) {
       s = s > td ? s : td;
     }
     if (p.fd.iterations > 0) {
-      const int fd = fd32_smem_bytes(J.ws, J.C, J.nb, p.fd.replace == REP_RANDOM);
+      const int fd = fd32_smem_bytes(J.ws, J.C, J.nb, p.fd.replace == REP_RANDOM, J.prog != nullptr);
       s = s > fd ? s : fd;
     }
   }

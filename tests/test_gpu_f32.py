@@ -271,6 +271,26 @@ def test_fp32_workload_full_launch_sampled(oracle, ctx):
     assert nd <= 4
 
 
+@pytest.mark.parametrize("rep", ["mean", "median"])
+def test_f32_cut_records(oracle, ctx, rep):
+    # Option f32_records: fused TDSC rows record their cuts instead of writing
+    # the row, and FDSC items replay them on the input.  The fused launch must
+    # equal TDSC then FDSC launched separately (bit for bit), in place and
+    # misaligned too, with rows beyond the stage among them.
+    rng = np.random.default_rng(3)
+    try:
+        ctx.set_option("f32_records", 1)
+        for C, T in [(64, 2048), (130, 333), (3, 52003)]:
+            x = chi2_block(rng, 2, C, T)
+            td = dict(k=2.5, iterations=3, replace=rep)
+            fd = dict(k=2.5, iterations=2, replace="mean", bin=min(32, C))
+            check_f32(oracle, ctx, x, td=td, fd=fd)
+            check_f32(oracle, ctx, x, td=td, fd=fd, in_place=True, in_off=4)
+            check_f32(oracle, ctx, x, td=dict(td, iterations=5), fd=fd, in_off=8, out_off=12)
+    finally:
+        ctx.set_option("f32_records", 0)
+
+
 def test_f32_tile_widths(oracle, ctx):
     rng = np.random.default_rng(21)
     x = chi2_block(rng, 2, 300, 203)
