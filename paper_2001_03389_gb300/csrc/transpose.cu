@@ -33,6 +33,38 @@ __global__ void __launch_bounds__(256) k_transpose(const E* __restrict__ in, E* 
   }
 }
 
+// Bytes, when rows and cols are multiples of 4 and the planes 4-byte aligned:
+// 64 x 64 tiles.  A thread loads a 4 x 4 block as four row words (16 lanes
+// read 64 contiguous bytes of a row), transposes it in registers (byte
+// permutes) and leaves the four column words in shared memory, from where 16
+// lanes store 64 contiguous bytes of an output row.
+__global__ void __launch_bounds__(256) k_transpose_u8x4(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
+                                                        int rows, int cols) {
+  __shared__ uint32_t tile[64][17];  // [column within the tile][row quad]; +1 word against bank conflicts
+  const size_t plane = (size_t)rows * cols;
+  const uint8_t* src = in + (size_t)blockIdx.z * plane;
+  uint8_t* dst = out + (size_t)blockIdx.z * plane;
+  const int c0 = blockIdx.x * 64, r0 = blockIdx.y * 64;
+  const int cq = threadIdx.x & 15, rq = threadIdx.x >> 4;
+  const int c = c0 + 4 * cq;
+  uint32_t w[4];
+#pragma unroll
+  for (int j = 0; j < 4; j++) {
+    const int r = r0 + 4 * rq + j;
+    w[j] = (r < rows && c < cols) ? __ldg(reinterpret_cast<const uint32_t*>(src + (size_t)r * cols + c)) : 0u;
+  }
+  transpose4x4(w[0], w[1], w[2], w[3]);  // w[i]: column c + i, rows r0 + 4 rq .. + 3
+#pragma unroll
+  for (int i = 0; i < 4; i++) tile[4 * cq + i][rq] = w[i];
+  __syncthreads();
+  const int wq = threadIdx.x & 15, r = r0 + 4 * wq;
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    const int cc = (threadIdx.x >> 4) + 16 * k, oc = c0 + cc;
+    if (oc < cols && r < rows) *reinterpret_cast<uint32_t*>(dst + (size_t)oc * rows + r) = tile[cc][wq];
+  }
+}
+
 // Bit masks: in is the BCT mask of a beam (rows c, words of 32 samples), out
 // the BTC mask (rows t, words of 32 channels).  One warp per 32 x 32 bit block:
 // lane i holds channel c0 + i's word; the ballot over bit j is sample t0 + j's word.
@@ -47,18 +79,23 @@ __global__ void __launch_bounds__(256) k_transpose_bits(const uint32_t* __restri
   uint32_t* dst = out + (size_t)blockIdx.y * T * WC;
   const int c = wc * 32 + lane;
   const uint32_t w = c < C ? src[(size_t)c * WT + wt] : 0u;
-#pragma unroll 4
+  uint32_t mine = 0;  // lane j keeps sample t0 + j's word; the 32 stores then go out together
+#pragma unroll 8
   for (int j = 0; j < 32; j++) {
     const uint32_t col = __ballot_sync(0xffffffffu, (w >> j) & 1u);
-    const int t = wt * 32 + j;
-    if (lane == 0 && t < T) dst[(size_t)t * WC + wc] = col;
+    if (lane == j) mine = col;
   }
+  const int t = wt * 32 + lane;
+  if (t < T) dst[(size_t)t * WC + wc] = mine;
 }
 
 int launch_transpose(const void* in, void* out, int batch, int rows, int cols, int esize, void* stream) {
   dim3 grid((cols + 31) / 32, (rows + 31) / 32, batch);
   cudaStream_t st = (cudaStream_t)stream;
-  if (esize == 1)
+  if (esize == 1 && (rows & 3) == 0 && (cols & 3) == 0 && (((uintptr_t)in | (uintptr_t)out) & 3) == 0) {
+    dim3 g4((cols + 63) / 64, (rows + 63) / 64, batch);
+    k_transpose_u8x4<<<g4, 256, 0, st>>>((const uint8_t*)in, (uint8_t*)out, rows, cols);
+  } else if (esize == 1)
     k_transpose<uint8_t><<<grid, 256, 0, st>>>((const uint8_t*)in, (uint8_t*)out, rows, cols);
   else
     k_transpose<float><<<grid, 256, 0, st>>>((const float*)in, (float*)out, rows, cols);
