@@ -47,9 +47,12 @@
  * reaches 2^53 (RFIM_ERR_RANGE beyond); rows longer than 98,273 samples do not
  * fit the on-chip stage and are read from memory in every pass (slower, same
  * results).  float32 TDSC rows longer than 52,000 samples are read from memory
- * in every pass, replaying the earlier iterations' decisions.  Random
- * replacement needs the staged row: uint8 rows of at most 78,609 samples,
- * float32 rows of at most 52,000 (RFIM_ERR_ARG beyond).
+ * in every pass, replaying the earlier iterations' decisions.  With random
+ * replacement, uint8 rows longer than 78,609 samples and float32 rows longer
+ * than 52,000 are not staged either: iteration 0 writes the output row and
+ * later iterations rewrite it in place, with the flags kept as bitmaps in
+ * shared memory (uint8 up to the 372,181 bound above, float32 up to 921,600
+ * samples; RFIM_ERR_ARG beyond).
  *
  * Conventions for every call below:
  *   - Pointers inside rfim_block are DEVICE pointers owned by the caller,
@@ -112,8 +115,8 @@ typedef enum { RFIM_LAYOUT_BCT = 0, RFIM_LAYOUT_BTC = 1 } rfim_layout;
  * channel), beam = the beam's index within its block, it = the iteration; the
  * first draw that hits an unflagged sample wins, and after 32 misses the
  * sample keeps its value.  In the interleaved order ("order" option) round r
- * is iteration r of each method and draws with it = r.  TDSC rows with RANDOM
- * hold at most 78,609 samples (uint8) or 52,000 (float32).
+ * is iteration r of each method and draws with it = r.  Row lengths with
+ * RANDOM: see "Row lengths" above.
  */
 typedef enum { RFIM_REPLACE_MEAN = 0, RFIM_REPLACE_MEDIAN = 1, RFIM_REPLACE_RANDOM = 2 } rfim_replace;
 
@@ -180,6 +183,10 @@ rfim_status rfim_destroy(rfim_ctx* ctx);
  *   "stage_group_bytes"  rfim_clean_host: bytes of beams copied and cleaned per
  *                     group (default 32 MB; at least one beam per group);
  *   "stage_streams"   rfim_clean_host: CUDA streams the groups rotate over (1..4, default 3);
+ *   "f32_records"     float32 fused launches: 1 = TDSC writes per-row cut records
+ *                     (band and replacement value per iteration) instead of its
+ *                     output, and FDSC replays them as it loads each tile (same
+ *                     results; less traffic, more arithmetic); 0 = off (default);
  *   "order"           order of the methods in rfim_clean and rfim_clean_batch:
  *                     0 = blocked (all TDSC iterations on every row, then all
  *                     FDSC iterations on every column; default), 1 = interleaved
@@ -188,7 +195,15 @@ rfim_status rfim_destroy(rfim_ctx* ctx);
  *   "ctas_per_sm"     persistent-kernel CTAs per SM (0 = occupancy maximum);
  *   "withhold_tdsc_done"  test hook: 1 makes the fused kernel never publish the
  *                     TDSC completion of beam 0, so its FDSC items time out
- *                     (RFIM_ERR_TIMEOUT via rfim_device_status).
+ *                     (RFIM_ERR_TIMEOUT via rfim_device_status);
+ *   "fail_alloc_after"  test hook: n >= 0 lets the context's next n device or
+ *                     pinned-host allocations succeed and refuses every later
+ *                     one (the call returns RFIM_ERR_OOM, nothing is allocated,
+ *                     and the context stays usable) until the option is set
+ *                     to -1 (off, the default).  It covers every allocation
+ *                     after rfim_create: BTC scratch, graph counters, float32
+ *                     cut records, host staging, autotuner scratch and the
+ *                     streaming slots.
  */
 rfim_status rfim_set_option(rfim_ctx* ctx, const char* key, long long value);
 

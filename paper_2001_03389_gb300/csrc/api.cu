@@ -54,6 +54,8 @@ struct rfim_ctx {
   int order = 0;  // 0 = blocked (all TDSC iterations, then FDSC), 1 = interleaved rounds
   int f32_records = 0;  // float32 fused launches: TDSC records its cuts and FDSC replays them
   long long stage_group_bytes = 32ll << 20;  // rfim_clean_host: bytes per staged group
+  // test hook: allocations left before every later one fails (-1 = off)
+  long long fail_alloc_after = -1;
   int stage_streams = 3;                     // rfim_clean_host: streams in the staging ring
   // graphs for rfim_clean_batch (each with its own counter blocks)
   std::map<std::vector<unsigned char>, std::pair<cudaGraphExec_t, unsigned*>> graphs;
@@ -208,9 +210,10 @@ rfim_status check_impl(rfim_ctx* ctx, const rfim_block* b, const CutNorm& td, co
   if (b->layout != RFIM_LAYOUT_BCT)
     return fail(ctx, RFIM_ERR_ARG, "BTC blocks are cleaned through a context's BCT scratch (not here)");
   if (b->dtype == RFIM_F32) {
-    if (td.on && td.rep == RFIM_REPLACE_RANDOM && b->samples > TD32_MAX_T)
+    if (td.on && td.rep == RFIM_REPLACE_RANDOM && b->samples > TD32_MAX_T &&
+        td32_rnd_long_bytes(b->samples) > MAX_SMEM_PER_CTA)
       return fail(ctx, RFIM_ERR_ARG, "float32 TDSC with random replacement: rows longer than %d samples are not "
-                  "supported", TD32_MAX_T);
+                  "supported", (MAX_SMEM_PER_CTA / 8) * 32);
     if (fd.on) {
       const int C = b->channels, nb = (C + fd.bin - 1) / fd.bin;
       if (fd32_smem_bytes(1, C, nb, fd.rep == RFIM_REPLACE_RANDOM) > MAX_SMEM_PER_CTA)
@@ -221,8 +224,7 @@ rfim_status check_impl(rfim_ctx* ctx, const rfim_block* b, const CutNorm& td, co
   if (td.on && td_row_mode(b->samples) < 0)
     return fail(ctx, RFIM_ERR_RANGE, "TDSC rows longer than %lld samples are not available", TD_MAX_T);
   if (td.on && td.rep == RFIM_REPLACE_RANDOM && td_random_row_mode(b->samples) < 0)
-    return fail(ctx, RFIM_ERR_ARG, "uint8 TDSC with random replacement: rows longer than 78609 samples are not "
-                "supported");
+    return fail(ctx, RFIM_ERR_ARG, "uint8 TDSC with random replacement: the row's flag bitmaps do not fit");
   if (fd.on) {
     // the smallest FDSC tile (8 samples x all channels) must fit one CTA's shared memory
     const int C = b->channels, nb = (C + fd.bin - 1) / fd.bin;
@@ -303,7 +305,8 @@ Job make_job(const rfim_block* b, int j, const CutNorm& fd, int tile_samples, in
 // uint8 TDSC with random replacement: warp or CTA rows by the stage the flags need
 void random_row_mode(Job& J, const rfim_block* b, const CutNorm& td) {
   if (b->dtype != RFIM_U8 || !td.on || td.rep != RFIM_REPLACE_RANDOM) return;
-  J.td_mode = td_random_row_mode(b->samples) == 1 ? 1 : 0;
+  const int m = td_random_row_mode(b->samples);
+  J.td_mode = m < 0 ? 0 : m;  // (-1 is refused by check_impl)
   J.td_items = J.td_mode == 0 ? (b->channels + TD_ROWS_PER_ITEM - 1) / TD_ROWS_PER_ITEM : b->channels;
 }
 
@@ -578,7 +581,7 @@ rfim_status make_plan(rfim_ctx* ctx, const rfim_block* blocks, int n, const rfim
     if (bytes > ctx->prog_cap) {
       float* p = nullptr;
       const size_t cap = std::max(bytes, 2 * ctx->prog_cap);
-      cudaError_t e = cudaMalloc(&p, cap);
+      cudaError_t e = ctx_malloc(ctx, reinterpret_cast<void**>(&p), cap);
       if (e != cudaSuccess) return fail(ctx, RFIM_ERR_OOM, "TDSC cut records: %s", cudaGetErrorString(e));
       if (ctx->prog) ctx->prog_retired.push_back(ctx->prog);
       ctx->prog = p;
@@ -686,6 +689,8 @@ rfim_status rfim_set_option(rfim_ctx* ctx, const char* key, long long value) {
   } else if (k == "smem_target") {
     if (value < 16384 || value > MAX_SMEM_PER_CTA) return fail(ctx, RFIM_ERR_ARG, "smem_target out of range");
     ctx->smem_target = (int)value;
+  } else if (k == "fail_alloc_after") {
+    ctx->fail_alloc_after = value < 0 ? -1 : value;
   } else if (k == "fused_lag") {
     if (value < 0 || value > 8) return fail(ctx, RFIM_ERR_ARG, "fused_lag must be in 0..8");
     ctx->fused_lag = (int)value;
@@ -719,7 +724,7 @@ static rfim_status run_btc(rfim_ctx* ctx, const rfim_block* blocks, int n, const
       cudaFree(ctx->btc_buf);
       ctx->btc_buf = nullptr;
       ctx->btc_cap = 0;
-      if (cudaMalloc(&ctx->btc_buf, N * es) != cudaSuccess) {
+      if (ctx_malloc(ctx, &ctx->btc_buf, N * es) != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx, RFIM_ERR_OOM, "BTC scratch of %zu bytes", N * es);
       }
@@ -729,7 +734,7 @@ static rfim_status run_btc(rfim_ctx* ctx, const rfim_block* blocks, int n, const
       cudaFree(ctx->btc_mask);
       ctx->btc_mask = nullptr;
       ctx->btc_mask_cap = 0;
-      if (cudaMalloc(&ctx->btc_mask, mbytes) != cudaSuccess) {
+      if (ctx_malloc(ctx, &ctx->btc_mask, mbytes) != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx, RFIM_ERR_OOM, "BTC mask scratch of %zu bytes", mbytes);
       }
@@ -820,7 +825,7 @@ rfim_status rfim_clean_batch(rfim_ctx* ctx, const rfim_block* blocks, int n, con
     const int rounds = ctx->order == 1 ? std::max(1, std::max(pl.td.it, pl.fd.it)) : 1;
     const int launches = 2 * rounds * (((int)pl.jobs.size() + MAX_JOBS - 1) / MAX_JOBS);
     unsigned* gc = nullptr;
-    cudaError_t e = cudaMalloc(&gc, sizeof(unsigned) * COUNTER_STRIDE * launches);
+    cudaError_t e = ctx_malloc(ctx, reinterpret_cast<void**>(&gc), sizeof(unsigned) * COUNTER_STRIDE * launches);
     if (e != cudaSuccess) return fail(ctx, RFIM_ERR_OOM, "graph counters: %s", cudaGetErrorString(e));
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal);
@@ -929,6 +934,18 @@ rfim_status ctx_clean_async(rfim_ctx* ctx, const rfim_block* blocks, int n, cons
 int ctx_device(rfim_ctx* ctx) { return ctx->device; }
 size_t ctx_hbm_budget(rfim_ctx* ctx) { return ctx->hbm_budget; }
 void ctx_set_error(rfim_ctx* ctx, const char* msg) { ctx->last_error = msg; }
+
+// Every device (and pinned host) allocation a context makes after rfim_create
+// goes through here, so that the "fail_alloc_after" test hook can refuse it
+// exactly as a full device would (cudaErrorMemoryAllocation, nothing allocated).
+cudaError_t ctx_malloc(rfim_ctx* ctx, void** p, size_t bytes, bool pinned_host) {
+  *p = nullptr;
+  if (ctx && ctx->fail_alloc_after >= 0) {
+    if (ctx->fail_alloc_after == 0) return cudaErrorMemoryAllocation;
+    ctx->fail_alloc_after--;
+  }
+  return pinned_host ? cudaMallocHost(p, bytes) : cudaMalloc(p, bytes);
+}
 StreamService*& ctx_stream_service(rfim_ctx* ctx) { return ctx->stream; }
 void ctx_stage_options(rfim_ctx* ctx, size_t& group_bytes, int& streams) {
   group_bytes = (size_t)ctx->stage_group_bytes;

@@ -116,13 +116,18 @@ constexpr int TD_WARP_CHUNKS = 800;
 constexpr int TD_WARP_STAGE = TD_WARP_CHUNKS * 16;
 constexpr int TD_CTA_CHUNKS = 6144;
 constexpr int TD_ROWS_PER_ITEM = NT / 32;
+// uint8 rows are exact up to (255 T)^2 < 2^53
+constexpr long long TD_MAX_T = 372181;
 // Random replacement keeps two 16-bit flag words per chunk beside the staged
 // row (this iteration's flags, and the OR over iterations): warp rows up to 640
-// chunks, longer rows (up to 4915 chunks) by the whole CTA.
+// chunks, longer rows (up to 4915 chunks) by the whole CTA.  Longer rows are
+// not staged (mode 2): their two flag bitmaps, one bit per sample, take the
+// CTA stage, up to the exactness bound of the uint8 decisions.
 __host__ __device__ inline int td_random_row_mode(long long T) {
   const long long nch = (T + 30) / 16 + 1;
   if (20 * nch <= TD_WARP_STAGE) return 0;
   if (20 * nch <= TD_CTA_CHUNKS * 16) return 1;
+  if (T <= TD_MAX_T && 2 * 4 * ((T + 31) / 32) <= TD_CTA_CHUNKS * 16) return 2;
   return -1;
 }
 
@@ -130,7 +135,6 @@ __host__ __device__ inline int td_random_row_mode(long long T) {
 // TDSC rows longer than the CTA stage are read from global memory in every
 // pass (mode 2), up to the exactness bound of the uint8 decisions,
 // (255 T)^2 < 2^53.
-constexpr long long TD_MAX_T = 372181;
 // Rows of up to TD_QUAD_CHUNKS chunks (about 3,150 samples) take a quarter warp
 // each, four rows per warp in a quarter of the warp's stage (mode 3), so that
 // the per-row steps (thresholds, reductions) are shared by fewer lanes.
@@ -159,6 +163,9 @@ int launch_engine_u8(const Params& p, const LaunchCfg& cfg, void* stream);
 // of ws x C floats plus per-(t, bin) and per-column scratch.
 constexpr int TD32_LIST = 1024;  // replaced values kept per iteration for the statistics update
 constexpr int TD32_MAX_T = 52000;
+// float32 rows beyond the stage with random replacement: two flag bitmaps,
+// one bit per sample, in shared memory
+__host__ __device__ inline int td32_rnd_long_bytes(long long T) { return (int)(8 * ((T + 31) / 32)); }
 __host__ __device__ inline int td32_smem_bytes(int T) {
   const int nch = (T + 6) / 4 + 1;
   return 16 * nch + align16i(nch) + 4 * TD32_LIST;

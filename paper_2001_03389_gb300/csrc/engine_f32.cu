@@ -693,6 +693,106 @@ __device__ __noinline__ void tdsc_row_f32_long(const Params& P, const Job& J, in
 }
 
 // ---------------------------------------------------------------------------
+// TDSC with random replacement on one float32 row longer than the stage (the
+// whole CTA).  A draw's outcome is not a function of the value, so the row
+// cannot be replayed as in tdsc_row_f32_long: iteration 0 reads the input row
+// and writes every sample of the output row, later iterations read the output
+// row and rewrite its flagged samples.  The flags are bitmaps over the sample
+// index in shared memory (fcur: this iteration's, facc: the OR over the
+// iterations), so a draw tests the flag of the very sample it would copy and an
+// iteration writes only samples that no draw of it may read.  Statistics,
+// finish and decisions as in tdsc_row_f32 (the row summed again every
+// iteration, as its random path does).  A warp takes one 32-sample word at a
+// time, lane i sample 32 w + i.
+// ---------------------------------------------------------------------------
+__device__ __noinline__ void tdsc_row_f32_long_rnd(const Params& P, const Job& J, int row, unsigned* bm, Red32* red) {
+  const CutDev& cut = P.td;
+  const int T = J.T, t = threadIdx.x, lane = t & 31;
+  const float* rin = static_cast<const float*>(J.in) + (size_t)row * T;
+  float* rout = static_cast<float*>(J.out) + (size_t)row * T;
+  const int I = cut.iterations, NW = (T + 31) >> 5;
+  const double rT = 1.0 / (double)T;
+  const FF kff{cut.k_hi, cut.k_lo};
+  unsigned* fcur = bm;
+  unsigned* facc = bm + NW;
+  for (int w = t; w < NW; w += NT) facc[w] = 0;
+  const unsigned long long key = draw_key(J.beam, row);
+  for (int it = 0; it < I; it++) {
+    const float* src = it == 0 ? rin : rout;  // the current values
+    FF S{0.f, 0.f}, Q{0.f, 0.f};
+    for (int i = t; i < T; i += NT) {
+      const float y = src[i];
+      ff_acc(S, y);
+      ff_acc_sq(Q, y);
+    }
+    grp_ff2<NT>(S, Q, red, t, 0);  // (the same in every thread)
+    if (it == 0 && J.stats && t == 0) {  // statistics of the input row, for the caller's records
+      J.stats[2 * (size_t)row] = (double)S.hi + (double)S.lo;
+      J.stats[2 * (size_t)row + 1] = (double)Q.hi + (double)Q.lo;
+    }
+    FF mu = ff_div_int(S, T);
+    const FF mq = ff_div_int(Q, T);
+    FF var = ff_add(mq, ff_neg(ff_mul(mu, mu)));
+    if (!(var.hi >= 1e-3f * mq.hi)) {
+      // cancellation (or a constant row): FP64 two-pass
+      double sd = 0.0;
+      for (int i = t; i < T; i += NT) sd += (double)src[i];
+      sd = grp_dsum<NT>(sd, red, t, 0);
+      const double m2 = sd * rT;
+      double ss = 0.0;
+      for (int i = t; i < T; i += NT) {
+        const double d = (double)src[i] - m2;
+        ss += d * d;
+      }
+      ss = grp_dsum<NT>(ss, red, t, 0);
+      mu = ff_from_d(m2);
+      var = ff_from_d(ss * rT);
+    }
+    const Cut32 c = make_cut32(mu, ff_mul(kff, ff_sqrt(var)));
+    for (int w = t >> 5; w < NW; w += NT / 32) {
+      const int i = 32 * w + lane;
+      const bool f = i < T && flag32(src[i], c);
+      const unsigned bits = __ballot_sync(0xffffffffu, f);
+      if (lane == 0) fcur[w] = bits;
+    }
+    gsync<NT>(0);
+    for (int w = t >> 5; w < NW; w += NT / 32) {
+      const int i = 32 * w + lane;
+      const unsigned fw = fcur[w];
+      if (i < T) {
+        if ((fw >> lane) & 1u) {
+          float y = src[i];
+          for (int a = 0; a < DRAW_ATTEMPTS; a++) {
+            const unsigned u = draw_pos(key, i, 1, cut.it0 + it, a, (unsigned)T);
+            if (!((fcur[u >> 5] >> (u & 31)) & 1u)) {
+              y = src[u];
+              break;
+            }
+          }
+          rout[i] = y;
+        } else if (it == 0 && rout != rin) {
+          rout[i] = rin[i];
+        }
+      }
+      if (lane == 0) facc[w] |= fw;
+    }
+    gsync<NT>(0);  // (also publishes this iteration's writes of the output row)
+  }
+  // the mask: facc holds the row's bits word for word
+  if (P.mask_kind == MASK_BITS && J.mask) {
+    unsigned* mrow = static_cast<unsigned*>(J.mask) + (size_t)row * NW;
+    for (int w = t; w < NW; w += NT) mrow[w] = P.td_mask_or ? (mrow[w] | facc[w]) : facc[w];
+  } else if (P.mask_kind == MASK_BYTES && J.mask) {
+    unsigned char* mb = static_cast<unsigned char*>(J.mask) + (size_t)row * T;
+    for (int i = t; i < T; i += NT) {
+      const unsigned char f = (unsigned char)((facc[i >> 5] >> (i & 31)) & 1u);
+      mb[i] = P.td_mask_or ? (unsigned char)(mb[i] | f) : f;
+    }
+  }
+  gsync<NT>(0);
+}
+
+// ---------------------------------------------------------------------------
 // FDSC on one item: one sub-slab of ws time samples x C channels of a float32
 // beam (16 bytes of each channel row for ws = 4).  Consecutive items, which
 // share the 128-byte lines of the rows, run at the same time, so the lines in
@@ -1141,7 +1241,12 @@ __global__ void __launch_bounds__(NT, 2) k_engine_f32(const __grid_constant__ Pa
       } else if (J.td_mode == 1) {
         tdsc_row_f32<NT, RND>(P, J, idx, smem, &red[0], threadIdx.x, 0, &s_mbar[2], mpar, 1);
       } else {
-        tdsc_row_f32_long(P, J, idx, &red[0]);
+        if constexpr (RND) {
+          if (P.td.replace == REP_RANDOM) tdsc_row_f32_long_rnd(P, J, idx, reinterpret_cast<unsigned*>(smem), &red[0]);
+          else tdsc_row_f32_long(P, J, idx, &red[0]);
+        } else {
+          tdsc_row_f32_long(P, J, idx, &red[0]);
+        }
       }
       __syncthreads();
       if (threadIdx.x == 0) {
@@ -1159,8 +1264,12 @@ int engine_smem_f32(const Params& p) {
   int s = 16;
   for (int j = 0; j < p.n_jobs; j++) {
     const Job& J = p.jobs[j];
-    if (p.td.iterations > 0 && J.td_mode != 2) {  // (mode 2 rows are not staged)
+    if (p.td.iterations > 0 && J.td_mode != 2) {
       const int td = (J.td_mode == 0 ? 2 : 1) * td32_smem_bytes(J.T);
+      s = s > td ? s : td;
+    } else if (p.td.iterations > 0 && p.td.replace == REP_RANDOM) {
+      // mode 2 rows are not staged; with random replacement they keep two flag bitmaps
+      const int td = td32_rnd_long_bytes(J.T);
       s = s > td ? s : td;
     }
     if (p.fd.iterations > 0) {

@@ -1633,6 +1633,100 @@ __device__ __noinline__ void tdsc_row_u8_long(const Params& P, const Job& J, int
   tdsc_row_u8<NT, false, true>(P, J, row, st, scr, threadIdx.x, nullptr, no_par, 0);
 }
 
+// TDSC with random replacement on a row longer than the random-replacement
+// stage (the whole CTA).  Nothing is staged.  Iteration 0 reads the input row
+// and writes every sample of the output row; later iterations read the output
+// row and rewrite its flagged samples.  The flags live in shared memory as
+// bitmaps over the sample index (fcur: this iteration's, facc: the OR over the
+// iterations), so a draw tests the flag of the very sample it would copy, and
+// an iteration writes only samples that no draw of it may read.  A warp takes
+// one 32-sample word at a time, lane i sample 32 w + i.  Out of line, as such
+// rows are rare.
+__device__ __noinline__ void tdsc_row_u8_long_rnd(const Params& P, const Job& J, int row, unsigned* bm,
+                                                  unsigned long long* scr) {
+  const CutDev& cut = P.td;
+  const int T = J.T, lane = threadIdx.x & 31;
+  const uint8_t* beam_in = static_cast<const uint8_t*>(J.in);
+  const uint8_t* rin = beam_in + (size_t)row * T;
+  uint8_t* rout = static_cast<uint8_t*>(J.out) + (size_t)row * T;
+  const int NW = (T + 31) >> 5;
+  unsigned* fcur = bm;
+  unsigned* facc = bm + NW;
+  for (int w = threadIdx.x; w < NW; w += NT) facc[w] = 0;
+  // sums of the input row
+  unsigned long long sq[2] = {0, 0};
+  for (int i = threadIdx.x; i < T; i += NT) {
+    const unsigned x = ld1_na(rin + i);
+    sq[0] += x;
+    sq[1] += x * x;
+  }
+  grp_sum<NT, 2>(sq, scr);
+  unsigned long long S = sq[0], Q = sq[1];
+  if (J.stats && threadIdx.x == 0) {
+    J.stats[2 * (size_t)row] = (double)S;
+    J.stats[2 * (size_t)row + 1] = (double)Q;
+  }
+  const unsigned long long key = draw_key(J.beam, row);
+  const float rcpT = 1.0f / (float)T;
+  for (int it = 0; it < cut.iterations; it++) {
+    const uint8_t* src = it == 0 ? rin : rout;  // the current values
+    int lo, hi;
+    tdsc_keep_warp<NT>(S, Q, T, rcpT, cut.k2, lo, hi);
+    for (int w = threadIdx.x >> 5; w < NW; w += NT / 32) {
+      const int i = 32 * w + lane;
+      bool f = false;
+      if (i < T) {
+        const int x = ld1_na(src + i);
+        f = x < lo || x > hi;
+      }
+      const unsigned bits = __ballot_sync(0xffffffffu, f);
+      if (lane == 0) fcur[w] = bits;
+    }
+    __syncthreads();
+    long long dS = 0, dQ = 0;
+    for (int w = threadIdx.x >> 5; w < NW; w += NT / 32) {
+      const int i = 32 * w + lane;
+      const unsigned fw = fcur[w];
+      if (i < T) {
+        if ((fw >> lane) & 1u) {
+          const unsigned x = ld1_na(src + i);
+          unsigned nv = x;
+          for (int a = 0; a < DRAW_ATTEMPTS; a++) {
+            const unsigned u = draw_pos(key, i, 1, cut.it0 + it, a, (unsigned)T);
+            if (!((fcur[u >> 5] >> (u & 31)) & 1u)) {
+              nv = ld1_na(src + u);
+              break;
+            }
+          }
+          rout[i] = (uint8_t)nv;
+          dS += (long long)nv - (long long)x;
+          dQ += (long long)(nv * nv) - (long long)(x * x);
+        } else if (it == 0 && rout != rin) {
+          rout[i] = ld1_na(rin + i);
+        }
+      }
+      if (lane == 0) facc[w] |= fw;
+    }
+    unsigned long long d[2] = {(unsigned long long)dS, (unsigned long long)dQ};
+    grp_sum<NT, 2>(d, scr);  // (its barriers also publish this iteration's writes of the output row)
+    S += d[0];
+    Q += d[1];
+  }
+  __syncthreads();
+  // the mask: facc holds the row's bits word for word
+  if (P.mask_kind == MASK_BITS && J.mask) {
+    unsigned* mrow = static_cast<unsigned*>(J.mask) + (size_t)row * NW;
+    for (int w = threadIdx.x; w < NW; w += NT) mrow[w] = P.td_mask_or ? (mrow[w] | facc[w]) : facc[w];
+  } else if (P.mask_kind == MASK_BYTES && J.mask) {
+    uint8_t* mb = static_cast<uint8_t*>(J.mask) + (size_t)row * T;
+    for (int i = threadIdx.x; i < T; i += NT) {
+      const uint8_t f = (uint8_t)((facc[i >> 5] >> (i & 31)) & 1u);
+      mb[i] = P.td_mask_or ? (uint8_t)(mb[i] | f) : f;
+    }
+  }
+  __syncthreads();
+}
+
 // MINB = CTAs per SM the register allocation targets (the TDSC row stage is
 // 102 KB, so two CTAs share an SM).  RND: random replacement is compiled in
 // (a separate build, so that the mean and median paths carry none of it).
@@ -1682,7 +1776,12 @@ __global__ void __launch_bounds__(NT, MINB) k_engine_u8(const __grid_constant__ 
         tdsc_row_u8<NT, RND>(P, J, idx, reinterpret_cast<uint4*>(smem), scr, threadIdx.x, &s_mbar[40], mpar, 2);
         done = 1;
       } else {
-        tdsc_row_u8_long(P, J, idx, reinterpret_cast<uint4*>(smem), scr);
+        if constexpr (RND) {
+          if (P.td.replace == REP_RANDOM) tdsc_row_u8_long_rnd(P, J, idx, reinterpret_cast<unsigned*>(smem), scr);
+          else tdsc_row_u8_long(P, J, idx, reinterpret_cast<uint4*>(smem), scr);
+        } else {
+          tdsc_row_u8_long(P, J, idx, reinterpret_cast<uint4*>(smem), scr);
+        }
         done = 1;
       }
       __syncthreads();

@@ -87,7 +87,7 @@ rfim_status stager_run(HostStager* s, rfim_ctx* ctx, const rfim_block* hb, const
     for (int i = 0; i < STAGE_MAX_STREAMS; i++) {
       cudaFree(s->dbuf[i]);
       s->dbuf[i] = nullptr;
-      if (cudaMalloc(&s->dbuf[i], need) != cudaSuccess) {
+      if (ctx_malloc(ctx, &s->dbuf[i], need) != cudaSuccess) {
         s->cap_buf = 0;
         ctx_set_error(ctx, "staging allocation failed");
         return RFIM_ERR_OOM;
@@ -99,7 +99,7 @@ rfim_status stager_run(HostStager* s, rfim_ctx* ctx, const rfim_block* hb, const
     for (int i = 0; i < STAGE_MAX_STREAMS; i++) {
       cudaFree(s->dmask[i]);
       s->dmask[i] = nullptr;
-      if (cudaMalloc(&s->dmask[i], needm) != cudaSuccess) {
+      if (ctx_malloc(ctx, &s->dmask[i], needm) != cudaSuccess) {
         s->cap_mask = 0;
         ctx_set_error(ctx, "staging allocation failed");
         return RFIM_ERR_OOM;
@@ -249,7 +249,7 @@ rfim_status tuner_apply(Tuner* t, rfim_ctx* ctx, const rfim_block* blocks, int n
   for (auto& b : tb) {
     const size_t bytes = (size_t)b.beams * b.channels * b.samples * esize(b.dtype);
     void* o = nullptr;
-    if (cudaMalloc(&o, bytes) != cudaSuccess) {
+    if (ctx_malloc(ctx, &o, bytes) != cudaSuccess) {
       cleanup();
       ctx_set_error(ctx, "autotune scratch allocation failed");
       return RFIM_ERR_OOM;
@@ -257,7 +257,7 @@ rfim_status tuner_apply(Tuner* t, rfim_ctx* ctx, const rfim_block* blocks, int n
     allocs.push_back(o);
     if (b.in == b.out) {
       void* i2 = nullptr;
-      if (cudaMalloc(&i2, bytes) != cudaSuccess) {
+      if (ctx_malloc(ctx, &i2, bytes) != cudaSuccess) {
         cleanup();
         ctx_set_error(ctx, "autotune scratch allocation failed");
         return RFIM_ERR_OOM;
@@ -270,7 +270,7 @@ rfim_status tuner_apply(Tuner* t, rfim_ctx* ctx, const rfim_block* blocks, int n
     const size_t mb = mask_beam_bytes(&b) * b.beams;
     if (mb) {
       void* m = nullptr;
-      if (cudaMalloc(&m, mb) != cudaSuccess) {
+      if (ctx_malloc(ctx, &m, mb) != cudaSuccess) {
         cleanup();
         ctx_set_error(ctx, "autotune scratch allocation failed");
         return RFIM_ERR_OOM;

@@ -27,6 +27,9 @@ rfim_status ctx_clean_async(rfim_ctx* ctx, const rfim_block* blocks, int n, cons
 int ctx_device(rfim_ctx* ctx);
 size_t ctx_hbm_budget(rfim_ctx* ctx);
 void ctx_set_error(rfim_ctx* ctx, const char* msg);
+// a device (or, with pinned_host, page-locked host) allocation on behalf of the
+// context; fails without allocating while the "fail_alloc_after" hook says so
+cudaError_t ctx_malloc(rfim_ctx* ctx, void** p, size_t bytes, bool pinned_host = false);
 StreamService*& ctx_stream_service(rfim_ctx* ctx);
 void ctx_get_tunables(rfim_ctx* ctx, Tunables& t);
 // host staging: bytes per group and streams in the ring

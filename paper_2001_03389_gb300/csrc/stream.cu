@@ -366,11 +366,12 @@ rfim_status rfim_stream_open(rfim_ctx* ctx, int n_beams, int channels, int chunk
     ctx_set_error(ctx, "HBM budget holds no streaming slot");
     return RFIM_ERR_OOM;
   }
-  if (cudaMalloc(&s->d_slots, s->chunk_bytes * s->n_slots) != cudaSuccess ||
-      cudaMalloc(&s->d_masks, s->mask_bytes * s->n_slots) != cudaSuccess ||
-      cudaMalloc(&s->d_stats, sizeof(double) * 2 * channels * s->n_slots) != cudaSuccess ||
-      cudaMalloc(&s->d_ctr, sizeof(unsigned) * CTR_WORDS * N_STREAMS) != cudaSuccess ||
-      cudaMallocHost(&s->h_status, sizeof(unsigned) * N_STREAMS) != cudaSuccess) {
+  if (ctx_malloc(ctx, reinterpret_cast<void**>(&s->d_slots), s->chunk_bytes * s->n_slots) != cudaSuccess ||
+      ctx_malloc(ctx, reinterpret_cast<void**>(&s->d_masks), s->mask_bytes * s->n_slots) != cudaSuccess ||
+      ctx_malloc(ctx, reinterpret_cast<void**>(&s->d_stats), sizeof(double) * 2 * channels * s->n_slots) !=
+          cudaSuccess ||
+      ctx_malloc(ctx, reinterpret_cast<void**>(&s->d_ctr), sizeof(unsigned) * CTR_WORDS * N_STREAMS) != cudaSuccess ||
+      ctx_malloc(ctx, reinterpret_cast<void**>(&s->h_status), sizeof(unsigned) * N_STREAMS, true) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(s->d_slots);
     cudaFree(s->d_masks);

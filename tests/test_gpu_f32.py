@@ -314,8 +314,8 @@ def test_f32_validation(ctx):
 
     from paper_2001_03389_gb300 import rfim
 
-    row = torch.zeros((1, 1, 60000), dtype=torch.float32, device="cuda:0")
-    with pytest.raises(rfim.RfimError) as e:  # random replacement needs the staged row
+    row = torch.zeros((1, 1, 921601), dtype=torch.float32, device="cuda:0")
+    with pytest.raises(rfim.RfimError) as e:  # random replacement: the row's flag bitmaps do not fit
         ctx.tdsc(ctx.block(row, torch.empty_like(row)), rfim.make_cut(3.0, replace="random"))
     assert e.value.status == rfim.ERR_ARG
     big = torch.zeros((1, 40000, 4), dtype=torch.float32, device="cuda:0")

@@ -51,9 +51,12 @@ def rfi_u8(rng, shape, frac=0.03):
     return x
 
 
-# warp rows, CTA rows (from 10210 samples: more than 640 chunks), ragged ends, the longest row
+# warp rows, CTA rows (from 10210 samples: more than 640 chunks), ragged ends,
+# the longest staged row, and rows beyond the stage (flag bitmaps, rows read
+# from memory) up to the longest uint8 row
 @pytest.mark.parametrize("C,T", [(1, 1), (3, 5), (7, 31), (37, 32), (64, 100), (100, 257), (33, 4099),
-                                 (5, 10209), (4, 10210), (3, 12500), (2, 25000), (1, 78609)])
+                                 (5, 10209), (4, 10210), (3, 12500), (2, 25000), (1, 78609), (1, 78610),
+                                 (2, 100003), (1, 372181)])
 def test_tdsc_random_u8(oracle, ctx, C, T):
     rng = np.random.default_rng(C * 7919 + T)
     x = rfi_u8(rng, (2, C, T))
@@ -120,18 +123,41 @@ def test_random_u8_full_beam(oracle, ctx):
     assert (wf & 1).any() and (wf & 2).any()
 
 
-def test_random_u8_row_limit(ctx):
+def test_random_row_limits(ctx):
     import torch
 
     from paper_2001_03389_gb300 import rfim
 
-    x = torch.zeros((1, 1, 78610), dtype=torch.uint8, device="cuda:0")
-    with pytest.raises(rfim.RfimError):
+    # uint8: random replacement reaches the exactness bound of every uint8 row
+    x = torch.zeros((1, 1, 372182), dtype=torch.uint8, device="cuda:0")
+    with pytest.raises(rfim.RfimError) as e:
         ctx.tdsc(ctx.block(x, torch.empty_like(x)), rfim.make_cut(3.0, replace="random"))
-    # float32 rows with random replacement reach the float32 TDSC row limit
-    y = torch.zeros((1, 1, 52000), dtype=torch.float32, device="cuda:0")
+    assert e.value.status == rfim.ERR_RANGE
+    # float32: rows beyond the stage keep two flag bitmaps in shared memory
+    y = torch.zeros((1, 1, 921600), dtype=torch.float32, device="cuda:0")
     ctx.tdsc(ctx.block(y, torch.empty_like(y)), rfim.make_cut(3.0, replace="random"))
     torch.cuda.synchronize()
+    y = torch.zeros((1, 1, 921601), dtype=torch.float32, device="cuda:0")
+    with pytest.raises(rfim.RfimError) as e:
+        ctx.tdsc(ctx.block(y, torch.empty_like(y)), rfim.make_cut(3.0, replace="random"))
+    assert e.value.status == rfim.ERR_ARG
+    assert ctx.device_status() == rfim.OK
+
+
+@pytest.mark.parametrize("mask_fmt", ["bits", "bytes"])
+def test_random_long_rows_misaligned_in_place(oracle, ctx, mask_fmt):
+    # rows beyond the stage: misaligned input and output, in place, both mask
+    # formats, and the fused launch with FDSC after them
+    rng = np.random.default_rng(404)
+    x = rfi_u8(rng, (2, 3, 100003))
+    td = dict(k=2.5, iterations=3, replace="random")
+    check_u8(oracle, ctx, x, td=td, mask_fmt=mask_fmt, in_off=5, out_off=11, api="tdsc")
+    check_u8(oracle, ctx, x, td=td, mask_fmt=mask_fmt, in_place=True, in_off=3, api="tdsc")
+    check_u8(oracle, ctx, x, td=td, fd=dict(k=2.5, iterations=2, replace="random", bin=3), mask_fmt=mask_fmt)
+    if mask_fmt == "bits":  # (the float32 checker reads bit masks)
+        y = chi2_f32(rng, (2, 3, 60001))
+        check_f32(oracle, ctx, y, td=td, in_place=True, api="tdsc")
+        check_f32(oracle, ctx, y, td=td, fd=dict(k=2.5, iterations=2, replace="random", bin=3))
 
 
 # ---- float32
@@ -167,7 +193,8 @@ def chi2_f32(rng, shape):
     return x
 
 
-@pytest.mark.parametrize("C,T", [(1, 1), (3, 7), (17, 129), (64, 1000), (5, 12500), (2, 40000)])
+@pytest.mark.parametrize("C,T", [(1, 1), (3, 7), (17, 129), (64, 1000), (5, 12500), (2, 40000), (1, 52001),
+                                 (2, 150000)])
 def test_tdsc_random_f32(oracle, ctx, C, T):
     rng = np.random.default_rng(C + 13 * T)
     x = chi2_f32(rng, (2, C, T))

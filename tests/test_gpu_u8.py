@@ -8,7 +8,7 @@ full-size ARTS configuration on whole beams of the launch the benchmark times.
 import numpy as np
 import pytest
 
-from gpu_util import noise_u8, run_gpu
+from gpu_util import noise_u8, run_gpu, unpack_bits
 
 pytestmark = pytest.mark.gpu
 
@@ -259,6 +259,69 @@ def test_validation_errors(ctx):
     with pytest.raises(rfim.RfimError) as e:
         ctx.tdsc(ctx.block(long_row, torch.empty_like(long_row)), rfim.make_cut(3.0))
     assert e.value.status == rfim.ERR_RANGE
+
+
+def test_allocation_failure_is_reported():
+    # Host-side fault injection: the "fail_alloc_after" hook refuses the
+    # context's device and pinned-host allocations.  Every call that needs one
+    # returns RFIM_ERR_OOM without launching, and once the hook is off the same
+    # calls succeed on the same context with the results of a plain launch.
+    import torch
+
+    from paper_2001_03389_gb300 import rfim
+
+    rng = np.random.default_rng(11)
+    B, C, T = 2, 96, 700
+    x = torch.from_numpy(noise_u8(rng, (B, C, T))).cuda()
+    td, fd = rfim.make_cut(3.0, 2, "median"), rfim.make_cut(3.0, 2, "median", 32)
+    ref = torch.empty_like(x)
+    ref_mask = torch.zeros(rfim.mask_words(C, T, B), dtype=torch.int32, device="cuda:0")
+    c = rfim.Context(0)
+    try:
+        c.clean(rfim.Context.block(x, ref, ref_mask, "bct", "bits"), td, fd)
+        torch.cuda.synchronize()
+        xt = x.transpose(1, 2).contiguous()  # BTC copy of the same beams
+        hin = x.cpu().pin_memory()
+        hout = torch.empty_like(hin).pin_memory()
+        hmask = torch.zeros(rfim.mask_words(C, T, B), dtype=torch.int32).pin_memory()
+        hblk = rfim.rfim_block(hin.data_ptr(), hout.data_ptr(), hmask.data_ptr(), B, C, T, rfim.U8,
+                               rfim.LAYOUT_BCT, rfim.MASK_BITS)
+
+        def calls():
+            out_t = torch.empty_like(xt)
+            m_t = torch.empty_like(xt)  # byte mask: the BTC path takes a data and a mask scratch
+            yield "btc", lambda: c.clean(rfim.Context.block(xt, out_t, m_t, "btc", "bytes"), td, fd), (out_t, m_t)
+            o = torch.empty_like(x)
+            yield "graph", lambda: c.clean_batch([rfim.Context.block(x, o)], td, fd, flags=rfim.BATCH_GRAPH), o
+            yield "host", lambda: c.clean_host(hblk, td, fd), None
+            yield "stream", lambda: c.stream_open(4, C, T, rfim.U8, td, fd), None
+
+        for after in (0, 1):
+            for name, call, _ in calls():
+                c.set_option("fail_alloc_after", after)
+                if name == "graph" and after == 1:
+                    continue  # the graph takes a single allocation
+                with pytest.raises(rfim.RfimError) as e:
+                    call()
+                assert e.value.status == rfim.ERR_OOM, name
+                assert c.last_error(), name
+        c.set_option("fail_alloc_after", -1)
+        for name, call, out in calls():
+            call()
+            torch.cuda.synchronize()
+            if name == "btc":
+                assert torch.equal(out[0].transpose(1, 2), ref)
+                flagged = unpack_bits(ref_mask.cpu().numpy(), B * C, T).reshape(B, C, T)
+                assert np.array_equal(out[1].transpose(1, 2).cpu().numpy() != 0, flagged)
+            elif name == "graph":
+                assert torch.equal(out, ref)
+            elif name == "host":
+                assert torch.equal(hout, ref.cpu()) and torch.equal(hmask, ref_mask.cpu())
+            else:
+                c.stream_close()
+        assert c.device_status() == rfim.OK
+    finally:
+        c.close()
 
 
 def test_device_wait_timeout_is_reported(ctx):
