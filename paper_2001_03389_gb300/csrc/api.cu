@@ -228,7 +228,7 @@ rfim_status check_impl(rfim_ctx* ctx, const rfim_block* b, const CutNorm& td, co
   if (fd.on) {
     // the smallest FDSC tile (8 samples x all channels) must fit one CTA's shared memory
     const int C = b->channels, nb = (C + fd.bin - 1) / fd.bin;
-    if (fd_smem_bytes(8, fd_pitch(C), nb, C, fd.rep == RFIM_REPLACE_RANDOM) > MAX_SMEM_PER_CTA)
+    if (fd_smem_bytes(8, fd_pitch(C), nb, C, fd.rep == RFIM_REPLACE_RANDOM, fd.bin) > MAX_SMEM_PER_CTA)
       return fail(ctx, RFIM_ERR_RANGE, "FDSC: %d channels do not fit the on-chip tile", C);
   }
   return RFIM_OK;
@@ -243,10 +243,10 @@ struct Plan {
   bool prog = false;  // the jobs carry TDSC cut records (float32; used by fused launches only)
 };
 
-int pick_ws_opt(int tile_samples, int C, int nb, int pitch, int budget, bool rnd) {
+int pick_ws_opt(int tile_samples, int C, int nb, int pitch, int budget, bool rnd, int bin) {
   if (tile_samples > 0) return tile_samples < 8 ? 8 : tile_samples;  // uint8 tiles are 8, 16 or 32 wide
   for (int ws : {32, 16, 8})
-    if (fd_smem_bytes(ws, pitch, nb, C, rnd) <= budget) return ws;
+    if (fd_smem_bytes(ws, pitch, nb, C, rnd, bin) <= budget) return ws;
   return 8;
 }
 
@@ -279,7 +279,7 @@ Job make_job(const rfim_block* b, int j, const CutNorm& fd, int tile_samples, in
   J.m_full = (unsigned long long)(L / G);
   J.m_last = (unsigned long long)(L / J.last_g);
   J.pitch = fd_pitch(C * (int)es);
-  J.ws = pick_ws_opt(tile_samples, C, J.nb, J.pitch, smem_target, fd.on && fd.rep == RFIM_REPLACE_RANDOM);
+  J.ws = pick_ws_opt(tile_samples, C, J.nb, J.pitch, smem_target, fd.on && fd.rep == RFIM_REPLACE_RANDOM, G);
   J.fd_items = (T + FD_ITEM_T - 1) / FD_ITEM_T;
   const int tm = td_row_mode(T);  // (-1 only with TDSC off: no TDSC items then)
   J.td_mode = tm < 0 ? 1 : tm;

@@ -93,12 +93,24 @@ __host__ __device__ inline int align16i(int x) { return (x + 15) & ~15; }
 // 8 lanes of 4 neighbouring columns hit 32 distinct banks.
 __host__ __device__ inline int fd_nbp(int nb) { return nb + ((8 - nb) % 32 + 32) % 32; }
 
+// Flag bits of an item.  With 32-channel bins and no random replacement, one
+// word per (time sample of the item, bin), bit j = channel 32 g + j, each
+// written by the one lane that resolves that bin at that sample, and turned
+// into per-channel words by a 32 x 32 bit transpose at the end of the item;
+// rows of nb | 1 words (odd: the 32 rows of one bin fall in distinct banks).
+// Otherwise one word per channel, bit = time sample, set by shared atomics.
+__host__ __device__ inline bool fd_bin_bits(int bin, bool rnd) { return bin == 32 && !rnd; }
+__host__ __device__ inline int fd_flag_bytes(int C, int nb, bool bin_bits) {
+  return align16i((bin_bits ? FD_ITEM_T * (nb | 1) : C) * 4);
+}
+
 // rnd: random replacement adds one word per channel (the flags of the
-// iteration in progress, bit = tile row)
-__host__ __device__ inline int fd_smem_bytes(int ws, int pitch, int nb, int C, bool rnd = false) {
+// iteration in progress, bit = tile row); bin: the FDSC bin size
+__host__ __device__ inline int fd_smem_bytes(int ws, int pitch, int nb, int C, bool rnd, int bin) {
   const int nbp = fd_nbp(nb);
   return ws * pitch + 2 * align16i(ws * nbp * 4) + align16i(ws * nbp * 2) + align16i(ws * 8) + align16i(ws * 8) +
-         align16i(C * 4) + align16i(ws * nb * 4) + 4 * (NT / 32) + (rnd ? align16i(C * 4) : 0);
+         fd_flag_bytes(C, nb, fd_bin_bits(bin, rnd)) + align16i(ws * nb * 4) + 4 * (NT / 32) +
+         (rnd ? align16i(C * 4) : 0);
 }
 
 // Tile row pitch: C bytes rounded up to 128, so that the XOR swizzle of the 16-byte

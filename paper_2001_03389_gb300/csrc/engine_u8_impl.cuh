@@ -270,8 +270,9 @@ __device__ __forceinline__ uint4 chunk_valid(const RowGeom& g, int k) {
 // Lower median of a staged row: m = min{p : #(x <= p) >= need}, need = floor((T+1)/2).
 // With f(p) = sum |x - p| (SAD), #(x <= p) = (T + f(p+1) - f(p)) / 2 for p <= 254,
 // and a median lies within one standard deviation of the mean.  The first pass
-// probes three consecutive points around the mean; later passes split the
-// remaining window in three.
+// counts at three consecutive points just below the mean, settling a median of
+// floor(mu) - 1 or floor(mu) (bright interference lifts the mean of a row above
+// its median); later passes split the remaining window in three.
 struct MedSearch {
   int lo, hi;    // the median lies in [lo, hi]
   int pts[4];    // probe points of the current pass
@@ -285,7 +286,7 @@ __device__ __forceinline__ void med_init(MedSearch& m, unsigned long long S, uns
   const float sd = sqrtf(var);
   m.lo = max(0, (int)floorf(mu - sd) - 1);
   m.hi = min(255, (int)ceilf(mu + sd) + 1);
-  int c = (int)floorf(mu) - 1;
+  int c = (int)floorf(mu) - 2;
   if (c > m.hi - 2) c = m.hi - 2;
   if (c < m.lo) c = m.lo;
   if (c < 0) c = 0;
@@ -867,13 +868,14 @@ struct FdLayout {
   uint16_t* med;          // ws x nbp cached bin medians (0xFFFF unknown)
   unsigned long long* V;  // ws: sum of D^2 per column
   unsigned* A;            // ws x 2: keep half-widths per bin-size class
-  unsigned* fmask;        // C: FDSC flag bits of the item (bit = t - t_item)
+  unsigned* fmask;        // flag bits of the item: [FD_ITEM_T][nb | 1] words (bit j = channel 32 g + j) when
+                          // bin_bits, else C words (bit = t - t_item)
   unsigned* list;         // ws x nb flagged (t, bin) pairs, one segment per warp
   unsigned* cnt;          // per-warp list lengths
   unsigned* fcur;         // C (random replacement only): flags of the iteration in progress (bit = tile row)
 };
 
-__device__ __forceinline__ FdLayout fd_layout(unsigned char* smem, int ws, int pitch, int nb, int C) {
+__device__ __forceinline__ FdLayout fd_layout(unsigned char* smem, int ws, int pitch, int nb, int C, bool bin_bits) {
   FdLayout L;
   const int nbp = fd_nbp(nb);
   unsigned char* p = smem;
@@ -890,7 +892,7 @@ __device__ __forceinline__ FdLayout fd_layout(unsigned char* smem, int ws, int p
   L.A = reinterpret_cast<unsigned*>(p);
   p += align16i(ws * 8);
   L.fmask = reinterpret_cast<unsigned*>(p);
-  p += align16i(C * 4);
+  p += fd_flag_bytes(C, nb, bin_bits);
   L.list = reinterpret_cast<unsigned*>(p);
   p += align16i(ws * nb * 4);
   L.cnt = reinterpret_cast<unsigned*>(p);
@@ -1135,6 +1137,88 @@ __device__ __forceinline__ void store4_row(uint8_t* a, uint32_t w, int n) {
   for (int b = 0; b < n; b++) a[b] = (uint8_t)(w >> (8 * b));
 }
 
+// 32 x 32 bit transpose across a warp: lane r holds row r (bit c = column c) and
+// gets column r (bit c = row c).  Five butterfly stages; stage s swaps the
+// off-diagonal s x s blocks between lanes r and r ^ s.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t v) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t m[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int i = 0; i < 5; i++) {
+    const int sh = 16 >> i;
+    const uint32_t o = __shfl_xor_sync(0xffffffffu, v, sh);
+    v = (lane & sh) ? ((v & ~m[i]) | ((o >> sh) & m[i])) : ((v & m[i]) | ((o << sh) & ~m[i]));
+  }
+  return v;
+}
+
+// bit b of the result: byte b of a 4-byte flag word (0x80 per flagged byte) is set
+__device__ __forceinline__ uint32_t bits_of4(uint32_t f) { return (((f >> 7) * 0x01020408u) >> 24); }
+
+// The FDSC flags of item `item` (nt samples) from the flag words fm into the
+// mask (the forms other than bit masks from [t][bin] words, which the item
+// writes inline).  Out of line: inlined, these paths raised the register
+// pressure of the item loop into spills.
+__device__ __noinline__ void fd_write_flags(const Params& P, const Job& J, const unsigned* fm, int item, int nt,
+                                            int NB, bool bin_bits) {
+  const int C = J.C, T = J.T, t_item = item * FD_ITEM_T, W32 = (T + 31) >> 5;
+  const unsigned valid = nt >= 32 ? 0xFFFFFFFFu : ((1u << nt) - 1u);
+  if (!J.mask || P.mask_kind == MASK_NONE) return;
+  if (bin_bits) {
+    // per-channel words from the [t][bin] words: a warp per bin, one transpose
+    // each; lane j then holds the word of channel 32 gi + j
+    const int lane = threadIdx.x & 31, NBO = NB | 1;
+    for (int gi = threadIdx.x >> 5; gi < NB; gi += NT / 32) {
+      const unsigned f = warp_transpose32(fm[lane * NBO + gi]) & valid;
+      const int c = gi * 32 + lane;
+      if (c >= C) continue;
+      if (P.mask_kind == MASK_BITS) {
+        unsigned* wp = static_cast<unsigned*>(J.mask) + (size_t)c * W32 + item;
+        if (P.mask_or) {
+          // the word holds this beam's TDSC flags (published before this item
+          // started) and only this item writes its FDSC bits: a reduction that
+          // returns nothing, so the item does not wait for the word
+          if (f) atomicOr(wp, f);
+        } else {
+          *wp = f;
+        }
+      } else {
+        uint8_t* bp = static_cast<uint8_t*>(J.mask) + (size_t)c * T + t_item;
+        for (int t = 0; t < nt; t++) {
+          if (P.mask_or) {
+            if ((f >> t) & 1u) bp[t] = (uint8_t)(__ldcg(bp + t) | 2u);
+          } else {
+            bp[t] = (uint8_t)(((f >> t) & 1u) << 1);
+          }
+        }
+      }
+    }
+  } else if (P.mask_kind == MASK_BITS) {
+    unsigned* mb = static_cast<unsigned*>(J.mask) + item;
+    for (int c = threadIdx.x; c < C; c += NT) {
+      const unsigned f = fm[c] & valid;
+      unsigned* wp = mb + (size_t)c * W32;
+      if (P.mask_or) {
+        if (f) atomicOr(wp, f);  // (as above)
+      } else {
+        *wp = f;
+      }
+    }
+  } else {
+    uint8_t* mb = static_cast<uint8_t*>(J.mask);
+    for (int u = threadIdx.x; u < C * nt; u += NT) {
+      const int c = u / nt, t = u % nt;
+      const unsigned f = (fm[c] >> t) & 1u;
+      uint8_t* bp = mb + (size_t)c * T + t_item + t;
+      if (P.mask_or) {
+        if (f) *bp = (uint8_t)(__ldcg(bp) | 2u);
+      } else {
+        *bp = (uint8_t)(f ? 2u : 0u);
+      }
+    }
+  }
+}
+
 template <bool RND>
 __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned char* smem) {
   const CutDev& cut = P.fd;
@@ -1148,7 +1232,10 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
   const uint8_t* bhi = src + (size_t)C * T;
   const bool words = (G & 3) == 0;  // bins start on 4-byte boundaries of a tile row
   const unsigned long long mf = J.m_full, ml = J.m_last;
-  FdLayout L = fd_layout(smem, Ws, pitch, NB, C);
+  const bool rnd = RND && cut.replace == REP_RANDOM;
+  const bool bin_bits = fd_bin_bits(G, rnd);  // flag bits per (t, bin), see fd_flag_bytes
+  const int NBO = NB | 1;
+  FdLayout L = fd_layout(smem, Ws, pitch, NB, C, bin_bits);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // column ownership: LPC lanes per column, each warp owns 32 / LPC columns
   const int LPC = NT / Ws;  // Ws in {8, 16, 32} -> 32, 16, 8 lanes per column
@@ -1164,8 +1251,7 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
   const unsigned long long multF = (unsigned long long)C * mf * mf;
   const unsigned long long multL = (unsigned long long)C * ml * ml;
 
-  const bool rnd = RND && cut.replace == REP_RANDOM;
-  for (int c = threadIdx.x; c < C; c += NT) L.fmask[c] = 0;
+  for (int i = threadIdx.x, n = bin_bits ? FD_ITEM_T * NBO : C; i < n; i += NT) L.fmask[i] = 0;
   if (rnd)
     for (int c = threadIdx.x; c < C; c += NT) L.fcur[c] = 0;  // each bin clears its own bits after use
 
@@ -1314,13 +1400,20 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
           }
           if (!(lo == 0 && hi == 255)) {
             if (fast32 && gsz == 32) {
+              // exact: sum over the bin of (x - hi)^+ is (f(hi) + S - 32 hi) / 2 and
+              // of (lo - x)^+ is (f(lo) - S + 32 lo) / 2, f(p) the sum of |x - p|
               uint32_t w[8];
               load_bin32(L.tile, tcol, gi, pitch, (sl >> 2) & 1, w);
-              const ByteKeep kp = make_keep(lo, hi);
-              uint32_t acc = 0;
+              const uint32_t h4 = splat4((uint32_t)hi), l4 = splat4((uint32_t)lo);
+              unsigned fh0 = 0, fh1 = 0, fl0 = 0, fl1 = 0;
 #pragma unroll
-              for (int i = 0; i < 8; i++) acc |= outside_fast(w[i], kp);
-              any = (acc & 0x80808080u) != 0;
+              for (int i = 0; i < 8; i += 2) {
+                fh0 = sad4(w[i], h4, fh0);
+                fh1 = sad4(w[i + 1], h4, fh1);
+                fl0 = sad4(w[i], l4, fl0);
+                fl1 = sad4(w[i + 1], l4, fl1);
+              }
+              any = (int)(fh0 + fh1) + (int)S > 32 * hi || (int)(fl0 + fl1) + 32 * lo > (int)S;
             } else if (words) {
               const BinView bv{L.tile, tcol, gi * G, (int)gsz, pitch};
               const ByteKeep kp = make_keep(lo, hi);
@@ -1445,11 +1538,7 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
               L.Sg[t * NBP + gi] = s0 + s1;
               L.Qg[t * NBP + gi] = q0 + q1;
             }
-            while (fbm) {
-              const int j = __ffs(fbm) - 1;
-              fbm &= fbm - 1;
-              atomicOr(&L.fmask[gi * 32 + j], bit);
-            }
+            L.fmask[(t0 - t_item + t) * NBO + gi] |= fbm;  // (this lane alone resolves (t, gi))
           }
           continue;
         }
@@ -1495,11 +1584,15 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
             q_new = dp4a_u(y, y, q_new);
             if (f) {
               bv.word(i) = y;
-              uint32_t ff = f;
-              while (ff) {
-                const int byte = (__ffs(ff) - 1) >> 3;
-                ff &= ff - 1;
-                atomicOr(&L.fmask[gi * G + 4 * i + byte], bit);
+              if (bin_bits) {  // (G = 32: word i holds bin channels 4 i .. 4 i + 3)
+                L.fmask[(t0 - t_item + t) * NBO + gi] |= bits_of4(f) << (4 * i);
+              } else {
+                uint32_t ff = f;
+                while (ff) {
+                  const int byte = (__ffs(ff) - 1) >> 3;
+                  ff &= ff - 1;
+                  atomicOr(&L.fmask[gi * G + 4 * i + byte], bit);
+                }
               }
             }
           }
@@ -1556,35 +1649,31 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
   }
 
   // ---- flags
-  const int nt = t_end - t_item;
-  const unsigned valid = nt >= 32 ? 0xFFFFFFFFu : ((1u << nt) - 1u);
-  if (P.mask_kind == MASK_BITS && J.mask) {
-    const int W32 = (T + 31) >> 5;
-    unsigned* mb = static_cast<unsigned*>(J.mask) + item;
-    for (int c = threadIdx.x; c < C; c += NT) {
-      const unsigned f = L.fmask[c] & valid;
-      unsigned* wp = mb + (size_t)c * W32;
-      if (P.mask_or) {
-        // the word holds this beam's TDSC flags (published before this item
-        // started) and only this item writes its FDSC bits: a reduction that
-        // returns nothing, so the item does not wait for the word
-        if (f) atomicOr(wp, f);
-      } else {
-        *wp = f;
+  if (bin_bits && P.mask_kind == MASK_BITS && J.mask) {
+    // per-channel words from the [t][bin] words: a warp per bin, one transpose
+    // each; lane j then holds the word of channel 32 gi + j
+    const int nt = t_end - t_item, W32 = (T + 31) >> 5;
+    const unsigned valid = nt >= 32 ? 0xFFFFFFFFu : ((1u << nt) - 1u);
+    for (int gi = warp; gi < NB; gi += NT / 32) {
+      const unsigned v = L.fmask[lane * NBO + gi];
+      const bool any = __any_sync(0xffffffffu, v != 0u);  // (a bin with no flag in the item skips the transpose)
+      if (!any && P.mask_or) continue;
+      const unsigned f = any ? warp_transpose32(v) & valid : 0u;
+      const int c = gi * 32 + lane;
+      if (c < C) {
+        unsigned* wp = static_cast<unsigned*>(J.mask) + (size_t)c * W32 + item;
+        if (P.mask_or) {
+          // the word holds this beam's TDSC flags (published before this item
+          // started) and only this item writes its FDSC bits: a reduction that
+          // returns nothing, so the item does not wait for the word
+          if (f) atomicOr(wp, f);
+        } else {
+          *wp = f;
+        }
       }
     }
-  } else if (P.mask_kind == MASK_BYTES && J.mask) {
-    uint8_t* mb = static_cast<uint8_t*>(J.mask);
-    for (int u = threadIdx.x; u < C * nt; u += NT) {
-      const int c = u / nt, t = u % nt;
-      const unsigned f = (L.fmask[c] >> t) & 1u;
-      uint8_t* bp = mb + (size_t)c * T + t_item + t;
-      if (P.mask_or) {
-        if (f) *bp = (uint8_t)(__ldcg(bp) | 2u);
-      } else {
-        *bp = (uint8_t)(f ? 2u : 0u);
-      }
-    }
+  } else {
+    fd_write_flags(P, J, L.fmask, item, t_end - t_item, NB, bin_bits);
   }
   __syncthreads();
 }
