@@ -54,6 +54,14 @@
  * shared memory (uint8 up to the 372,181 bound above, float32 up to 921,600
  * samples; RFIM_ERR_ARG beyond).
  *
+ * Column heights: FDSC cleans tiles of 8 to 32 time samples x all channels in
+ * shared memory.  Beams whose tile does not fit (uint8: about 14,700 channels
+ * in 32-channel bins; float32: about 26,700) are cleaned one column at a time,
+ * the column gathered into shared memory (slower, same results), up to 115,200
+ * uint8 or 49,800 float32 channels in 32-channel bins (fewer with smaller bins:
+ * per bin the column layout keeps its sums and replacement value);
+ * RFIM_ERR_RANGE beyond.
+ *
  * Conventions for every call below:
  *   - Pointers inside rfim_block are DEVICE pointers owned by the caller,
  *     except for rfim_clean_host.  `out == in` cleans in place; any other
@@ -80,7 +88,8 @@ extern "C" {
 typedef enum {
   RFIM_OK = 0,
   RFIM_ERR_ARG = 1,     /* invalid argument (null pointer, bad size, bad enum, overlap) */
-  RFIM_ERR_RANGE = 2,   /* shape outside the exact-integer range of the uint8 decisions */
+  RFIM_ERR_RANGE = 2,   /* shape outside the exact-integer range of the uint8 decisions, or a
+                           column too tall for shared memory (see "Column heights") */
   RFIM_ERR_OOM = 3,     /* a device or pinned-host allocation failed */
   RFIM_ERR_CUDA = 4,    /* a CUDA runtime call failed (message in rfim_last_error) */
   RFIM_ERR_TIMEOUT = 5, /* a bounded device-side wait gave up (see rfim_device_status) */

@@ -215,9 +215,11 @@ rfim_status check_impl(rfim_ctx* ctx, const rfim_block* b, const CutNorm& td, co
       return fail(ctx, RFIM_ERR_ARG, "float32 TDSC with random replacement: rows longer than %d samples are not "
                   "supported", (MAX_SMEM_PER_CTA / 8) * 32);
     if (fd.on) {
+      // the tile of one sample, else the column-at-a-time layout, must fit a CTA's shared memory
       const int C = b->channels, nb = (C + fd.bin - 1) / fd.bin;
-      if (fd32_smem_bytes(1, C, nb, fd.rep == RFIM_REPLACE_RANDOM) > MAX_SMEM_PER_CTA)
-        return fail(ctx, RFIM_ERR_RANGE, "FDSC: %d float32 channels do not fit the on-chip tile", C);
+      if (fd32_smem_bytes(1, C, nb, fd.rep == RFIM_REPLACE_RANDOM) > MAX_SMEM_PER_CTA &&
+          fd_wide_smem_f32(C, nb) > MAX_SMEM_PER_CTA)
+        return fail(ctx, RFIM_ERR_RANGE, "FDSC: a column of %d float32 channels does not fit shared memory", C);
     }
     return RFIM_OK;
   }
@@ -226,10 +228,12 @@ rfim_status check_impl(rfim_ctx* ctx, const rfim_block* b, const CutNorm& td, co
   if (td.on && td.rep == RFIM_REPLACE_RANDOM && td_random_row_mode(b->samples) < 0)
     return fail(ctx, RFIM_ERR_ARG, "uint8 TDSC with random replacement: the row's flag bitmaps do not fit");
   if (fd.on) {
-    // the smallest FDSC tile (8 samples x all channels) must fit one CTA's shared memory
+    // the smallest FDSC tile (8 samples x all channels), else the column-at-a-time
+    // layout, must fit one CTA's shared memory
     const int C = b->channels, nb = (C + fd.bin - 1) / fd.bin;
-    if (fd_smem_bytes(8, fd_pitch(C), nb, C, fd.rep == RFIM_REPLACE_RANDOM, fd.bin) > MAX_SMEM_PER_CTA)
-      return fail(ctx, RFIM_ERR_RANGE, "FDSC: %d channels do not fit the on-chip tile", C);
+    if (fd_smem_bytes(8, fd_pitch(C), nb, C, fd.rep == RFIM_REPLACE_RANDOM, fd.bin) > MAX_SMEM_PER_CTA &&
+        fd_wide_smem_u8(C, nb) > MAX_SMEM_PER_CTA)
+      return fail(ctx, RFIM_ERR_RANGE, "FDSC: a column of %d channels does not fit shared memory", C);
   }
   return RFIM_OK;
 }
@@ -298,6 +302,12 @@ Job make_job(const rfim_block* b, int j, const CutNorm& fd, int tile_samples, in
         break;
       }
     J.fd_items = (T + J.ws - 1) / J.ws;
+    if (fd.on && fd32_smem_bytes(1, C, J.nb, fd.rep == RFIM_REPLACE_RANDOM) > MAX_SMEM_PER_CTA) {
+      J.fd_wide = 1;  // columns one at a time, 32 samples per item
+      J.fd_items = (T + FD_ITEM_T - 1) / FD_ITEM_T;
+    }
+  } else if (fd.on && fd_smem_bytes(8, J.pitch, J.nb, C, fd.rep == RFIM_REPLACE_RANDOM, G) > MAX_SMEM_PER_CTA) {
+    J.fd_wide = 1;  // columns one at a time
   }
   return J;
 }

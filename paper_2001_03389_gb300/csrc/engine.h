@@ -49,6 +49,7 @@ struct Job {
                     //          2 = one row per item, read from global memory in every pass (no stage)
   int td_items;     // number of TDSC work items
   int beam;         // index of the beam within its block (keys the random-replacement draws)
+  int fd_wide;      // 1: the FDSC tile does not fit; each item cleans its columns one at a time (fd_wide_*)
   double* stats;    // or null: per row, the sum and the sum of squares of the input row ([2 * row], [2 * row + 1]),
                     // written by the first TDSC iteration (the streaming service's per-beam state)
   float* prog;      // or null (float32, fused launches with a bit mask, option "f32_records"): per row and
@@ -111,6 +112,19 @@ __host__ __device__ inline int fd_smem_bytes(int ws, int pitch, int nb, int C, b
   return ws * pitch + 2 * align16i(ws * nbp * 4) + align16i(ws * nbp * 2) + align16i(ws * 8) + align16i(ws * 8) +
          fd_flag_bytes(C, nb, fd_bin_bits(bin, rnd)) + align16i(ws * nb * 4) + 4 * (NT / 32) +
          (rnd ? align16i(C * 4) : 0);
+}
+
+// FDSC on columns wider than the tile: a CTA cleans one column (time sample)
+// at a time, holding the column, two flag bits per channel (this iteration's,
+// and the OR over iterations) and per-bin sums, keep intervals and replacement
+// values.
+__host__ __device__ inline int fd_wide_smem_u8(int C, int nb) {
+  const int W = (C + 31) / 32;
+  return align16i(C) + 2 * align16i(W * 4) + 2 * align16i(nb * 8) + 2 * align16i(nb * 4);
+}
+__host__ __device__ inline int fd_wide_smem_f32(int C, int nb) {
+  const int W = (C + 31) / 32;
+  return align16i(C * 4) + 2 * align16i(W * 4) + align16i(nb * 8) + align16i(nb * 4);
 }
 
 // Tile row pitch: C bytes rounded up to 128, so that the XOR swizzle of the 16-byte

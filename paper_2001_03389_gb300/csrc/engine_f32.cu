@@ -853,6 +853,137 @@ __device__ float bin_median_f32(const float* tile, int c0, int n, int ws, int t)
   return key_f(prefix);
 }
 
+// ---------------------------------------------------------------------------
+// FDSC on float32 columns wider than the tile: the CTA cleans the item's time
+// samples one column at a time.  The column is gathered into shared memory
+// (read through L2), cleaned there and scattered back; the flags are bits per
+// channel.  The column statistics are taken in FP64 (bin means, deviations
+// from them, their mean and spread), the decisions |d - mu| > k sigma' in FP64
+// as well.  A warp takes a bin for the means and the medians, 32 channels for
+// the flags and replacements.  Out of line: such beams are rare.
+// ---------------------------------------------------------------------------
+template <bool RND>
+__device__ __noinline__ void fdsc_wide_f32(const Params& P, const Job& J, int item, unsigned char* smem, Red32* red) {
+  const CutDev& cut = P.fd;
+  const int C = J.C, T = J.T, G = cut.bin, NB = J.nb;
+  const int W = (C + 31) >> 5, W32 = (T + 31) >> 5, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int t_item = item * FD_ITEM_T, t_end = min(t_item + FD_ITEM_T, T);
+  const float* src = static_cast<const float*>(P.fd_reads_out ? J.out : J.in);
+  float* dst = static_cast<float*>(J.out);
+  unsigned char* p = smem;
+  float* x = reinterpret_cast<float*>(p);  // the column
+  p += align16i(C * 4);
+  unsigned* fcur = reinterpret_cast<unsigned*>(p);  // flags of this iteration, bit c % 32 of word c / 32
+  p += align16i(W * 4);
+  unsigned* facc = reinterpret_cast<unsigned*>(p);  // flags of every iteration so far
+  p += align16i(W * 4);
+  double* mb = reinterpret_cast<double*>(p);  // per bin: mean
+  p += align16i(NB * 8);
+  float* rep = reinterpret_cast<float*>(p);  // replacement value
+  const bool rnd = RND && cut.replace == REP_RANDOM;
+  const double rC = 1.0 / (double)C;
+  // this item's mask words start from zero unless they hold the beam's TDSC flags
+  if (J.mask && P.mask_kind == MASK_BITS && !P.mask_or)
+    for (int c = t; c < C; c += NT) static_cast<unsigned*>(J.mask)[(size_t)c * W32 + item] = 0u;
+  for (int tc = t_item; tc < t_end; tc++) {
+    for (int c = t; c < C; c += NT) x[c] = src[(size_t)c * T + tc];
+    for (int w = t; w < W; w += NT) facc[w] = 0u;
+    __syncthreads();
+    const unsigned long long key = draw_key(J.beam, tc);
+    for (int it = 0; it < cut.iterations; it++) {
+      for (int g = warp; g < NB; g += NT / 32) {
+        const int c0 = g * G, c1 = min(c0 + G, C);
+        double s = 0.0;
+        for (int c = c0 + lane; c < c1; c += 32) s += (double)x[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+          mb[g] = s / (double)(c1 - c0);
+          rep[g] = (float)mb[g];  // (the mean; medians below)
+        }
+      }
+      __syncthreads();
+      double sd = 0.0;
+      for (int c = t; c < C; c += NT) sd += (double)x[c] - mb[c / G];
+      const double mu = grp_dsum<NT>(sd, red, t, 0) * rC;
+      double ss = 0.0;
+      for (int c = t; c < C; c += NT) {
+        const double e = ((double)x[c] - mb[c / G]) - mu;
+        ss += e * e;
+      }
+      const double thr = cut.k * sqrt(grp_dsum<NT>(ss, red, t, 0) * rC);
+      for (int w = warp; w < W; w += NT / 32) {
+        const int c = 32 * w + lane;
+        const bool f = c < C && fabs(((double)x[c] - mb[c / G]) - mu) > thr;
+        const unsigned bits = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) fcur[w] = bits;
+      }
+      __syncthreads();
+      if (cut.replace == REP_MEDIAN) {
+        // lower median of each bin with a flag: radix select on order-preserving keys
+        for (int g = warp; g < NB; g += NT / 32) {
+          const int c0 = g * G, c1 = min(c0 + G, C);
+          bool any = false;
+          for (int c = c0 + lane; c < c1; c += 32) any |= ((fcur[c >> 5] >> (c & 31)) & 1u) != 0u;
+          if (!__any_sync(0xffffffffu, any)) continue;
+          const int rank = (c1 - c0 - 1) >> 1;
+          unsigned prefix = 0;
+          for (int b = 31; b >= 0; b--) {
+            const unsigned test = prefix | (1u << b);
+            unsigned cnt = 0;
+            for (int c = c0 + lane; c < c1; c += 32) cnt += fkey(x[c]) < test ? 1u : 0u;
+            cnt = __reduce_add_sync(0xffffffffu, cnt);
+            if ((int)cnt <= rank) prefix = test;
+          }
+          if (lane == 0) rep[g] = key_f(prefix);
+        }
+        __syncthreads();
+      }
+      // replace; a draw copies an unflagged value, which no thread writes in this iteration
+      for (int w = warp; w < W; w += NT / 32) {
+        const int c = 32 * w + lane;
+        const unsigned fw = fcur[w];
+        if (c < C && ((fw >> lane) & 1u)) {
+          const int g = c / G;
+          float y = x[c];
+          if (rnd) {
+            const int c0 = g * G;
+            const unsigned gs = (unsigned)(min(c0 + G, C) - c0);
+            for (int a = 0; a < DRAW_ATTEMPTS; a++) {
+              const int u = c0 + (int)draw_pos(key, c, 2, cut.it0 + it, a, gs);
+              if (!((fcur[u >> 5] >> (u & 31)) & 1u)) {
+                y = x[u];
+                break;
+              }
+            }
+          } else {
+            y = rep[g];
+          }
+          x[c] = y;
+        }
+        if (lane == 0) facc[w] |= fw;
+      }
+      __syncthreads();
+    }
+    for (int c = t; c < C; c += NT) {
+      dst[(size_t)c * T + tc] = x[c];
+      const bool f = ((facc[c >> 5] >> (c & 31)) & 1u) != 0u;
+      if (!J.mask) continue;
+      if (P.mask_kind == MASK_BITS) {
+        if (f) atomicOr(static_cast<unsigned*>(J.mask) + (size_t)c * W32 + item, 1u << (tc - t_item));
+      } else if (P.mask_kind == MASK_BYTES) {
+        unsigned char* bp = static_cast<unsigned char*>(J.mask) + (size_t)c * T + tc;
+        if (P.mask_or) {
+          if (f) *bp = (unsigned char)(__ldcg(bp) | 2u);
+        } else {
+          *bp = (unsigned char)(f ? 2u : 0u);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 template <bool RND>
 __device__ void fdsc_item_f32(const Params& P, const Job& J, int item, unsigned char* smem, Red32* red) {
   const CutDev& cut = P.fd;
@@ -1255,7 +1386,8 @@ __global__ void __launch_bounds__(NT, 2) k_engine_f32(const __grid_constant__ Pa
       }
     } else {
       if (P.wait_tdsc && !wait_rows_f32(P, sg.job, (unsigned)J.rows, &s_flag)) continue;
-      fdsc_item_f32<RND>(P, J, idx, smem, &red[0]);
+      if (J.fd_wide) fdsc_wide_f32<RND>(P, J, idx, smem, &red[0]);
+      else fdsc_item_f32<RND>(P, J, idx, smem, &red[0]);
     }
   }
 }
@@ -1273,7 +1405,8 @@ int engine_smem_f32(const Params& p) {
       s = s > td ? s : td;
     }
     if (p.fd.iterations > 0) {
-      const int fd = fd32_smem_bytes(J.ws, J.C, J.nb, p.fd.replace == REP_RANDOM, J.prog != nullptr);
+      const int fd = J.fd_wide ? fd_wide_smem_f32(J.C, J.nb)
+                               : fd32_smem_bytes(J.ws, J.C, J.nb, p.fd.replace == REP_RANDOM, J.prog != nullptr);
       s = s > fd ? s : fd;
     }
   }

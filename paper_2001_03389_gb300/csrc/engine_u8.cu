@@ -22,7 +22,8 @@ int engine_smem_u8(const Params& p) {
       s = s > td ? s : td;
     }
     if (p.fd.iterations > 0) {
-      const int fd = fd_smem_bytes(J.ws, J.pitch, J.nb, J.C, p.fd.replace == REP_RANDOM, p.fd.bin);
+      const int fd = J.fd_wide ? fd_wide_smem_u8(J.C, J.nb)
+                               : fd_smem_bytes(J.ws, J.pitch, J.nb, J.C, p.fd.replace == REP_RANDOM, p.fd.bin);
       s = s > fd ? s : fd;
     }
   }

@@ -1679,6 +1679,164 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
 }
 
 // ---------------------------------------------------------------------------
+// FDSC on columns wider than the tile: the CTA cleans the item's time samples
+// one column at a time.  The column is gathered into shared memory (one byte
+// per channel row, read through L2), cleaned there with the same exact integer
+// decisions as the tile path, and scattered back; the flags are bits per
+// channel.  A warp takes a bin for the sums and the medians, 32 channels for
+// the flags and replacements.  Out of line: such beams are rare.
+// ---------------------------------------------------------------------------
+template <bool RND>
+__device__ __noinline__ void fdsc_wide_u8(const Params& P, const Job& J, int item, unsigned char* smem,
+                                          unsigned long long* scr) {
+  const CutDev& cut = P.fd;
+  const int C = J.C, T = J.T, G = cut.bin, NB = J.nb, Gl = J.last_g;
+  const int W = (C + 31) >> 5, W32 = (T + 31) >> 5, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int t_item = item * FD_ITEM_T, t_end = min(t_item + FD_ITEM_T, T);
+  const uint8_t* src = static_cast<const uint8_t*>(P.fd_reads_out ? J.out : J.in);
+  uint8_t* dst = static_cast<uint8_t*>(J.out);
+  unsigned char* p = smem;
+  uint8_t* x = p;  // the column
+  p += align16i(C);
+  unsigned* fcur = reinterpret_cast<unsigned*>(p);  // flags of this iteration, bit c % 32 of word c / 32
+  p += align16i(W * 4);
+  unsigned* facc = reinterpret_cast<unsigned*>(p);  // flags of every iteration so far
+  p += align16i(W * 4);
+  unsigned long long* Sb = reinterpret_cast<unsigned long long*>(p);  // per bin: sum
+  p += align16i(NB * 8);
+  unsigned long long* Qb = reinterpret_cast<unsigned long long*>(p);  // sum of squares
+  p += align16i(NB * 8);
+  unsigned* lh = reinterpret_cast<unsigned*>(p);  // keep interval, lo | hi << 16
+  p += align16i(NB * 4);
+  unsigned* rep = reinterpret_cast<unsigned*>(p);  // replacement value
+  const bool rnd = RND && cut.replace == REP_RANDOM;
+  const unsigned long long mf = J.m_full, ml = J.m_last;
+  const unsigned long long multF = (unsigned long long)C * mf * mf, multL = (unsigned long long)C * ml * ml;
+  const float rcpG = 1.0f / (float)G, rcpL = 1.0f / (float)Gl;
+  // this item's mask words start from zero unless they hold the beam's TDSC flags
+  if (J.mask && P.mask_kind == MASK_BITS && !P.mask_or)
+    for (int c = threadIdx.x; c < C; c += NT) static_cast<unsigned*>(J.mask)[(size_t)c * W32 + item] = 0u;
+  for (int t = t_item; t < t_end; t++) {
+    for (int c = threadIdx.x; c < C; c += NT) x[c] = src[(size_t)c * T + t];
+    for (int w = threadIdx.x; w < W; w += NT) facc[w] = 0u;
+    __syncthreads();
+    const unsigned long long key = draw_key(J.beam, t);
+    for (int it = 0; it < cut.iterations; it++) {
+      for (int g = warp; g < NB; g += NT / 32) {
+        const int c0 = g * G, c1 = min(c0 + G, C);
+        unsigned long long s = 0, q = 0;
+        for (int c = c0 + lane; c < c1; c += 32) {
+          const unsigned v = x[c];
+          s += v;
+          q += v * v;
+        }
+        s = warp_sum(s);
+        q = warp_sum(q);
+        if (lane == 0) {
+          Sb[g] = s;
+          Qb[g] = q;
+        }
+      }
+      __syncthreads();
+      // sum over the column of D^2 = sum over bins of m^2 G (G Q - S^2)
+      unsigned long long v[1] = {0};
+      for (int g = threadIdx.x; g < NB; g += NT) {
+        const bool last = g == NB - 1;
+        const unsigned long long gs = last ? (unsigned)Gl : (unsigned)G, m = last ? ml : mf;
+        v[0] += m * m * gs * (gs * Qb[g] - Sb[g] * Sb[g]);
+      }
+      grp_sum<NT, 1>(v, scr);
+      const unsigned long long F = thr_floor(v[0], cut.k2);
+      const unsigned Af = max_keep_grp<32>(F, multF, 255u * (unsigned)G);
+      const unsigned Al = Gl == G ? Af : max_keep_grp<32>(F, multL, 255u * (unsigned)Gl);
+      for (int g = threadIdx.x; g < NB; g += NT) {
+        const bool last = g == NB - 1;
+        const unsigned gs = last ? (unsigned)Gl : (unsigned)G;
+        int lo, hi;
+        keep_from((unsigned)Sb[g], last ? Al : Af, gs, last ? rcpL : rcpG, lo, hi);
+        lh[g] = (unsigned)lo | ((unsigned)hi << 16);
+        rep[g] = udiv_q((unsigned)(2 * Sb[g] + gs), 2u * gs, 0.5f * (last ? rcpL : rcpG));  // the mean
+      }
+      __syncthreads();
+      for (int w = warp; w < W; w += NT / 32) {
+        const int c = 32 * w + lane;
+        bool f = false;
+        if (c < C) {
+          const unsigned b = lh[c / G];
+          const int xv = x[c];
+          f = xv < (int)(b & 0xFFFFu) || xv > (int)(b >> 16);
+        }
+        const unsigned bits = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) fcur[w] = bits;
+      }
+      __syncthreads();
+      if (cut.replace == REP_MEDIAN) {
+        // lower median of each bin with a flag: bisection on counts
+        for (int g = warp; g < NB; g += NT / 32) {
+          const int c0 = g * G, c1 = min(c0 + G, C);
+          bool any = false;
+          for (int c = c0 + lane; c < c1; c += 32) any |= ((fcur[c >> 5] >> (c & 31)) & 1u) != 0u;
+          if (!__any_sync(0xffffffffu, any)) continue;
+          const int need = (c1 - c0 + 1) >> 1;
+          int lo = 0, hi = 255;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            unsigned cnt = 0;
+            for (int c = c0 + lane; c < c1; c += 32) cnt += x[c] <= mid ? 1u : 0u;
+            cnt = __reduce_add_sync(0xffffffffu, cnt);
+            if ((int)cnt >= need) hi = mid;
+            else lo = mid + 1;
+          }
+          if (lane == 0) rep[g] = (unsigned)lo;
+        }
+        __syncthreads();
+      }
+      // replace; a draw copies an unflagged value, which no thread writes in this iteration
+      for (int w = warp; w < W; w += NT / 32) {
+        const int c = 32 * w + lane;
+        const unsigned fw = fcur[w];
+        if (c < C && ((fw >> lane) & 1u)) {
+          const int g = c / G;
+          unsigned y = x[c];
+          if (rnd) {
+            const int c0 = g * G;
+            const unsigned gs = g == NB - 1 ? (unsigned)Gl : (unsigned)G;
+            for (int a = 0; a < DRAW_ATTEMPTS; a++) {
+              const int u = c0 + (int)draw_pos(key, c, 2, cut.it0 + it, a, gs);
+              if (!((fcur[u >> 5] >> (u & 31)) & 1u)) {
+                y = x[u];
+                break;
+              }
+            }
+          } else {
+            y = rep[g];
+          }
+          x[c] = (uint8_t)y;
+        }
+        if (lane == 0) facc[w] |= fw;
+      }
+      __syncthreads();
+    }
+    for (int c = threadIdx.x; c < C; c += NT) {
+      dst[(size_t)c * T + t] = x[c];
+      const bool f = ((facc[c >> 5] >> (c & 31)) & 1u) != 0u;
+      if (!J.mask) continue;
+      if (P.mask_kind == MASK_BITS) {
+        if (f) atomicOr(static_cast<unsigned*>(J.mask) + (size_t)c * W32 + item, 1u << (t - t_item));
+      } else if (P.mask_kind == MASK_BYTES) {
+        uint8_t* bp = static_cast<uint8_t*>(J.mask) + (size_t)c * T + t;
+        if (P.mask_or) {
+          if (f) *bp = (uint8_t)(__ldcg(bp) | 2u);
+        } else {
+          *bp = (uint8_t)(f ? 2u : 0u);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // persistent engine
 // ---------------------------------------------------------------------------
 __device__ bool wait_rows(const Params& P, int job, unsigned need, int* flag) {
@@ -1880,7 +2038,8 @@ __global__ void __launch_bounds__(NT, MINB) k_engine_u8(const __grid_constant__ 
       }
     } else {
       if (P.wait_tdsc && !wait_rows(P, sg.job, (unsigned)J.rows, &s_flag)) continue;
-      fdsc_item_u8<RND>(P, J, idx, smem);
+      if (J.fd_wide) fdsc_wide_u8<RND>(P, J, idx, smem, scr);
+      else fdsc_item_u8<RND>(P, J, idx, smem);
     }
   }
 }

@@ -97,7 +97,7 @@ def test_fdsc_channel_limit(ctx):
 
     from paper_2001_03389_gb300 import rfim
 
-    x = torch.zeros((1, 40000, 8), dtype=torch.uint8, device="cuda:0")
+    x = torch.zeros((1, 120000, 8), dtype=torch.uint8, device="cuda:0")  # beyond the column-at-a-time layout too
     with pytest.raises(rfim.RfimError) as e:
         ctx.fdsc(ctx.block(x, torch.empty_like(x)), rfim.make_cut(3.0, bin=32))
     assert e.value.status == rfim.ERR_RANGE

@@ -318,7 +318,7 @@ def test_f32_validation(ctx):
     with pytest.raises(rfim.RfimError) as e:  # random replacement: the row's flag bitmaps do not fit
         ctx.tdsc(ctx.block(row, torch.empty_like(row)), rfim.make_cut(3.0, replace="random"))
     assert e.value.status == rfim.ERR_ARG
-    big = torch.zeros((1, 40000, 4), dtype=torch.float32, device="cuda:0")
+    big = torch.zeros((1, 60000, 4), dtype=torch.float32, device="cuda:0")  # beyond the column-at-a-time layout too
     with pytest.raises(rfim.RfimError) as e:
         ctx.fdsc(ctx.block(big, torch.empty_like(big)), rfim.make_cut(3.0, bin=32))
     assert e.value.status == rfim.ERR_RANGE
