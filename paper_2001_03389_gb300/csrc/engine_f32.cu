@@ -177,6 +177,24 @@ __device__ __forceinline__ bool flag32(float y, const Cut32& c) {
   return flag64(y, c.mu_f, c.mu_lo, c.thr_hi, c.thr_lo);
 }
 
+// flag32 on four samples at once, bit i for sample i: the float32 tests of all
+// four first, and one branch to the FP64 expression when any lies in its band.
+__device__ __forceinline__ unsigned flag32x4(const float4& v, const Cut32& c0, const Cut32& c1, const Cut32& c2,
+                                             const Cut32& c3) {
+  const float a0 = fabsf(__fsub_rn(v.x, c0.mu_f)), a1 = fabsf(__fsub_rn(v.y, c1.mu_f));
+  const float a2 = fabsf(__fsub_rn(v.z, c2.mu_f)), a3 = fabsf(__fsub_rn(v.w, c3.mu_f));
+  unsigned f = (a0 > c0.hi_f ? 1u : 0u) | (a1 > c1.hi_f ? 2u : 0u) | (a2 > c2.hi_f ? 4u : 0u) | (a3 > c3.hi_f ? 8u : 0u);
+  const unsigned band =
+      ((a0 > c0.lo_f ? 1u : 0u) | (a1 > c1.lo_f ? 2u : 0u) | (a2 > c2.lo_f ? 4u : 0u) | (a3 > c3.lo_f ? 8u : 0u)) & ~f;
+  if (band) {
+    if ((band & 1u) && flag64(v.x, c0.mu_f, c0.mu_lo, c0.thr_hi, c0.thr_lo)) f |= 1u;
+    if ((band & 2u) && flag64(v.y, c1.mu_f, c1.mu_lo, c1.thr_hi, c1.thr_lo)) f |= 2u;
+    if ((band & 4u) && flag64(v.z, c2.mu_f, c2.mu_lo, c2.thr_hi, c2.thr_lo)) f |= 4u;
+    if ((band & 8u) && flag64(v.w, c3.mu_f, c3.mu_lo, c3.thr_hi, c3.thr_lo)) f |= 8u;
+  }
+  return f;
+}
+
 // The cut of mean mu and threshold thr (float-float, mu normalised so that
 // |mu - mu.hi| = |mu.lo|).
 __device__ __forceinline__ Cut32 make_cut32(FF mu, FF thr) {
@@ -492,18 +510,15 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
     for (int k = t; k < nch; k += GN) {
       float4 v = st[k];
       const int lo = k == 0 ? head : 0, hi = k == nch - 1 ? tail : 4;
-      unsigned nib = 0;
-#pragma unroll
-      for (int i = 0; i < 4; i++) {
-        const float y = f4_get(v, i);
-        if (i >= lo && i < hi && flag32(y, c)) {
-          nib |= 1u << i;
-          f4_set(v, i, r);
-          const int pos = atomicAdd(&s_nlist, 1);
-          if (pos < TD32_LIST) lst[pos] = y;
-        }
-      }
+      const unsigned nib = flag32x4(v, c, c, c, c) & (0xFu << lo) & (0xFu >> (4 - hi));
       if (nib) {
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+          if (!((nib >> i) & 1u)) continue;
+          const int pos = atomicAdd(&s_nlist, 1);
+          if (pos < TD32_LIST) lst[pos] = f4_get(v, i);
+          f4_set(v, i, r);
+        }
         st[k] = v;
         fl4[k] |= (unsigned char)nib;
       }
@@ -1192,12 +1207,12 @@ __device__ void fdsc_item_f32(const Params& P, const Job& J, int item, unsigned 
           for (int j = 0; j < 16; j++) {
             const int c = c0 + ((j + rot) & 15);
             float4 v = tile4[c];
-            unsigned nib = 0;
-            if (flag32(v.x, cc[0])) { v.x = cc[0].mu_f; nib |= 1u; }
-            if (flag32(v.y, cc[1])) { v.y = cc[1].mu_f; nib |= 2u; }
-            if (flag32(v.z, cc[2])) { v.z = cc[2].mu_f; nib |= 4u; }
-            if (flag32(v.w, cc[3])) { v.w = cc[3].mu_f; nib |= 8u; }
+            const unsigned nib = flag32x4(v, cc[0], cc[1], cc[2], cc[3]);
             if (nib) {
+              if (nib & 1u) v.x = cc[0].mu_f;
+              if (nib & 2u) v.y = cc[1].mu_f;
+              if (nib & 4u) v.z = cc[2].mu_f;
+              if (nib & 8u) v.w = cc[3].mu_f;
               tile4[c] = v;
               L.fm[c] |= nib << sh;
             }
