@@ -478,10 +478,7 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
       for (int k = t; k < nch; k += GN) {
         const float4 v = st[k];
         const int lo = k == 0 ? head : 0, hi = k == nch - 1 ? tail : 4;
-        unsigned nib = 0;
-#pragma unroll
-        for (int i = 0; i < 4; i++)
-          if (i >= lo && i < hi && flag32(f4_get(v, i), c)) nib |= 1u << i;
+        const unsigned nib = flag32x4(v, c, c, c, c) & (0xFu << lo) & (0xFu >> (4 - hi));
         fl4[k] = (unsigned char)((fl4[k] & 0xFu) | nib | (nib << 4));
       }
       gsync<GN>(h);
