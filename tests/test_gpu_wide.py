@@ -74,6 +74,28 @@ def test_wide_clean_u8(oracle, ctx, mask_fmt):
     assert (wf & 1).any() and (wf & 2).any()
 
 
+def test_wide_btc_and_interleaved_u8(oracle, ctx):
+    # tall columns through the BTC scratch copy, and in the interleaved order
+    # (one iteration of each method per round, single-iteration launches)
+    rng = np.random.default_rng(91)
+    x = rfi_cols_u8(rng, (2, 16000, 48))
+    td = dict(k=2.5, iterations=2, replace="median")
+    fd = dict(k=2.5, iterations=2, replace="median", bin=32)
+    want, wf = oracle.clean(x, "bct", tdsc=td, fdsc=fd)
+    xt = np.ascontiguousarray(x.transpose(0, 2, 1))
+    got, gf = run_gpu(ctx, xt, layout="btc", tdsc=td, fdsc=fd, mask_fmt="bytes")
+    assert np.array_equal(got.transpose(0, 2, 1), want)
+    assert np.array_equal(gf.transpose(0, 2, 1), wf)
+    try:
+        ctx.set_option("order", 1)
+        want, wf = oracle.clean(x, "bct", tdsc=td, fdsc=fd, order="interleaved")
+        got, gf = run_gpu(ctx, x, tdsc=td, fdsc=fd)
+        assert np.array_equal(got, want)
+        assert np.array_equal(gf, wf > 0)
+    finally:
+        ctx.set_option("order", 0)
+
+
 def check_f32(oracle, ctx, x, td, fd, api="clean"):
     want, wf, margin = oracle.clean_f32_margin(x, "bct", tdsc=td, fdsc=fd)
     got, gf = run_gpu(ctx, x, tdsc=td, fdsc=fd, api=api)
