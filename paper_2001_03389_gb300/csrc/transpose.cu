@@ -34,33 +34,40 @@ __global__ void __launch_bounds__(256) k_transpose(const E* __restrict__ in, E* 
 }
 
 // Bytes, when rows and cols are multiples of 4 and the planes 4-byte aligned:
-// 64 x 64 tiles.  A thread loads a 4 x 4 block as four row words (16 lanes
-// read 64 contiguous bytes of a row), transposes it in registers (byte
-// permutes) and leaves the four column words in shared memory, from where 16
-// lanes store 64 contiguous bytes of an output row.
+// tiles of 64 columns x 256 rows.  A thread loads four 4 x 4 blocks as row
+// words (16 lanes read 64 contiguous bytes of a row; all 16 loads in flight),
+// transposes each in registers (byte permutes) and leaves the column words in
+// shared memory, from where 32 lanes store 128 contiguous bytes of an output
+// row.
+constexpr int TR_ROWS = 256;  // rows of a tile
 __global__ void __launch_bounds__(256) k_transpose_u8x4(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
                                                         int rows, int cols) {
-  __shared__ uint32_t tile[64][17];  // [column within the tile][row quad]; +1 word against bank conflicts
+  __shared__ uint32_t tile[64][TR_ROWS / 4 + 1];  // [column within the tile][row quad]; +1 word against bank conflicts
   const size_t plane = (size_t)rows * cols;
   const uint8_t* src = in + (size_t)blockIdx.z * plane;
   uint8_t* dst = out + (size_t)blockIdx.z * plane;
-  const int c0 = blockIdx.x * 64, r0 = blockIdx.y * 64;
+  const int c0 = blockIdx.x * 64, r0 = blockIdx.y * TR_ROWS;
   const int cq = threadIdx.x & 15, rq = threadIdx.x >> 4;
   const int c = c0 + 4 * cq;
-  uint32_t w[4];
+  uint32_t w[4][4];
 #pragma unroll
-  for (int j = 0; j < 4; j++) {
-    const int r = r0 + 4 * rq + j;
-    w[j] = (r < rows && c < cols) ? __ldg(reinterpret_cast<const uint32_t*>(src + (size_t)r * cols + c)) : 0u;
+  for (int p = 0; p < 4; p++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const int r = r0 + 4 * (rq + 16 * p) + j;
+      w[p][j] = (r < rows && c < cols) ? __ldg(reinterpret_cast<const uint32_t*>(src + (size_t)r * cols + c)) : 0u;
+    }
+#pragma unroll
+  for (int p = 0; p < 4; p++) {
+    transpose4x4(w[p][0], w[p][1], w[p][2], w[p][3]);  // w[p][i]: column c + i, rows r0 + 4 (rq + 16 p) .. + 3
+#pragma unroll
+    for (int i = 0; i < 4; i++) tile[4 * cq + i][rq + 16 * p] = w[p][i];
   }
-  transpose4x4(w[0], w[1], w[2], w[3]);  // w[i]: column c + i, rows r0 + 4 rq .. + 3
-#pragma unroll
-  for (int i = 0; i < 4; i++) tile[4 * cq + i][rq] = w[i];
   __syncthreads();
-  const int wq = threadIdx.x & 15, r = r0 + 4 * wq;
+  const int wq = threadIdx.x & 63, r = r0 + 4 * wq;
 #pragma unroll
-  for (int k = 0; k < 4; k++) {
-    const int cc = (threadIdx.x >> 4) + 16 * k, oc = c0 + cc;
+  for (int k = 0; k < 16; k++) {
+    const int cc = (threadIdx.x >> 6) + 4 * k, oc = c0 + cc;
     if (oc < cols && r < rows) *reinterpret_cast<uint32_t*>(dst + (size_t)oc * rows + r) = tile[cc][wq];
   }
 }
@@ -93,7 +100,7 @@ int launch_transpose(const void* in, void* out, int batch, int rows, int cols, i
   dim3 grid((cols + 31) / 32, (rows + 31) / 32, batch);
   cudaStream_t st = (cudaStream_t)stream;
   if (esize == 1 && (rows & 3) == 0 && (cols & 3) == 0 && (((uintptr_t)in | (uintptr_t)out) & 3) == 0) {
-    dim3 g4((cols + 63) / 64, (rows + 63) / 64, batch);
+    dim3 g4((cols + 63) / 64, (rows + TR_ROWS - 1) / TR_ROWS, batch);
     k_transpose_u8x4<<<g4, 256, 0, st>>>((const uint8_t*)in, (uint8_t*)out, rows, cols);
   } else if (esize == 1)
     k_transpose<uint8_t><<<grid, 256, 0, st>>>((const uint8_t*)in, (uint8_t*)out, rows, cols);
