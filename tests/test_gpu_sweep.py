@@ -1,0 +1,77 @@
+"""Randomised uint8 sweep against the oracle (Sec. IV, both methods).
+
+Two hundred seeded cases draw a shape, a layout, a mask format, the entry point,
+buffer offsets and in-place use, and for each method a threshold, an
+iteration count, a replacement and (FDSC) a bin size, in blocked or
+interleaved order.  uint8 results must equal the oracle's bit for bit, so
+every combination the planner can reach is checked exactly, including the
+ones no hand-written case lists.
+"""
+import numpy as np
+import pytest
+
+from gpu_util import noise_u8, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2001_03389_gb300 import build
+
+    build.build()
+    from paper_2001_03389_gb300 import rfim
+
+    c = rfim.Context(0)
+    yield c
+    c.set_option("order", 0)
+    c.close()
+
+
+def draw_case(seed):
+    r = np.random.default_rng(seed)
+    B = int(r.integers(1, 4))
+    C = int(r.choice([1, 2, 3, 5, 17, 31, 32, 33, 64, 96, 130, 257, 300]))
+    T = int(r.choice([1, 2, 7, 31, 32, 33, 100, 257, 1000, 1250, 1501, 3001, 3999]))
+    api = str(r.choice(["clean", "clean", "tdsc", "fdsc"]))
+    cut = lambda: dict(k=float(r.choice([1.5, 2.0, 2.5, 3.0, 4.0])), iterations=int(r.integers(1, 4)),
+                       replace=str(r.choice(["mean", "median", "random"])))
+    td = cut() if api in ("clean", "tdsc") else None
+    fd = None
+    if api in ("clean", "fdsc"):
+        fd = cut()
+        fd["bin"] = int(min(C, r.choice([1, 2, 3, 7, 16, 32, 32, C])))
+    if api == "clean" and td is None:
+        td = cut()
+    order = "interleaved" if api == "clean" and r.random() < 0.25 else "blocked"
+    layout = "btc" if r.random() < 0.2 else "bct"
+    mask_fmt = str(r.choice(["bits", "bits", "bytes", "none"]))
+    in_place = bool(r.random() < 0.2)
+    in_off = int(r.integers(0, 8)) if r.random() < 0.3 else 0
+    out_off = int(r.integers(0, 8)) if r.random() < 0.3 else 0
+    return dict(B=B, C=C, T=T, api=api, td=td, fd=fd, order=order, layout=layout, mask_fmt=mask_fmt,
+                in_place=in_place, in_off=in_off, out_off=out_off)
+
+
+@pytest.mark.parametrize("seed", range(200))
+def test_uint8_sweep(oracle, ctx, seed):
+    case = draw_case(9000 + seed)
+    B, C, T = case["B"], case["C"], case["T"]
+    rng = np.random.default_rng(seed)
+    x = noise_u8(rng, (B, C, T))
+    if case["layout"] == "btc":
+        x = np.ascontiguousarray(x.transpose(0, 2, 1))
+    want, wf = oracle.clean(x, case["layout"], tdsc=case["td"], fdsc=case["fd"], order=case["order"])
+    try:
+        ctx.set_option("order", 1 if case["order"] == "interleaved" else 0)
+        mf = None if case["mask_fmt"] == "none" else case["mask_fmt"]
+        got, gf = run_gpu(ctx, x, layout=case["layout"], tdsc=case["td"], fdsc=case["fd"], mask_fmt=mf,
+                          in_place=case["in_place"], in_off=case["in_off"], out_off=case["out_off"], api=case["api"])
+    finally:
+        ctx.set_option("order", 0)
+    bad = np.argwhere(got != want)
+    assert bad.size == 0, f"{case}: {len(bad)} samples differ, first at {bad[:3].tolist()}"
+    if case["mask_fmt"] == "bits":
+        assert np.array_equal(gf, wf > 0), case
+    elif case["mask_fmt"] == "bytes":
+        assert np.array_equal(gf, wf), case
