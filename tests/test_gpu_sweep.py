@@ -1,11 +1,12 @@
-"""Randomised uint8 sweep against the oracle (Sec. IV, both methods).
+"""Randomised sweeps against the oracle (Sec. IV, both methods).
 
 Two hundred seeded cases draw a shape, a layout, a mask format, the entry point,
 buffer offsets and in-place use, and for each method a threshold, an
 iteration count, a replacement and (FDSC) a bin size, in blocked or
 interleaved order.  uint8 results must equal the oracle's bit for bit, so
 every combination the planner can reach is checked exactly, including the
-ones no hand-written case lists.
+ones no hand-written case lists.  Eighty float32 cases do the same for one
+method at a time under the float32 tolerance.
 """
 import numpy as np
 import pytest
@@ -75,3 +76,48 @@ def test_uint8_sweep(oracle, ctx, seed):
         assert np.array_equal(gf, wf > 0), case
     elif case["mask_fmt"] == "bytes":
         assert np.array_equal(gf, wf), case
+
+
+MARGIN = 1e-9
+
+
+@pytest.mark.parametrize("seed", range(80))
+def test_float32_sweep(oracle, ctx, seed):
+    # One method per case (a mask disagreement near a threshold then changes
+    # only its own row or column): decisions may differ from the oracle's only
+    # within 1e-9 relative of the threshold; values away from disagreements
+    # match, unflagged ones bit for bit and replaced ones within 1e-6.
+    r = np.random.default_rng(7000 + seed)
+    B = int(r.integers(1, 3))
+    C = int(r.choice([1, 3, 17, 32, 33, 96, 130, 300]))
+    T = int(r.choice([1, 7, 33, 100, 257, 1000, 3001]))
+    api = str(r.choice(["tdsc", "fdsc"]))
+    cut = dict(k=float(r.choice([2.0, 2.5, 3.0])), iterations=int(r.integers(1, 4)),
+               replace=str(r.choice(["mean", "median", "random"])))
+    if api == "fdsc":
+        cut["bin"] = int(min(C, r.choice([1, 2, 7, 16, 32, C])))
+    td, fd = (cut, None) if api == "tdsc" else (None, cut)
+    layout = "btc" if r.random() < 0.2 else "bct"
+    in_place = bool(r.random() < 0.2)
+    x = (r.standard_exponential((B, C, T)) * 2.0).astype(np.float32)
+    x.reshape(-1)[r.integers(0, x.size, max(1, x.size // 40))] *= 8.0
+    if layout == "btc":
+        x = np.ascontiguousarray(x.transpose(0, 2, 1))
+    want, wf, margin = oracle.clean_f32_margin(x, layout, tdsc=td, fdsc=fd)
+    got, gf = run_gpu(ctx, x, layout=layout, tdsc=td, fdsc=fd, api=api, in_place=in_place)
+    wflag = wf > 0
+    dis = gf != wflag
+    assert not (dis & ~(margin <= MARGIN)).any(), "mask disagreements away from the threshold"
+    # axes of the line a disagreement affects: TDSC rows are (beam, channel),
+    # FDSC columns (beam, time); BTC blocks hold (beam, time, channel)
+    ok = np.ones_like(wflag)
+    for b, i, j in np.argwhere(dis):
+        if (api == "tdsc") == (layout == "bct"):
+            ok[b, i, :] = False
+        else:
+            ok[b, :, j] = False
+    keep = ok & ~wflag & ~gf
+    assert np.array_equal(got[keep].view(np.uint32), x[keep].view(np.uint32)), "unflagged samples changed"
+    both = ok & wflag & gf
+    err = np.abs(got[both].astype(np.float64) - want[both].astype(np.float64))
+    assert np.all(err <= 1e-6 * np.maximum(np.abs(want[both].astype(np.float64)), 1e-30)), "replaced values differ"
