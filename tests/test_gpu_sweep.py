@@ -6,7 +6,8 @@ iteration count, a replacement and (FDSC) a bin size, in blocked or
 interleaved order.  uint8 results must equal the oracle's bit for bit, so
 every combination the planner can reach is checked exactly, including the
 ones no hand-written case lists.  Eighty float32 cases do the same for one
-method at a time under the float32 tolerance.
+method at a time under the float32 tolerance, and twenty ragged uint8
+batches go through rfim_clean_batch, eager or captured.
 """
 import numpy as np
 import pytest
@@ -121,3 +122,35 @@ def test_float32_sweep(oracle, ctx, seed):
     both = ok & wflag & gf
     err = np.abs(got[both].astype(np.float64) - want[both].astype(np.float64))
     assert np.all(err <= 1e-6 * np.maximum(np.abs(want[both].astype(np.float64)), 1e-30)), "replaced values differ"
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_batch_sweep(oracle, ctx, seed):
+    # ragged uint8 batches through rfim_clean_batch (eager or captured, each
+    # block its own shape and beam count) against the oracle block by block
+    import torch
+
+    from gpu_util import unpack_bits
+    from paper_2001_03389_gb300 import rfim
+
+    r = np.random.default_rng(5000 + seed)
+    n = int(r.integers(1, 7))
+    shapes = [(int(r.integers(1, 3)), int(r.choice([3, 32, 64, 96, 200])), int(r.choice([5, 64, 500, 1250, 3000])))
+              for _ in range(n)]
+    rep = str(r.choice(["mean", "median", "random"]))
+    td = dict(k=float(r.choice([2.0, 3.0])), iterations=int(r.integers(1, 3)), replace=rep)
+    fd = dict(k=float(r.choice([2.0, 3.0])), iterations=int(r.integers(1, 3)), replace=rep, bin=3)
+    flags = rfim.BATCH_GRAPH if r.random() < 0.5 else 0
+    xs = [noise_u8(np.random.default_rng(seed * 31 + i), s) for i, s in enumerate(shapes)]
+    dev = torch.device("cuda:0")
+    ins = [torch.from_numpy(x).to(dev) for x in xs]
+    outs = [torch.empty_like(t) for t in ins]
+    masks = [torch.full((rfim.mask_words(s[1], s[2], s[0]),), -1, dtype=torch.int32, device=dev) for s in shapes]
+    blks = [rfim.Context.block(i, o, m, "bct", "bits") for i, o, m in zip(ins, outs, masks)]
+    ctx.clean_batch(blks, rfim.make_cut(**td), rfim.make_cut(**fd), flags=flags)
+    torch.cuda.synchronize()
+    for x, o, m, (B, C, T) in zip(xs, outs, masks, shapes):
+        want, wf = oracle.clean(x, "bct", tdsc=td, fdsc=fd)
+        assert np.array_equal(o.cpu().numpy(), want), (seed, B, C, T)
+        assert np.array_equal(unpack_bits(m.cpu().numpy(), B * C, T).reshape(B, C, T), wf > 0), (seed, B, C, T)
+    assert ctx.device_status() == rfim.OK
