@@ -87,8 +87,8 @@ struct Params {
 
 __host__ __device__ inline int align16i(int x) { return (x + 15) & ~15; }
 
-// Shared memory of one FDSC tile (uint8): ws x pitch tile, per-(t, bin) sums and
-// cached medians, per-column sums of D^2 and keep half-widths, item flag bits,
+// Shared memory of one FDSC tile (uint8): ws x pitch tile, per-(t, bin) sums,
+// cached medians and byte extremes, per-column sums of D^2 and keep half-widths, item flag bits,
 // list of flagged (t, bin) pairs.
 // Rows of the per-(t, bin) arrays are padded to nbp = 8 (mod 32) entries, so the
 // 8 lanes of 4 neighbouring columns hit 32 distinct banks.
@@ -109,7 +109,7 @@ __host__ __device__ inline int fd_flag_bytes(int C, int nb, bool bin_bits) {
 // iteration in progress, bit = tile row); bin: the FDSC bin size
 __host__ __device__ inline int fd_smem_bytes(int ws, int pitch, int nb, int C, bool rnd, int bin) {
   const int nbp = fd_nbp(nb);
-  return ws * pitch + 2 * align16i(ws * nbp * 4) + align16i(ws * nbp * 2) + align16i(ws * 8) + align16i(ws * 8) +
+  return ws * pitch + 2 * align16i(ws * nbp * 4) + 2 * align16i(ws * nbp * 2) + align16i(ws * 8) + align16i(ws * 8) +
          fd_flag_bytes(C, nb, fd_bin_bits(bin, rnd)) + align16i(ws * nb * 4) + 4 * (NT / 32) +
          (rnd ? align16i(C * 4) : 0);
 }

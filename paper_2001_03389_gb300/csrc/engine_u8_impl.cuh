@@ -866,6 +866,7 @@ struct FdLayout {
   unsigned* Sg;           // ws x nbp bin sums
   unsigned* Qg;           // ws x nbp bin sums of squares
   uint16_t* med;          // ws x nbp cached bin medians (0xFFFF unknown)
+  uint16_t* mm;           // ws x nbp byte maximum (low byte) and minimum (high byte) of 32-channel bins
   unsigned long long* V;  // ws: sum of D^2 per column
   unsigned* A;            // ws x 2: keep half-widths per bin-size class
   unsigned* fmask;        // flag bits of the item: [FD_ITEM_T][nb | 1] words (bit j = channel 32 g + j) when
@@ -886,6 +887,8 @@ __device__ __forceinline__ FdLayout fd_layout(unsigned char* smem, int ws, int p
   L.Qg = reinterpret_cast<unsigned*>(p);
   p += align16i(ws * nbp * 4);
   L.med = reinterpret_cast<uint16_t*>(p);
+  p += align16i(ws * nbp * 2);
+  L.mm = reinterpret_cast<uint16_t*>(p);
   p += align16i(ws * nbp * 2);
   L.V = reinterpret_cast<unsigned long long*>(p);
   p += align16i(ws * 8);
@@ -1006,6 +1009,31 @@ __device__ __forceinline__ void fd_store_full(const uint8_t* tile, uint8_t* dst,
 __device__ __forceinline__ unsigned long long fd_contrib(unsigned long long m, unsigned gsz, unsigned S, unsigned Q) {
   // sum over the bin of D^2 = m^2 * G * (G Q - S^2)
   return m * m * (unsigned long long)gsz * ((unsigned long long)gsz * Q - (unsigned long long)S * S);
+}
+
+// The same for a 32-channel bin when every bin has 32 channels (m = L / G = 1):
+// 32 (32 Q - S^2) <= 32 * 32 * 32 * 255^2 < 2^32, so 32-bit arithmetic is exact.
+__device__ __forceinline__ unsigned fd_contrib32(unsigned S, unsigned Q) { return 32u * (32u * Q - S * S); }
+
+// Byte maximum (low byte of the result) and minimum (high byte) of the 32 bytes
+// held in w.  The maximum (minimum) of two 16-bit lanes has the larger (smaller)
+// high byte, so the 16-bit lane extremes (__vmaxu2 / __vminu2, one instruction
+// each, where the byte-lane forms take several) of the words carry the extremes
+// of bytes 1 and 3 in their high bytes, and those of the words shifted up one
+// byte carry the extremes of bytes 0 and 2.
+__device__ __forceinline__ unsigned bin_extremes32(const uint32_t (&w)[8]) {
+  uint32_t hx = w[0], lx = w[0] << 8, hn = w[0], ln = w[0] << 8;
+#pragma unroll
+  for (int i = 1; i < 8; i++) {
+    const uint32_t u = w[i] << 8;
+    hx = __vmaxu2(hx, w[i]);
+    lx = __vmaxu2(lx, u);
+    hn = __vminu2(hn, w[i]);
+    ln = __vminu2(ln, u);
+  }
+  const uint32_t x = __vmaxu2(hx, lx), n = __vminu2(hn, ln);  // bytes 1 and 3: the extremes of two halves
+  const unsigned mx = max(x >> 24, (x >> 8) & 0xFFu), mn = min(n >> 24, (n >> 8) & 0xFFu);
+  return mx | (mn << 8);
 }
 
 // Channels [c0, c0+n) of tile row r, read as words (c0 % 4 == 0; bytes past C are 0).
@@ -1250,6 +1278,19 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
   const bool out4 = ((((uintptr_t)dst) | (uintptr_t)T) & 3) == 0;
   const unsigned long long multF = (unsigned long long)C * mf * mf;
   const unsigned long long multL = (unsigned long long)C * ml * ml;
+  // In place (the item writes the buffer its tile was read from: the fused and
+  // the separate schedules, or a caller's in-place call), the only samples that
+  // differ from what the buffer holds are the flagged ones, and the per-(sample,
+  // bin) flag words name them: the item writes back those bytes alone instead
+  // of the whole tile.
+  const bool sparse_store = bin_bits && static_cast<const void*>(src) == static_cast<const void*>(dst);
+  // 32-channel bins keep their byte extremes (L.mm), taken in the statistics pass
+  // and again whenever a bin changes, so that the flag pass decides a bin with
+  // two comparisons: a byte x of a bin is flagged iff |32 x - S| > A, hence the
+  // bin holds one iff 32 max - S > A or S - 32 min > A.  (Random replacement
+  // changes bins outside the resolution path below and keeps the sum test.)
+  const bool mm_ok = fast32 && !rnd;
+  const bool unit_m = mf == 1ull && ml == 1ull;  // every bin has 32 channels (G = 32, C % 32 == 0)
 
   for (int i = threadIdx.x, n = bin_bits ? FD_ITEM_T * NBO : C; i < n; i += NT) L.fmask[i] = 0;
   if (rnd)
@@ -1332,6 +1373,7 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
             }
             s += s1;
             q += q1;
+            if (mm_ok) L.mm[t * NBP + gi] = (uint16_t)bin_extremes32(w);
           } else if (words) {
             const BinView bv{L.tile, t, gi * G, (int)gsz, pitch};
             const int nw = (gsz + 3) >> 2;  // bytes past C in the tile are zero
@@ -1350,7 +1392,7 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
           }
           L.Sg[t * NBP + gi] = s;
           L.Qg[t * NBP + gi] = q;
-          v += fd_contrib(gi == NB - 1 ? ml : mf, gsz, s, q);
+          v += unit_m && gsz == 32 ? (unsigned long long)fd_contrib32(s, q) : fd_contrib(gi == NB - 1 ? ml : mf, gsz, s, q);
         }
       }
       for (int o = 1; o < LPC; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -1362,7 +1404,9 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
       if (it > 0) {
         // sum of D^2 per column from the bin sums as the last iteration left them
         unsigned long long v = 0;
-        if (own)
+        if (own && unit_m && G == 32)
+          for (int gi = sl; gi < NB; gi += LPC) v += fd_contrib32(L.Sg[tcol * NBP + gi], L.Qg[tcol * NBP + gi]);
+        else if (own)
           for (int gi = sl; gi < NB; gi += LPC)
             v += fd_contrib(gi == NB - 1 ? ml : mf, gi == NB - 1 ? (unsigned)Gl : (unsigned)G, L.Sg[tcol * NBP + gi],
                             L.Qg[tcol * NBP + gi]);
@@ -1390,7 +1434,13 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
           const unsigned gsz = lastbin ? (unsigned)Gl : (unsigned)G;
           int lo, hi;
           const unsigned S = L.Sg[tcol * NBP + gi];
-          if (fast32 && gsz == 32) {
+          if (mm_ok && gsz == 32) {
+            const int A = (int)(lastbin ? Al : Af);
+            const unsigned mm = L.mm[tcol * NBP + gi];
+            any = (int)(32u * (mm & 0xFFu)) - (int)S > A || (int)S - (int)(32u * (mm >> 8)) > A;
+            lo = 0;  // (decided)
+            hi = 255;
+          } else if (fast32 && gsz == 32) {
             const unsigned A = lastbin ? Al : Af;
             lo = S <= A ? 0 : (int)((S - A + 31) >> 5);
             const unsigned hv = (S + A) >> 5;
@@ -1537,6 +1587,7 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
               }
               L.Sg[t * NBP + gi] = s0 + s1;
               L.Qg[t * NBP + gi] = q0 + q1;
+              L.mm[t * NBP + gi] = (uint16_t)bin_extremes32(w);
             }
             L.fmask[(t0 - t_item + t) * NBO + gi] |= fbm;  // (this lane alone resolves (t, gi))
           }
@@ -1620,8 +1671,22 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
     }
     __syncthreads();
 
-    // ---- store: transpose back to [c][t], lanes along time
-    if (full && out4) fd_store_full<true>(L.tile, dst, C, T, t0, pitch);
+    // ---- store: transpose back to [c][t], lanes along time; in place, only the
+    //      flagged bytes of this sub-slab (a warp per tile row, a lane per bin)
+    if (sparse_store) {
+      for (int t = warp; t < ws; t += NT / 32) {
+        const unsigned* frow = L.fmask + (t0 - t_item + t) * NBO;
+        uint8_t* drow = dst + t0 + t;
+        for (int gi = lane; gi < NB; gi += 32) {
+          unsigned f = frow[gi];
+          while (f) {
+            const int c = 32 * gi + __ffs(f) - 1;
+            f &= f - 1;
+            drow[(size_t)c * T] = L.tile[toff(t, c, pitch)];
+          }
+        }
+      }
+    } else if (full && out4) fd_store_full<true>(L.tile, dst, C, T, t0, pitch);
     else if (full) fd_store_full<false>(L.tile, dst, C, T, t0, pitch);
     else for (int u = threadIdx.x; u < nq * nt4; u += NT) {
       const int tq = u % nt4, cq = u / nt4;
