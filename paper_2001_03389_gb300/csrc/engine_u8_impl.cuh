@@ -1355,7 +1355,27 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
     const bool own = tcol < ws;
     {
       unsigned long long v = 0;
-      if (own) {
+      if (own && mm_ok && unit_m) {
+        // every bin has 32 channels: sums, extremes and D^2 with no per-bin cases
+        const int t = tcol;
+        for (int gi = sl; gi < NB; gi += LPC) {
+          uint32_t w[8];
+          load_bin32(L.tile, t, gi, pitch, (sl >> 2) & 1, w);
+          unsigned s0 = 0, q0 = 0, s1 = 0, q1 = 0;
+#pragma unroll
+          for (int i = 0; i < 8; i += 2) {
+            s0 = dp4a_u(w[i], 0x01010101u, s0);
+            q0 = dp4a_u(w[i], w[i], q0);
+            s1 = dp4a_u(w[i + 1], 0x01010101u, s1);
+            q1 = dp4a_u(w[i + 1], w[i + 1], q1);
+          }
+          const unsigned s = s0 + s1, q = q0 + q1;
+          L.Sg[t * NBP + gi] = s;
+          L.Qg[t * NBP + gi] = q;
+          L.mm[t * NBP + gi] = (uint16_t)bin_extremes32(w);
+          v += fd_contrib32(s, q);
+        }
+      } else if (own) {
         const int t = tcol;
         for (int gi = sl; gi < NB; gi += LPC) {
           const unsigned gsz = gi == NB - 1 ? (unsigned)Gl : (unsigned)G;
@@ -1426,6 +1446,25 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
       //        warp's list (the running length is the same in every lane)
       unsigned nlist = 0;
       const int nsteps = (NB + LPC - 1) / LPC;
+      if (mm_ok && unit_m) {
+        // every bin has 32 channels and stored extremes: two comparisons per bin
+        const int A = (int)Af;
+        const unsigned* srow = L.Sg + tcol * NBP;
+        const uint16_t* xrow = L.mm + tcol * NBP;
+        const unsigned below = (1u << lane) - 1u;
+        for (int stp = 0; stp < nsteps; stp++) {
+          const int gi = sl + stp * LPC;
+          bool any = false;
+          if (own && gi < NB) {
+            const int S = (int)srow[gi];
+            const unsigned mm = xrow[gi];
+            any = (int)(32u * (mm & 0xFFu)) - S > A || S - (int)(32u * (mm >> 8)) > A;
+          }
+          const unsigned b = __ballot_sync(0xffffffffu, any);
+          if (any) wlist[nlist + __popc(b & below)] = ((unsigned)tcol << 16) | (unsigned)gi;
+          nlist += __popc(b);
+        }
+      } else
       for (int stp = 0; stp < nsteps; stp++) {
         const int gi = sl + stp * LPC;
         bool any = false;
