@@ -803,6 +803,33 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
     if (mrow && !P.td_mask_or)
       for (int wi = gl; wi < W32; wi += LANES) mrow[wi] = 0u;
     grp_sync<LANES>();  // (orders the zeroed words before the reductions)
+    if (single && !mrowb) {
+      // one keep interval and one replacement value, bit mask or none: the
+      // exact path of final_chunk without its other cases
+      while (slow) {
+        const int r = __ffs(slow) - 1;
+        slow &= slow - 1;
+        const int k = gl + r * LANES;
+        const uint4 w = st[k];
+        const uint4 f = outside4(w, kk);
+        const uint4 y = make_uint4(sel8(w.x, rm4, wide8(f.x)), sel8(w.y, rm4, wide8(f.y)), sel8(w.z, rm4, wide8(f.z)),
+                                   sel8(w.w, rm4, wide8(f.w)));
+        const bool edge = k == 0 || k == g.nch - 1;
+        const int clo = k == 0 ? g.head : 0, chi = k == g.nch - 1 ? g.tail : 16;
+        if (!edge) *reinterpret_cast<uint4*>(ob + 16 * k) = y;
+        else store16_partial(ob + 16 * k, y, clo, chi);
+        if (!mrow) continue;
+        uint32_t fb = chunk_bits16(f);
+        if (edge) fb &= (chi >= 16 ? 0xFFFFu : ((1u << chi) - 1u)) & ~((1u << clo) - 1u);  // not samples
+        if (!fb) continue;
+        const int s0 = 16 * k - g.head;  // chunk byte b is row sample s0 + b
+        const unsigned long long v = s0 < 0 ? (unsigned long long)(fb >> (-s0)) : (unsigned long long)fb << (s0 & 31);
+        const int w0 = s0 < 0 ? 0 : s0 >> 5;
+        if ((uint32_t)v) atomicOr(mrow + w0, (uint32_t)v);
+        if ((uint32_t)(v >> 32)) atomicOr(mrow + w0 + 1, (uint32_t)(v >> 32));
+      }
+      return;
+    }
     while (slow) {
       const int r = __ffs(slow) - 1;
       slow &= slow - 1;
@@ -1523,6 +1550,65 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
       __syncwarp();  // the list entries are visible to the whole warp
       const unsigned n = nlist;
       // resolve the flagged bins of this warp's columns, one per lane
+      if (mm_ok && unit_m) {
+        // every bin has 32 channels: the bin in registers, no per-bin cases
+        const bool more = it + 1 < cut.iterations;
+        const bool med = cut.replace == REP_MEDIAN;
+        const int frow0 = t0 - t_item;
+        for (unsigned e = lane; e < n; e += 32) {
+          const int pair = (int)wlist[e];
+          const int t = pair >> 16, gi = pair & 0xFFFF;  // (column, bin) packed by the flag pass
+          uint32_t w[8];
+          load_bin32(L.tile, t, gi, pitch, lane & 1, w);
+          const int ix = t * NBP + gi;
+          const unsigned s_old = L.Sg[ix];
+          const unsigned A = L.A[2 * t];
+          const int lo = s_old <= A ? 0 : (int)((s_old - A + 31) >> 5);
+          const unsigned hv = (s_old + A) >> 5;
+          const int hi = hv > 255 ? 255 : (int)hv;
+          unsigned r;
+          if (med) {
+            unsigned m = L.med[ix];
+            if (m == 0xFFFFu) {
+              // the lower median lies within one standard deviation of the bin mean
+              const float mu = (float)s_old * (1.0f / 32.0f);
+              const float var = (float)L.Qg[ix] * (1.0f / 32.0f) - mu * mu;
+              const float sd = sqrtf(var > 0.f ? var : 0.f);
+              m = median32_regs(w, max(0, (int)floorf(mu - sd) - 1), min(255, (int)ceilf(mu + sd) + 1));
+              L.med[ix] = (uint16_t)m;
+            }
+            r = m;
+          } else {
+            r = (s_old + 16) >> 5;  // floor((2 S + 32) / 64)
+          }
+          const ByteKeep kp = make_keep(lo, hi);
+          const uint32_t r4 = splat4(r);
+          uint32_t fbm = 0;  // flagged channels of the bin: bit j = channel 32 gi + j
+#pragma unroll
+          for (int i = 0; i < 8; i++) {
+            const uint32_t f = outside_exact(w[i], kp);
+            w[i] = sel8(w[i], r4, wide8(f));
+            fbm |= (((f >> 7) * 0x01020408u) >> 24) << (4 * i);
+          }
+          if (fbm) {
+            store_bin32(L.tile, t, gi, pitch, w);
+            if (more) {  // later iterations start from the new sums and extremes
+              unsigned s0 = 0, q0 = 0, s1 = 0, q1 = 0;
+#pragma unroll
+              for (int i = 0; i < 8; i += 2) {
+                s0 = dp4a_u(w[i], 0x01010101u, s0);
+                q0 = dp4a_u(w[i], w[i], q0);
+                s1 = dp4a_u(w[i + 1], 0x01010101u, s1);
+                q1 = dp4a_u(w[i + 1], w[i + 1], q1);
+              }
+              L.Sg[ix] = s0 + s1;
+              L.Qg[ix] = q0 + q1;
+              L.mm[ix] = (uint16_t)bin_extremes32(w);
+            }
+            L.fmask[(frow0 + t) * NBO + gi] |= fbm;  // (this lane alone resolves (t, gi))
+          }
+        }
+      } else
       for (unsigned e = lane; e < n; e += 32) {
         const int pair = (int)wlist[e];
         const int t = pair >> 16, gi = pair & 0xFFFF;  // (column, bin) packed by the flag pass
