@@ -490,8 +490,10 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
       mbar_arrive_expect_tx(mbar, 16u * (unsigned)(k1 - k0));
       bulk_copy_g2s(st + k0, g.cb + 16 * k0, 16u * (unsigned)(k1 - k0), mbar);
     }
-    for (int k = gl; k < g.nch; k += LANES)
-      if (k < k0 || k >= k1) st[k] = load16_guarded(g.cb + 16 * k, blo, bhi);
+    // the chunks the bulk copy leaves out: at most the first and the last
+    if (k0 == 1 && gl == 0) st[0] = load16_guarded(g.cb, blo, bhi);
+    if (k1 == g.nch - 1 && gl == (g.nch - 1) % LANES)
+      st[g.nch - 1] = load16_guarded(g.cb + 16 * (g.nch - 1), blo, bhi);
     if (bulk) {
       if (!mbar_wait_bounded(mbar, (mpar >> pb) & 1u, P.spin_limit_ns)) atomicExch(P.status, 5u);
       mpar ^= 1u << pb;
@@ -500,20 +502,29 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
   }
   unsigned long long sq[2];
   {
-    unsigned s = 0;
-    unsigned long long q = 0;
-    for (int k = gl; k < g.nch; k += LANES) {
-      uint4 w = rd(k);
-      if (!STREAM && (k == 0 || k == g.nch - 1)) {
-        w = and4(w, chunk_valid(g, k));
-        st[k] = w;
-      }
-      s = dp4a_u(w.x, 0x01010101u, s) + dp4a_u(w.y, 0x01010101u, 0u) + dp4a_u(w.z, 0x01010101u, 0u) +
-          dp4a_u(w.w, 0x01010101u, 0u);
-      q += dp4a_u(w.x, w.x, 0u) + dp4a_u(w.y, w.y, 0u) + dp4a_u(w.z, w.z, 0u) + dp4a_u(w.w, w.w, 0u);
+    if (!STREAM) {
+      // the bytes of the edge chunks outside the row are zeroed in the stage
+      // (by the lane that reads that chunk below)
+      if (gl == 0) st[0] = and4(st[0], chunk_valid(g, 0));
+      const int kl = g.nch - 1;
+      if (kl > 0 && gl == kl % LANES) st[kl] = and4(st[kl], chunk_valid(g, kl));
     }
-    sq[0] = s;
-    sq[1] = q;
+    // A lane sums at most 372,181 / 16 / 256 + 2 chunks (rows read from memory
+    // by the whole CTA; 25 for staged rows), so its partial sums fit 32 bits.
+    unsigned s0 = 0, s1 = 0, q0 = 0, q1 = 0;
+    for (int k = gl; k < g.nch; k += LANES) {
+      const uint4 w = rd(k);
+      s0 = dp4a_u(w.x, 0x01010101u, s0);
+      q0 = dp4a_u(w.x, w.x, q0);
+      s1 = dp4a_u(w.y, 0x01010101u, s1);
+      q1 = dp4a_u(w.y, w.y, q1);
+      s0 = dp4a_u(w.z, 0x01010101u, s0);
+      q0 = dp4a_u(w.z, w.z, q0);
+      s1 = dp4a_u(w.w, 0x01010101u, s1);
+      q1 = dp4a_u(w.w, w.w, q1);
+    }
+    sq[0] = (unsigned long long)s0 + s1;
+    sq[1] = (unsigned long long)q0 + q1;
   }
   if (LANES <= 32) __syncwarp(grp_mask<LANES>());
   grp_sum_row<LANES, 2>(sq, scr);  // (the CTA variant's barriers also publish the staged row)
@@ -787,17 +798,32 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
       }
     const ByteKeep ki = make_keep(ilo, ihi);
     uint32_t slow = 0;  // bit r: chunk gl + r * LANES takes the exact path
-    for (int k = gl, r = 0; k < g.nch; k += LANES, r++) {
-      const uint4 w = st[k];
-      const uint32_t t = outside_fast(w.x, ki) | outside_fast(w.y, ki) | outside_fast(w.z, ki) | outside_fast(w.w, ki);
-      if (k == 0 || k == g.nch - 1 || (t & 0x80808080u)) {
-        slow |= 1u << r;
-        continue;
-      }
-      *reinterpret_cast<uint4*>(ob + 16 * k) = w;
-      if (mrowb && !P.td_mask_or) {
+    // the edge chunks always do; the sweep runs over the interior ones
+    const int kend = g.nch - 1;
+    if (gl == 0) slow = 1u;
+    if (kend > 0 && gl == kend % LANES) slow |= 1u << (kend / LANES);
+    const int kfirst = gl == 0 ? LANES : gl, rfirst = gl == 0 ? 1 : 0;
+    if (mrowb && !P.td_mask_or) {
+      for (int k = kfirst, r = rfirst; k < kend; k += LANES, r++) {
+        const uint4 w = st[k];
+        const uint32_t t = outside_fast(w.x, ki) | outside_fast(w.y, ki) | outside_fast(w.z, ki) | outside_fast(w.w, ki);
+        if (t & 0x80808080u) {
+          slow |= 1u << r;
+          continue;
+        }
+        *reinterpret_cast<uint4*>(ob + 16 * k) = w;
         if (mb_align) *reinterpret_cast<uint4*>(mbb + 16 * k) = make_uint4(0u, 0u, 0u, 0u);
         else store16_partial(mbb + 16 * k, make_uint4(0u, 0u, 0u, 0u), 0, 16);
+      }
+    } else {
+      for (int k = kfirst, r = rfirst; k < kend; k += LANES, r++) {
+        const uint4 w = st[k];
+        const uint32_t t = outside_fast(w.x, ki) | outside_fast(w.y, ki) | outside_fast(w.z, ki) | outside_fast(w.w, ki);
+        if (t & 0x80808080u) {
+          slow |= 1u << r;
+          continue;
+        }
+        *reinterpret_cast<uint4*>(ob + 16 * k) = w;
       }
     }
     if (mrow && !P.td_mask_or)
