@@ -279,11 +279,14 @@ struct MedSearch {
   bool first;
 };
 
-__device__ __forceinline__ void med_init(MedSearch& m, unsigned long long S, unsigned long long Q, int T) {
-  const float mu = (float)S / (float)T;
-  float var = (float)Q / (float)T - mu * mu;
+// rcpT ~ 1 / T: the window and the first probes need the mean and the
+// deviation to well within one unit only (the window has a unit of margin on
+// each side, and the search is exact inside any window holding the median).
+__device__ __forceinline__ void med_init(MedSearch& m, unsigned long long S, unsigned long long Q, float rcpT) {
+  const float mu = (float)S * rcpT;
+  float var = (float)Q * rcpT - mu * mu;
   var = var > 0.f ? var : 0.f;
-  const float sd = sqrtf(var);
+  const float sd = var > 0.f ? var * rsqrtf(var) : 0.f;
   m.lo = max(0, (int)floorf(mu - sd) - 1);
   m.hi = min(255, (int)ceilf(mu + sd) + 1);
   int c = (int)floorf(mu) - 2;
@@ -542,7 +545,7 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
   const bool single = !random && (median || cut.iterations == 1);
   const unsigned long long npad = 16ull * (unsigned)g.nch - (unsigned)T;  // zero bytes in the chunk grid
   const int I = cut.iterations;
-  const float rcpT = 1.0f / (float)T, rcp2T = 0.5f / (float)T;
+  const float rcpT = __frcp_rn((float)T), rcp2T = 0.5f * rcpT;  // (= 1.0f / T, 0.5f / T)
   unsigned r_med = 0;
   int lo_i[16], hi_i[16];
   ByteKeep kp_i[16];
@@ -555,7 +558,7 @@ __device__ void tdsc_row_u8(const Params& P, const Job& J, int row, uint4* st, u
     // with s_in = S0 - (sum of the samples outside), S0 the sum of the input row.
     const unsigned long long S0 = S, Q0 = Q;
     MedSearch ms;
-    med_init(ms, S, Q, T);
+    med_init(ms, S, Q, rcpT);
     for (int it = 0; it < I; it++) {
       int lo, hi;
       tdsc_keep_warp<LANES>(S, Q, T, rcpT, cut.k2, lo, hi);
@@ -1319,12 +1322,13 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
   FdLayout L = fd_layout(smem, Ws, pitch, NB, C, bin_bits);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // column ownership: LPC lanes per column, each warp owns 32 / LPC columns
-  const int LPC = NT / Ws;  // Ws in {8, 16, 32} -> 32, 16, 8 lanes per column
-  const int cpw = 32 / LPC;
-  const int sl = lane % LPC;
-  const int tcol = warp * cpw + lane / LPC;
+  const int lsh = Ws == 32 ? 3 : (Ws == 16 ? 4 : 5);  // Ws in {32, 16, 8} -> 8, 16, 32 lanes per column
+  const int LPC = 1 << lsh;
+  const int cpw = 32 >> lsh;
+  const int sl = lane & (LPC - 1);
+  const int tcol = warp * cpw + (lane >> lsh);
   unsigned* wlist = L.list + warp * (cpw * NB);
-  const float rcpG = 1.0f / (float)G, rcpL = 1.0f / (float)Gl;
+  const float rcpG = __frcp_rn((float)G), rcpL = __frcp_rn((float)Gl);  // (= 1.0f / G, 1.0f / Gl)
   const int NBP = fd_nbp(NB);
   const bool fast32 = G == 32;  // whole bins are two 16-byte tile units
   const bool rows4 = ((((uintptr_t)src) | (uintptr_t)T) & 3) == 0;
@@ -1401,7 +1405,7 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
         }
       }
     }
-    for (int i = threadIdx.x; i < Ws * NBP; i += NT) L.med[i] = 0xFFFFu;
+    for (int i = threadIdx.x; i < Ws * NBP / 2; i += NT) reinterpret_cast<unsigned*>(L.med)[i] = 0xFFFFFFFFu;
     __syncthreads();
 
     // ---- per-warp column work, no CTA barrier until the store
@@ -1498,7 +1502,7 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
       // pass B: bins with a byte outside their keep interval, compacted into this
       //        warp's list (the running length is the same in every lane)
       unsigned nlist = 0;
-      const int nsteps = (NB + LPC - 1) / LPC;
+      const int nsteps = (NB + LPC - 1) >> lsh;
       if (mm_ok && unit_m) {
         // every bin has 32 channels and stored extremes: two comparisons per bin
         const int A = (int)Af;
@@ -1928,7 +1932,7 @@ __device__ __noinline__ void fdsc_wide_u8(const Params& P, const Job& J, int ite
   const bool rnd = RND && cut.replace == REP_RANDOM;
   const unsigned long long mf = J.m_full, ml = J.m_last;
   const unsigned long long multF = (unsigned long long)C * mf * mf, multL = (unsigned long long)C * ml * ml;
-  const float rcpG = 1.0f / (float)G, rcpL = 1.0f / (float)Gl;
+  const float rcpG = __frcp_rn((float)G), rcpL = __frcp_rn((float)Gl);  // (= 1.0f / G, 1.0f / Gl)
   // this item's mask words start from zero unless they hold the beam's TDSC flags
   if (J.mask && P.mask_kind == MASK_BITS && !P.mask_or)
     for (int c = threadIdx.x; c < C; c += NT) static_cast<unsigned*>(J.mask)[(size_t)c * W32 + item] = 0u;
