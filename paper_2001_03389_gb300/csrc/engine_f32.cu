@@ -429,7 +429,6 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
     J.stats[2 * (size_t)row] = (double)S.hi + (double)S.lo;
     J.stats[2 * (size_t)row + 1] = (double)Q.hi + (double)Q.lo;
   }
-  const double rT = 1.0 / (double)T;
   const FF kff{cut.k_hi, cut.k_lo};
   const int I = cut.iterations;
   const bool rnd = RND && cut.replace == REP_RANDOM;  // (RND: the kernel build that holds random replacement)
@@ -447,6 +446,7 @@ __device__ void tdsc_row_f32(const Params& P, const Job& J, int row, unsigned ch
         sd += ((double)v.x + (double)v.y) + ((double)v.z + (double)v.w);  // padding is 0
       }
       sd = grp_dsum<GN>(sd, red, t, h);
+      const double rT = 1.0 / (double)T;  // (only on this rare path)
       const double m2 = sd * rT;
       double ss = 0.0;
       for (int k = t; k < nch; k += GN) {
@@ -612,7 +612,6 @@ __device__ __noinline__ void tdsc_row_f32_long(const Params& P, const Job& J, in
   const float* rin = static_cast<const float*>(J.in) + (size_t)row * T;
   float* rout = static_cast<float*>(J.out) + (size_t)row * T;
   const int I = cut.iterations;
-  const double rT = 1.0 / (double)T;
   const FF kff{cut.k_hi, cut.k_lo};
   __shared__ Cut32 s_cut[16];
   __shared__ float s_rep[16];
@@ -650,6 +649,7 @@ __device__ __noinline__ void tdsc_row_f32_long(const Params& P, const Job& J, in
         sd += (double)cur(i, it, fl);
       }
       sd = grp_dsum<NT>(sd, red, t, 0);
+      const double rT = 1.0 / (double)T;  // (only on this rare path)
       const double m2 = sd * rT;
       double ss = 0.0;
       for (int i = t; i < T; i += NT) {
@@ -723,7 +723,6 @@ __device__ __noinline__ void tdsc_row_f32_long_rnd(const Params& P, const Job& J
   const float* rin = static_cast<const float*>(J.in) + (size_t)row * T;
   float* rout = static_cast<float*>(J.out) + (size_t)row * T;
   const int I = cut.iterations, NW = (T + 31) >> 5;
-  const double rT = 1.0 / (double)T;
   const FF kff{cut.k_hi, cut.k_lo};
   unsigned* fcur = bm;
   unsigned* facc = bm + NW;
@@ -750,6 +749,7 @@ __device__ __noinline__ void tdsc_row_f32_long_rnd(const Params& P, const Job& J
       double sd = 0.0;
       for (int i = t; i < T; i += NT) sd += (double)src[i];
       sd = grp_dsum<NT>(sd, red, t, 0);
+      const double rT = 1.0 / (double)T;  // (only on this rare path)
       const double m2 = sd * rT;
       double ss = 0.0;
       for (int i = t; i < T; i += NT) {
@@ -1010,7 +1010,6 @@ __device__ void fdsc_item_f32(const Params& P, const Job& J, int item, unsigned 
   const FF kff{cut.k_hi, cut.k_lo};
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool vec = ((((uintptr_t)src) | ((uintptr_t)dst)) & 15) == 0 && (T & 3) == 0;
-  const double rC = 1.0 / (double)C;
 
   for (int c = threadIdx.x; c < C; c += NT) L.fm[c] = 0;
   if (rnd)
@@ -1166,6 +1165,7 @@ __device__ void fdsc_item_f32(const Params& P, const Job& J, int item, unsigned 
             sd += (double)L.tile[c * Ws + t] - ((double)m.x + (double)m.y);
           }
           sd = warp_sum(sd);
+          const double rC = 1.0 / (double)C;  // (only on this rare path)
           const double mup = sd * rC;
           double ss = 0.0;
           for (int c = lane; c < C; c += 32) {
