@@ -92,13 +92,14 @@ __device__ __forceinline__ void or16_partial(uint8_t* dst, const uint4& v, int l
 // (W = 8 or 32) each test one candidate around a float estimate; the passing
 // candidates form a prefix.  All lanes of the group return A.
 template <int W>
-__device__ __forceinline__ unsigned max_keep_grp(unsigned long long F, unsigned long long mult, unsigned amax) {
+__device__ __forceinline__ unsigned max_keep_grp(unsigned long long F, unsigned long long mult, unsigned amax,
+                                                 float rcp_mult) {
   const int lane = threadIdx.x & 31;
   const int gl = lane & (W - 1);
   const int gshift = lane & ~(W - 1);
   const unsigned full = (W == 32) ? 0xffffffffu : ((1u << W) - 1u);
   const unsigned gmask = full << gshift;
-  const float est = sqrtf((float)F / (float)mult);
+  const float est = sqrtf((float)F * rcp_mult);  // rcp_mult ~ 1 / mult: an estimate, the candidates decide
   long long e = est < 4.0e9f ? (long long)est : (long long)amax;
   if (e > (long long)amax) e = amax;  // A never exceeds amax
   long long base = e - (W / 2 - 1);
@@ -136,7 +137,7 @@ __device__ __forceinline__ void tdsc_keep_warp(unsigned long long S, unsigned lo
                                                const ExactK2& k2, int& lo, int& hi) {
   const unsigned long long Tl = (unsigned long long)T;
   const unsigned long long R = Tl * Q - S * S;
-  const unsigned A = max_keep_grp<(LANES < 32 ? LANES : 32)>(thr_floor(R, k2), 1ull, 255u * (unsigned)T);
+  const unsigned A = max_keep_grp<(LANES < 32 ? LANES : 32)>(thr_floor(R, k2), 1ull, 255u * (unsigned)T, 1.0f);
   keep_from((unsigned)S, A, (unsigned)T, rcpT, lo, hi);
 }
 
@@ -238,7 +239,10 @@ __device__ __forceinline__ void grp_sum(unsigned long long (&v)[N], unsigned lon
 template <int LANES, int N>
 __device__ __forceinline__ void grp_sum_row(unsigned long long (&v)[N], unsigned long long* scr) {
   static_assert(TD_WARP_CHUNKS * 16 * 255ull * 255ull < (1ull << 32), "warp-row sums fit 32 bits");
-  if constexpr (LANES <= 32) {
+  if constexpr (LANES == 32) {
+#pragma unroll
+    for (int i = 0; i < N; i++) v[i] = __reduce_add_sync(0xffffffffu, (unsigned)v[i]);  // (whole warps only)
+  } else if constexpr (LANES < 32) {
 #pragma unroll
     for (int i = 0; i < N; i++) v[i] = grp_lane_sum<LANES>((unsigned)v[i]);
   } else {
@@ -1335,6 +1339,7 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
   const bool out4 = ((((uintptr_t)dst) | (uintptr_t)T) & 3) == 0;
   const unsigned long long multF = (unsigned long long)C * mf * mf;
   const unsigned long long multL = (unsigned long long)C * ml * ml;
+  const float rcpF = __frcp_rn((float)multF), rcpLm = __frcp_rn((float)multL);
   // In place (the item writes the buffer its tile was read from: the fused and
   // the separate schedules, or a caller's in-place call), the only samples that
   // differ from what the buffer holds are the flagged ones, and the per-(sample,
@@ -1493,8 +1498,8 @@ __device__ void fdsc_item_u8(const Params& P, const Job& J, int item, unsigned c
       }
       // per-column keep half-widths (8-lane candidate groups)
       const unsigned long long Ft = thr_floor(own ? L.V[tcol] : 0ull, cut.k2);
-      const unsigned Af = max_keep_grp<8>(Ft, multF, own ? 255u * (unsigned)G : 0u);
-      const unsigned Al = (Gl == G) ? Af : max_keep_grp<8>(Ft, multL, own ? 255u * (unsigned)Gl : 0u);
+      const unsigned Af = max_keep_grp<8>(Ft, multF, own ? 255u * (unsigned)G : 0u, rcpF);
+      const unsigned Al = (Gl == G) ? Af : max_keep_grp<8>(Ft, multL, own ? 255u * (unsigned)Gl : 0u, rcpLm);
       if (own && sl == 0) {
         L.A[2 * tcol] = Af;
         L.A[2 * tcol + 1] = Al;
@@ -1967,8 +1972,8 @@ __device__ __noinline__ void fdsc_wide_u8(const Params& P, const Job& J, int ite
       }
       grp_sum<NT, 1>(v, scr);
       const unsigned long long F = thr_floor(v[0], cut.k2);
-      const unsigned Af = max_keep_grp<32>(F, multF, 255u * (unsigned)G);
-      const unsigned Al = Gl == G ? Af : max_keep_grp<32>(F, multL, 255u * (unsigned)Gl);
+      const unsigned Af = max_keep_grp<32>(F, multF, 255u * (unsigned)G, __frcp_rn((float)multF));
+      const unsigned Al = Gl == G ? Af : max_keep_grp<32>(F, multL, 255u * (unsigned)Gl, __frcp_rn((float)multL));
       for (int g = threadIdx.x; g < NB; g += NT) {
         const bool last = g == NB - 1;
         const unsigned gs = last ? (unsigned)Gl : (unsigned)G;
@@ -2201,7 +2206,7 @@ template <int MINB, bool RND>
 __global__ void __launch_bounds__(NT, MINB) k_engine_u8(const __grid_constant__ Params P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long scr[GRP_SUM_MAX * (NT / 32)];
-  __shared__ int s_item, s_flag;
+  __shared__ int s_item, s_seg, s_flag;
   // TDSC staging mbarriers, one per staging group so that a barrier's phases
   // are always tracked by the same threads: [0, 8) warps, [8, 40) quarter
   // warps, 40 the CTA.  mpar bits: 0 this warp's, 1 this octet's, 2 the CTA's.
@@ -2211,12 +2216,16 @@ __global__ void __launch_bounds__(NT, MINB) k_engine_u8(const __grid_constant__ 
   __syncthreads();
   unsigned mpar = 0;
   for (;;) {
-    if (threadIdx.x == 0) s_item = (int)atomicAdd(P.counters, 1u);
+    if (threadIdx.x == 0) {
+      const int it = (int)atomicAdd(P.counters, 1u);
+      s_item = it;
+      s_seg = it < P.n_items ? seg_of(P, it) : 0;  // (one thread searches the segment table)
+    }
     __syncthreads();
-    const int item = s_item;
+    const int item = s_item, seg = s_seg;
     __syncthreads();
     if (item >= P.n_items) return;
-    const Seg sg = P.segs[seg_of(P, item)];
+    const Seg sg = P.segs[seg];
     const int idx = item - sg.start;
     const Job& J = P.jobs[sg.job];
     if (sg.kind == 0) {
