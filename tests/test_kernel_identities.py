@@ -1,8 +1,8 @@
 """Arithmetic identities the uint8 kernels rely on, checked on the CPU.
 
 These are not pins of the oracle: they check, by brute force over random and
-edge-case bytes, two shortcuts the FDSC item takes on 32-channel bins, so a
-reader can see that they decide exactly what the definition decides.
+edge-case bytes, the shortcuts the kernels take, so a reader can see that
+they decide exactly what the definition decides.
 
 1. The flag pass.  A byte x of a bin with sum S is flagged iff |32 x - S| > A
    (the exact keep rule for 32-channel bins when every bin has 32 channels,
@@ -12,6 +12,12 @@ reader can see that they decide exactly what the definition decides.
    the larger (smaller) high byte, so the 16-bit lane extremes of the words
    carry the extremes of bytes 1 and 3 in their high bytes, and those of the
    words shifted up one byte carry the extremes of bytes 0 and 2.
+3. The median window.  Both median searches (TDSC rows, FDSC bins) start
+   inside [floor(mu - sigma) - 1, ceil(mu + sigma) + 1], which holds the
+   lower median because any median is within one population sigma of the
+   mean.
+4. Counting by sums of absolute differences.  With f(p) the sum of |x - p|,
+   #(x <= p) = (n + f(p + 1) - f(p)) / 2, which is how both searches count.
 """
 import numpy as np
 
@@ -82,3 +88,40 @@ def test_byte_extremes_from_16bit_lanes():
     mx, mn = extremes_from_words(words)
     assert np.array_equal(mx, x.max(axis=1))
     assert np.array_equal(mn, x.min(axis=1))
+
+
+def lower_median(x):
+    """Rank floor((n - 1) / 2) (0-based) of each row, the lower median."""
+    return np.sort(x, axis=1)[:, (x.shape[1] - 1) // 2]
+
+
+def test_median_window_holds_the_lower_median():
+    # Both median searches start from the window [floor(mu - sigma) - 1,
+    # ceil(mu + sigma) + 1]: any median m minimises E|x - c|, so
+    # |mu - m| <= E|x - m| <= E|x - mu| <= sigma (population sigma).
+    rng = np.random.default_rng(11)
+    for n in [1, 2, 3, 4, 7, 31, 32, 33, 100, 1250]:
+        x = np.clip(np.rint(rng.normal(128, 16, size=(300, n))), 0, 255).astype(np.int64)
+        x[:100] = rng.integers(0, 256, size=(100, n))                         # uniform rows
+        x[100:150, : max(1, n // 3)] = 255                                    # a third of the row bright
+        x[150:200] = np.where(rng.random((50, n)) < 0.5, 0, 255)               # two-valued rows
+        m = lower_median(x)
+        mu = x.mean(axis=1)
+        sd = np.sqrt(((x - mu[:, None]) ** 2).mean(axis=1))
+        assert np.all(np.abs(m - mu) <= sd + 1e-9), n
+        assert np.all((np.floor(mu - sd) - 1 <= m) & (m <= np.ceil(mu + sd) + 1)), n
+
+
+def test_counts_from_sums_of_absolute_differences():
+    # f(p) = sum |x - p| over n bytes; for p <= 254, #(x <= p) = (n + f(p + 1) - f(p)) / 2,
+    # so the lower median is min{p : f(p + 1) - f(p) >= 2 * need - n}, need = floor((n + 1) / 2).
+    rng = np.random.default_rng(12)
+    x = bins(rng, 500)
+    for p in [0, 1, 100, 127, 128, 200, 254]:
+        f = np.abs(x - p).sum(axis=1)
+        f1 = np.abs(x - (p + 1)).sum(axis=1)
+        assert np.array_equal((32 + f1 - f) // 2, (x <= p).sum(axis=1)), p
+        assert np.all((32 + f1 - f) % 2 == 0), p
+    need = (32 + 1) // 2
+    med = np.array([min(p for p in range(256) if (row <= p).sum() >= need) for row in x])
+    assert np.array_equal(med, lower_median(x))
